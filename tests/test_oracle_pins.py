@@ -1,0 +1,465 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: numbers the paper
+prints for worked examples (tests/golden/paper_worked_examples.json), closed forms
+(Boris rotation angle, Yee dispersion relation, cold-plasma frequency, Eq. Belon per
+particle), invariants (Lorentz invariants of the transformed field, Gauss's law,
+canonical momentum, charge continuity) and exact rational brute force.  A plausible
+mistake (dropped term, wrong sign, transposed operand) fails at least one of them.
+"""
+import json
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import EX, EY, EZ, BX, BY, BZ, JX, JY, JZ, PERIODIC, PML, OPEN, LAB, BOOSTED
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_worked_examples.json")))
+C = 2.99792458e8
+
+
+@pytest.fixture(autouse=True)
+def _built(oracle_lib):
+    return oracle_lib
+
+
+# ------------------------------------------------------------------ frame transforms
+
+def test_beam_elongation_worked_example():
+    g = GOLD["beam_elongation"]
+    ratio = oracle.beam_elongation(g["gamma_B"], g["gamma_R"])
+    assert g["sigma_lab_m"] * ratio == pytest.approx(g["sigma_rrf_m_approx"], rel=g["rel_tol"])
+
+
+def test_lorentz_init_reproduces_eq_belon_per_particle():
+    # A monoenergetic beam (u_perp = 0): every particle's RRF position at t' = 0 is its lab
+    # position times the Eq. Belon factor, exactly (to roundoff).
+    for gB, gR in [(300.0, 10.0), (100.0, 10.0), (2000.0, 1372.0), (5.0, 2.0)]:
+        ratio = oracle.beam_elongation(gB, gR)
+        uz = math.sqrt(gB * gB - 1.0)
+        for z in [-3e-3, -1.0, 0.25, 7.0]:
+            xp, up = oracle.lab_to_boosted(gR, [0.0, 0.0, z], [0.0, 0.0, uz])
+            assert xp[2] / z == pytest.approx(ratio, rel=1e-9)
+            # u'_z = gamma_R (u_z - beta_R gamma): velocity addition, checked via beta'
+            bB, bR = uz / gB, math.sqrt(1 - 1 / gR ** 2)
+            bp = (bB - bR) / (1 - bB * bR)
+            assert up[2] / math.sqrt(1 + up[2] ** 2) == pytest.approx(bp, rel=1e-9, abs=1e-12)
+
+
+def test_gamma_R_one_is_identity():
+    rng = np.random.default_rng(0)
+    for _ in range(5):
+        x, u = rng.normal(size=3), rng.normal(size=3) * 3
+        xp, up = oracle.lab_to_boosted(1.0, x, u)
+        np.testing.assert_allclose(xp, x, rtol=0, atol=1e-15)
+        np.testing.assert_allclose(up, u, rtol=0, atol=1e-15)
+
+
+def test_boosted_to_lab_inverts_lab_to_boosted_on_the_worldline():
+    # The RRF event at t' = 0 back-transformed lies on the particle's lab straight line.
+    rng = np.random.default_rng(1)
+    for gR in [2.0, 20.0, 1372.0]:
+        for _ in range(4):
+            x = rng.normal(size=3)
+            u = np.array([rng.normal() * 0.1, rng.normal() * 0.1, 50 + 10 * rng.random()])
+            xp, up = oracle.lab_to_boosted(gR, x, u)
+            xl, tl, ul = oracle.boosted_to_lab(gR, xp, 0.0, up)
+            g = math.sqrt(1 + u @ u)
+            np.testing.assert_allclose(ul, u, rtol=1e-9)
+            np.testing.assert_allclose(xl, x + tl * u / g, rtol=1e-9, atol=1e-9)
+
+
+def test_rrf_time_to_lab_distance_caption_pairs():
+    g = GOLD["rrf_time_to_lab_distance"]
+    for p in g["pairs"]:
+        tp = p["t_rrf_ps"] * 1e-12 * C           # light-metres; c = 1 units
+        xl, tl, _ = oracle.boosted_to_lab(p["gamma_R"], [0.0, 0.0, 0.0], tp, [0.0, 0.0, 0.0])
+        assert xl[2] == pytest.approx(p["L_lab_m"], rel=g["rel_tol"]), p
+
+
+def test_time_skew_eq_DT():
+    # Two electrons at the same RRF instant, dX' apart: lab times differ by gamma_R beta_R dX'.
+    for gR in [10.0, 50.0]:
+        bR = math.sqrt(1 - 1 / gR ** 2)
+        _, t1, _ = oracle.boosted_to_lab(gR, [0, 0, 0.0], 3.0, [0, 0, 1.0])
+        _, t2, _ = oracle.boosted_to_lab(gR, [0, 0, 0.7], 3.0, [0, 0, 5.0])
+        assert t2 - t1 == pytest.approx(gR * bR * 0.7, rel=1e-12)
+
+
+def test_resonant_and_rrf_wavelength_examples():
+    g = GOLD["resonant_wavelength"]
+    K = 93.3729 * g["B_peak_T"] * g["lambda_u_m"]  # K = e B lambda_u / (2 pi m_e c)
+    lam = oracle.resonant_wavelength(g["lambda_u_m"], K, g["gamma_B"])
+    assert lam == pytest.approx(g["lambda_l_m_approx"], rel=g["rel_tol"])
+    r = GOLD["rrf_wavelength"]
+    assert oracle.doppler_rrf(lam, r["gamma_R"]) == pytest.approx(r["lambda_rrf_m_approx"], rel=r["rel_tol"])
+
+
+def test_field_transform_invariants_and_inverse():
+    rng = np.random.default_rng(2)
+    for beta in [0.3, 0.995, 1 - 1e-7]:
+        for _ in range(5):
+            E, B = rng.normal(size=3), rng.normal(size=3)
+            Ep, Bp = oracle.field_transform(E, B, beta)
+            assert Ep @ Bp == pytest.approx(E @ B, rel=1e-7, abs=1e-9 / (1 - beta))
+            assert Ep @ Ep - Bp @ Bp == pytest.approx(E @ E - B @ B, rel=1e-7, abs=1e-9 / (1 - beta))
+            assert Ep[2] == E[2] and Bp[2] == B[2]
+            E2, B2 = oracle.field_transform(Ep, Bp, -beta)
+            np.testing.assert_allclose(E2, E, rtol=1e-6, atol=1e-6)
+            np.testing.assert_allclose(B2, B, rtol=1e-6, atol=1e-6)
+
+
+def test_undulator_in_rrf_is_a_moving_magnet():
+    # A static lab B_y seen from a frame moving at +beta_R z: B'_y = gamma_R B_y and the
+    # motional field E' = -V x B' with V = -beta_R z (the element moves at -c beta_R, Eq. Vprime).
+    s = oracle.Sim((4, 4, 4), (1, 1, 1), 0.1, 20.0)
+    s.set_external(K=1.3, lambda_u=5.0)
+    gR, bR = 20.0, s.beta_R
+    for zp, tp in [(0.1, 0.0), (0.37, 2.0), (-1.0, 11.0)]:
+        E, B = s.external_at(zp, tp)
+        zlab = gR * (zp + bR * tp)
+        By = 1.3 * 2 * math.pi / 5.0 * math.cos(2 * math.pi / 5.0 * zlab)
+        assert B[1] == pytest.approx(gR * By, rel=1e-12, abs=1e-12)
+        V = np.array([0, 0, -bR])
+        np.testing.assert_allclose(E, -np.cross(V, B), rtol=1e-12, atol=1e-12)
+
+
+# ------------------------------------------------------------------ push
+
+def test_boris_uniform_electric_field_exact():
+    rng = np.random.default_rng(3)
+    for _ in range(10):
+        u, E = rng.normal(size=3) * 5, rng.normal(size=3)
+        qm, dt = -1.0, 0.37
+        np.testing.assert_allclose(oracle.boris(qm, dt, E, [0, 0, 0], u), u + qm * E * dt, rtol=1e-14, atol=1e-14)
+
+
+def test_boris_uniform_magnetic_rotation_angle():
+    rng = np.random.default_rng(4)
+    for _ in range(10):
+        u, B = rng.normal(size=3) * 3, rng.normal(size=3) * 2
+        qm, dt = -1.0, 0.2
+        u1 = oracle.boris(qm, dt, [0, 0, 0], B, u)
+        assert np.linalg.norm(u1) == pytest.approx(np.linalg.norm(u), rel=1e-14)
+        g = math.sqrt(1 + u @ u)
+        bh = B / np.linalg.norm(B)
+        upar0, upar1 = u @ bh, u1 @ bh
+        assert upar1 == pytest.approx(upar0, rel=1e-12, abs=1e-13)
+        p0, p1 = u - upar0 * bh, u1 - upar1 * bh
+        ang = math.atan2(np.cross(p0, p1) @ bh, p0 @ p1)
+        # du/dt = (q/m) u x B / gamma turns u about B by -(q/m)|B| dt/gamma (exact Boris: 2 atan)
+        expect = -2 * math.atan(qm * np.linalg.norm(B) * dt / (2 * g))
+        assert ang == pytest.approx(expect, rel=1e-12)
+
+
+def _single_particle_sim(grid, d, dt, gR, order=1):
+    s = oracle.Sim(grid, d, dt, gR, bc=((PERIODIC, PERIODIC),) * 3, order=order)
+    sid = s.add_species(-1.0, 1.0)
+    return s, sid
+
+
+def test_undulator_canonical_momentum_and_lab_trajectory():
+    # One test electron (zero weight: no self field) in the planar undulator of a frame
+    # with gamma_R = gamma/sqrt(1+K^2/2): transverse canonical momentum u_x + (q/m) A_x is
+    # conserved, the mean RRF drift vanishes and the lab orbit amplitude is K/(gamma k_u).
+    K, gB = 1.5, 200.0
+    gR = gB / math.sqrt(1 + K * K / 2)
+    lam_u = 2 * math.pi * gR          # lambda'_u = 2 pi (units of the undulator rule)
+    nz = 64
+    dz = 2 * math.pi / nz
+    dt = 0.02 * dz
+    s, sid = _single_particle_sim((4, 4, nz), (1.0, 1.0, dz), dt, gR)
+    s.set_external(K=K, lambda_u=lam_u)
+    x = np.array([[0.0], [0.0], [0.0]])
+    u = np.array([[0.0], [0.0], [math.sqrt(gB * gB - 1)]])
+    s.load(sid, x, u, w=np.zeros(1), frame=LAB, origin=(2.0, 2.0, 10.0), match_undulator=True)
+    bR = s.beta_R
+    P0 = None
+    uzs, xs = [], []
+    nsteps = int(round(2 * (2 * math.pi) / (bR * dt)))   # ~2 RRF undulator passes
+    X, U, _, _ = s.particles(sid)
+    for n in range(nsteps):
+        s.step(1)
+        X1, U1, _, _ = s.particles(sid)
+        tp = n * dt
+        zlab = gR * (X[0, 2] * dz + bR * tp)
+        # time-centred u_x^n = (u^{n-1/2} + u^{n+1/2})/2 against A_x at (x^n, t^n)
+        P = 0.5 * (U[0, 0] + U1[0, 0]) + (-1.0) * s.undulator_Ax(zlab)
+        if P0 is None:
+            P0 = P
+        assert abs(P - P0) < 1e-4 * K, (n, P, P0)
+        uzs.append(U[0, 2] / math.sqrt(1 + U[0] @ U[0]))
+        xs.append(X[0, 0])
+        X, U = X1, U1
+    assert abs(np.mean(uzs)) < 2e-3
+    amp_lab = 0.5 * (max(xs) - min(xs))     # cells of size 1 in x (transverse is invariant)
+    ku = 2 * math.pi / lam_u
+    assert amp_lab == pytest.approx(K / (gB * ku), rel=0.03)
+
+
+# ------------------------------------------------------------------ deposit
+
+def _rho_of(s, sid, X, w, q):
+    s.set_state(sid, np.array([X]), np.zeros((1, 3)), np.array([w]), np.array([0]))
+    return s.rho()
+
+
+def _div(J, d):
+    jx, jy, jz = J
+    return ((jx - np.roll(jx, 1, axis=2)) / d[0] + (jy - np.roll(jy, 1, axis=1)) / d[1]
+            + (jz - np.roll(jz, 1, axis=0)) / d[2])
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_esirkepov_continuity_node_by_node(order):
+    d = (0.7, 1.1, 0.9)
+    dt = 0.3
+    grid = (6, 7, 8)
+    s = oracle.Sim(grid, d, dt, 5.0, order=order)
+    sid = s.add_species(-1.0, 1.0)
+    rng = np.random.default_rng(10 + order)
+    for _ in range(40):
+        X0 = rng.uniform(0, 1, 3) * np.array(grid)
+        X1 = X0 + rng.uniform(-0.95, 0.95, 3)
+        w = rng.uniform(0.5, 2)
+        J = s.deposit_one(-1.0 * w, X0, X1)
+        X1w = np.mod(X1, grid)
+        r0 = _rho_of(s, sid, X0, w, -1.0)
+        r1 = _rho_of(s, sid, X1w, w, -1.0)
+        resid = (r1 - r0) / dt + _div(J, d)
+        assert np.max(np.abs(resid)) < 1e-12 * np.max(np.abs(r0) / dt)
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_esirkepov_total_current_identity(order):
+    d = (0.5, 0.8, 1.3)
+    dt = 0.2
+    s = oracle.Sim((7, 7, 7), d, dt, 5.0, order=order)
+    rng = np.random.default_rng(20 + order)
+    V = d[0] * d[1] * d[2]
+    for _ in range(20):
+        X0 = rng.uniform(1, 6, 3)
+        X1 = X0 + rng.uniform(-0.9, 0.9, 3)
+        qw = rng.uniform(-2, 2)
+        J = s.deposit_one(qw, X0, X1)
+        for c in range(3):
+            assert J[c].sum() * V == pytest.approx(qw * (X1[c] - X0[c]) * d[c] / dt, rel=1e-12, abs=1e-14)
+
+
+def _frac_shape(order, dd):
+    a = abs(dd)
+    if order == 1:
+        return 1 - a if a < 1 else Fraction(0)
+    if a <= Fraction(1, 2):
+        return Fraction(3, 4) - a * a
+    if a < Fraction(3, 2):
+        return Fraction(1, 2) * (Fraction(3, 2) - a) ** 2
+    return Fraction(0)
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_esirkepov_one_dimensional_motion_equals_exact_flux(order):
+    # Motion along x only: the charge-conserving current through face i+1/2 is uniquely
+    # the charge that left the nodes <= i, computed here exactly in rationals from the shape
+    # definition alone; J_y = J_z = 0.
+    grid = (8, 6, 6)
+    d = (1.0, 1.0, 1.0)
+    dt = 1.0
+    s = oracle.Sim(grid, d, dt, 5.0, order=order)
+    for X0x, X1x in [(Fraction(13, 4), Fraction(7, 2)), (Fraction(29, 8), Fraction(25, 8)),
+                     (Fraction(5, 2), Fraction(16, 5)), (Fraction(41, 10), Fraction(17, 5))]:
+        Y, Z = Fraction(11, 4), Fraction(13, 5)
+        J = s.deposit_one(1.0, [float(X0x), float(Y), float(Z)], [float(X1x), float(Y), float(Z)])
+        assert np.max(np.abs(J[1])) == 0 and np.max(np.abs(J[2])) == 0
+        for k in range(grid[2]):
+            for j in range(grid[1]):
+                syz = _frac_shape(order, j - Y) * _frac_shape(order, k - Z)
+                left0 = left1 = Fraction(0)
+                for i in range(grid[0]):
+                    left0 += _frac_shape(order, i - X0x)
+                    left1 += _frac_shape(order, i - X1x)
+                    expect = (left0 - left1) * syz / dt
+                    assert J[0][k, j, i] == pytest.approx(float(expect), abs=1e-14)
+
+
+# ------------------------------------------------------------------ fields
+
+def test_yee_single_mode_follows_discrete_dispersion():
+    # Standing wave E_y = cos(k.x) (k perpendicular to y), B = 0: the staggered leap-frog keeps
+    # it an eigenmode, E_y^n = cos(w n dt) cos(k.x) with (sin(w dt/2)/dt)^2 = sum (sin(k_i d_i/2)/d_i)^2.
+    grid = (16, 4, 12)
+    d = (0.5, 0.7, 0.6)
+    dt = 0.9 / math.sqrt(sum(1 / v ** 2 for v in d))
+    s = oracle.Sim(grid, d, dt, 1.0)
+    kx, kz = 2 * math.pi * 2 / (grid[0] * d[0]), 2 * math.pi * 1 / (grid[2] * d[2])
+    i = np.arange(grid[0])[None, None, :]
+    k = np.arange(grid[2])[:, None, None]
+    Ey0 = np.cos(kx * i * d[0] + kz * k * d[2]) * np.ones((grid[2], grid[1], grid[0]))
+    s.set_field(EY, Ey0)
+    lam = (2 * math.sin(kx * d[0] / 2) / d[0]) ** 2 + (2 * math.sin(kz * d[2] / 2) / d[2]) ** 2
+    w = 2 / dt * math.asin(dt * math.sqrt(lam) / 2)
+    for n in range(1, 31):
+        s.fdtd()
+        np.testing.assert_allclose(s.field(EY), math.cos(w * n * dt) * Ey0, atol=1e-11)
+    assert np.max(np.abs(s.field(EX))) < 1e-12 and np.max(np.abs(s.field(EZ))) < 1e-12
+
+
+def _curl_pulse(grid):
+    # Discretely divergence-free pulse: E = curl(psi z) on the Yee grid, psi a Gaussian at
+    # the B_z points, so no static (Coulomb-like) remnant is left once radiation leaves.
+    z, y, x = np.meshgrid(*[np.arange(n) for n in grid[::-1]], indexing="ij")
+    c = [g / 2 for g in grid]
+    psi = np.exp(-((x + 0.5 - c[0]) ** 2 + (y + 0.5 - c[1]) ** 2 + (z - c[2]) ** 2) / 4.0)
+    ex = psi - np.roll(psi, 1, axis=1)
+    ey = -(psi - np.roll(psi, 1, axis=2))
+    return ex, ey
+
+
+def test_cpml_absorbs_outgoing_pulse():
+    grid = (40, 40, 40)
+    d = (1.0, 1.0, 1.0)
+    dt = 0.5 / math.sqrt(3)
+    ex, ey = _curl_pulse(grid)
+    energies = {}
+    for bc, pml in [(PML, 8), (OPEN, 0)]:
+        s = oracle.Sim(grid, d, dt, 1.0, bc=((bc, bc),) * 3, pml=pml)
+        s.set_field(EX, ex)
+        s.set_field(EY, ey)
+        e0 = sum(np.sum(s.field(c) ** 2) for c in range(6))
+        for _ in range(int(70 / dt)):
+            s.fdtd()
+        energies[bc] = sum(np.sum(s.field(c) ** 2) for c in range(6)) / e0
+    assert energies[PML] < 1e-3          # radiation absorbed by the layers
+    assert energies[OPEN] > 0.3           # a conducting box keeps it
+
+
+# ------------------------------------------------------------------ whole step
+
+def test_gauss_law_invariant_whole_step():
+    grid = (8, 6, 10)
+    d = (0.6, 0.5, 0.8)
+    dt = 0.5 / math.sqrt(sum(1 / v ** 2 for v in d))
+    for order in (1, 2):
+        s = oracle.Sim(grid, d, dt, 3.0, order=order)
+        se = s.add_species(-1.0, 1.0)
+        si = s.add_species(1.0, 1836.0)
+        rng = np.random.default_rng(30 + order)
+        for sid in (se, si):
+            n = 300
+            X = rng.uniform(0, 1, (n, 3)) * np.array(grid)
+            U = rng.normal(size=(n, 3)) * 2
+            s.set_state(sid, X, U, rng.uniform(0.5, 1.5, n) * 0.05, np.arange(n))
+        G0 = s.divE() - s.rho()
+        for _ in range(6):
+            s.step(1)
+            G = s.divE() - s.rho()
+            assert np.max(np.abs(G - G0)) < 1e-11 * max(1.0, np.max(np.abs(G0)))
+        assert np.max(np.abs(s.field(EX))) > 1e-4  # fields really evolved
+
+
+def test_drifting_cold_plasma_oscillates_at_wp_over_gamma():
+    # RRF plasma: density gamma_R n0 (Eq. Nnormi), drift -beta_R (Eq. Vprime), frozen ions.
+    # A uniform longitudinal velocity perturbation oscillates at w_p0/gamma_R (longitudinal
+    # mass gamma^3 m, density gamma_R n0), with the leap-frog correction (2/dt) asin(w dt/2).
+    gR = 4.0
+    n0 = 1.0
+    grid = (2, 2, 8)
+    d = (1.0, 1.0, 1.0)
+    dt = 0.05
+    s = oracle.Sim(grid, d, dt, gR, order=1)
+    se = s.add_species(-1.0, 1.0)
+    si = s.add_species(1.0, 1836.0, frozen=True)
+    bR = s.beta_R
+    ppc = 2
+    pos = []
+    for k in range(grid[2]):
+        for j in range(grid[1]):
+            for i in range(grid[0]):
+                for a in range(ppc):
+                    pos.append([i + 0.5, j + 0.5, k + (a + 0.5) / ppc])
+    X = np.array(pos)
+    n = len(X)
+    w = gR * n0 * (d[0] * d[1] * d[2]) / ppc
+    Ui = np.tile([0.0, 0.0, -gR * bR], (n, 1))
+    Ue = Ui.copy()
+    Ue[:, 2] += 1e-4
+    s.set_state(se, X, Ue, np.full(n, w), np.arange(n))
+    s.set_state(si, X, Ui, np.full(n, w), np.arange(n))
+    ez = []
+    for _ in range(1400):
+        s.step(1)
+        ez.append(s.field(EZ).mean())
+    ez = np.array(ez)
+    sgn = np.sign(ez)
+    zc = np.where(sgn[1:] * sgn[:-1] < 0)[0]
+    period = 2 * np.mean(np.diff(zc)) * dt
+    wp = math.sqrt(n0) / gR
+    w_disc = 2 / dt * math.asin(wp * dt / 2)
+    assert 2 * math.pi / period == pytest.approx(w_disc, rel=0.01)
+
+
+def test_moving_window_and_plasma_injection_keep_lattice_density():
+    # Cold neutral plasma only: the front injection must keep exactly ppc particles in every
+    # interior cell at every step (no gap or double plane), fields stay zero, and the window
+    # shifts at floor(v_w n dt / dz).
+    grid = (6, 6, 24)
+    d = (1.0, 1.0, 1.0)
+    gR = 5.0
+    dt = 0.45
+    vw = 0.9
+    s = oracle.Sim(grid, d, dt, gR, bc=((PERIODIC, PERIODIC), (PERIODIC, PERIODIC), (OPEN, OPEN)),
+                   order=2, moving_window=True, window_v=vw)
+    se = s.add_species(-1.0, 1.0)
+    si = s.add_species(1.0, 1836.0, frozen=True)
+    s.set_plasma(se, si, (1, 2, 2), (0, 6, 0, 6), (-1e9, 1e9), (0.3, 0.3))
+    for n in range(60):
+        X, _, _, _ = s.particles(se)
+        cz = np.floor(X[:, 2]).astype(int)
+        counts = np.bincount(cz, minlength=grid[2])
+        interior = counts[3:grid[2] - 4]
+        assert np.all(interior == 6 * 6 * 4), (n, counts)
+        assert s.time()[1] == math.floor(vw * n * dt / d[2])
+        s.step(1)
+    assert max(np.max(np.abs(s.field(c))) for c in range(9)) < 1e-12
+
+
+def test_moments_definitions():
+    grid = (4, 4, 64)
+    d = (1.0, 1.0, 0.25)
+    s = oracle.Sim(grid, d, 0.1, 1.0 + 1e-12, order=1)
+    sid = s.add_species(-1.0, 1.0)
+    rng = np.random.default_rng(7)
+    n = 20000
+    x = rng.normal(0, 0.3, n)
+    ux = 0.5 * x + rng.normal(0, 0.2, n)
+    lam = 2.0
+    z = 8 + lam * rng.integers(0, 3, n) + 1e-9
+    X = np.stack([x + 2, np.full(n, 2.0), z / d[2]], 1)
+    U = np.stack([ux, np.zeros(n), np.full(n, 3.0)], 1)
+    s.set_state(sid, X, U, np.ones(n), np.arange(n))
+    m = s.moments(sid, frame=0, k=2 * math.pi / lam)
+    sx, sux = np.std(x), np.std(ux)
+    cxu = np.mean((x - x.mean()) * (ux - ux.mean()))
+    assert m["emit_nx"] == pytest.approx(math.sqrt(sx ** 2 * sux ** 2 - cxu ** 2), rel=1e-9)
+    assert m["emit_nx"] == pytest.approx(0.3 * 0.2, rel=0.03)
+    assert m["bunching"] == pytest.approx(1.0, abs=1e-6)
+    assert m["count"] == n
+
+
+def test_tile_sort_groups_tiles_and_cells():
+    rng = np.random.default_rng(8)
+    grid, tile = (20, 18, 44), (8, 8, 8)
+    cells = np.stack([rng.integers(0, g, 5000) for g in grid], 1)
+    order, keys = oracle.tile_sort(cells, grid, tile)
+    assert sorted(order.tolist()) == list(range(5000))
+    assert np.all(np.diff(keys) >= 0)
+    c = cells[order]
+    t = (c[:, 2] // 8 * 3 + c[:, 1] // 8) * 3 + c[:, 0] // 8
+    assert np.all(np.diff(t) >= 0)
+    same = np.diff(keys) == 0
+    assert np.all(np.diff(order)[same] > 0)           # stable among equal keys
+    assert np.all((np.diff(c, axis=0) == 0).all(1) == same)
