@@ -1,0 +1,238 @@
+/*
+ * gbpic — C-ABI of the GB300 (sm_103a) hot path of the relativistic-reference-frame (RRF,
+ * boosted-frame) particle-in-cell method of arXiv 2411.04703.
+ *
+ * The calls follow the paper's statement of the problem: a Maxwell solver and current
+ * weighting in a frame moving at gamma_R (Sec. "Relativistic booster frame", Eq. Max1-Max4),
+ * a beam defined in the laboratory frame and transformed by the code (Eq. Lor1, Lor2,
+ * RRFVel; the beam paragraph of Sec. "Electron propagation in vacuum"), static lab elements
+ * (undulator, plasma) transformed into the RRF (Eq. M1-M4, Nnormi, Vprime), a moving window
+ * with absorbing field boundaries and dummy particles, and a leap-frog push.
+ *
+ * Units (normalisation rule stated with Table I): c = 1, time in 1/w_n, length in c/w_n,
+ * momentum u = p/(m_e c), fields in m_e c w_n / e, densities in n_n = eps0 m_e w_n^2/e^2.
+ * Then dE/dt = curl B - J, dB/dt = -curl E, div E = rho.
+ *
+ * Conventions shared by every call:
+ *  - Every function returns an int status: PIC_OK (0) or a negative PIC_ERR_* code.  No
+ *    exception or signal crosses the ABI.  pic_last_error() gives a message.
+ *  - Errors are sticky: after a device-side error (PIC_ERR_DEVICE) or a CUDA error the
+ *    context refuses further work and only pic_last_error / pic_destroy are valid.
+ *  - Host arrays are borrowed for the duration of the call only.  Pointers documented as
+ *    "host or device" may be either (the copy uses cudaMemcpyDefault).
+ *  - Grid arrays are float, x fastest: index = (k * ny + j) * nx + i.  Yee staggering:
+ *    E_x at (i+1/2, j, k), E_y at (i, j+1/2, k), E_z at (i, j, k+1/2), B_x at
+ *    (i, j+1/2, k+1/2), B_y at (i+1/2, j, k+1/2), B_z at (i+1/2, j+1/2, k), J like E,
+ *    rho at the nodes (i, j, k).
+ *  - Every call that launches work enqueues it on the context's stream and returns without
+ *    waiting, except the getters, which synchronise that stream.
+ *  - Limits: nx, ny <= 1024, nz <= 2048 (cell index packed into 32 bits); fewer than
+ *    2^31 particles per species.
+ */
+#ifndef GBPIC_H
+#define GBPIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PIC_OK 0
+#define PIC_ERR_ARG (-1)       /* invalid argument (message says which) */
+#define PIC_ERR_CUDA (-2)      /* a CUDA runtime call failed */
+#define PIC_ERR_ALLOC (-3)     /* device allocation failed (allocator returned NULL) */
+#define PIC_ERR_STATE (-4)     /* call not valid in the context's state (e.g. poisoned) */
+#define PIC_ERR_DEVICE (-5)    /* a kernel raised its device error word (see message) */
+#define PIC_ERR_CAPACITY (-6)  /* a species' particle storage is full */
+
+enum { PIC_BC_PERIODIC = 0, PIC_BC_PML = 1, PIC_BC_OPEN = 2 };
+enum { PIC_FRAME_LAB = 0, PIC_FRAME_BOOSTED = 1 };
+enum {
+    PIC_EX = 0, PIC_EY, PIC_EZ, PIC_BX, PIC_BY, PIC_BZ, PIC_JX, PIC_JY, PIC_JZ, PIC_RHO
+};
+enum { PIC_EXT_NONE = 0, PIC_EXT_PLANAR_UNDULATOR = 1 };
+
+typedef struct pic_ctx pic_ctx;
+
+typedef struct { int nx, ny, nz; } pic_grid;
+
+/* Field boundaries per face (face[d][0] low, face[d][1] high; a periodic dim must be
+ * periodic on both faces).  PIC_BC_PML: convolutional PML of pml_cells cells ("the fields
+ * are absorbed upon interaction with the boundaries", Sec. "Relativistic booster frame");
+ * PIC_BC_OPEN: field values outside the grid are zero.  Particles whose cell leaves
+ * [margin_lo, n-1-margin_hi] of a non-periodic dim become dummy (inactive) particles
+ * (margins 1/2 for CIC, 2/3 for TSC).  moving_window: the window moves along +z at
+ * window_v (units of c) in whole cells, floor(window_v n dt / dz) shifts by step n
+ * (the paper's moving window "adjusted to the RRF time-step"). */
+typedef struct {
+    int face[3][2];
+    int pml_cells;
+    int moving_window;
+    double window_v;
+} pic_boundaries;
+
+/* Device memory and stream supplied by the caller (e.g. PyTorch's caching allocator and
+ * current stream).  alloc/free may be NULL (then cudaMalloc/cudaFree are used); stream may
+ * be NULL (then the context creates its own non-blocking stream).  device: CUDA ordinal. */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *user);
+    void (*free)(void *ptr, size_t bytes, void *user);
+    void *user;
+    void *stream;
+    int device;
+} pic_device;
+
+/* Create a simulation context: grid of nx*ny*nz cells of size dx[3] (normalised), time step
+ * dt, frame Lorentz factor gamma_boost >= 1 (beta_R = sqrt(1 - 1/gamma^2), Eq. RRFVel),
+ * boundaries bc, particle shape order 1 (CIC) or 2 (TSC).  Fields start at zero.  dt must
+ * satisfy the Yee Courant limit dt < 1/sqrt(sum 1/dx_i^2).  On success *out owns all device
+ * state (allocated through dev); on failure *out is NULL and the status says why
+ * (pic_last_error(NULL) gives the message of a failed create). */
+int pic_create(pic_ctx **out, pic_grid grid, const double dx[3], double dt, double gamma_boost,
+               const pic_boundaries *bc, int shape_order, const pic_device *dev);
+
+/* Tile size for the per-tile sort and the particle kernel (cells, each 2..16), number of
+ * steps between sorts (>= 1), and the margin (cells, 0..2) a particle may drift outside its
+ * tile between sorts before it takes the slower global-memory path.  Defaults 8x8x8, 8, 1. */
+typedef struct {
+    int tile[3];
+    int sort_every;
+    int margin;
+} pic_tuning;
+int pic_set_tuning(pic_ctx *ctx, const pic_tuning *t);
+
+/* A particle population (beam electrons, plasma electrons and ions are separate
+ * populations, Sec. "Relativistic booster frame").  q, m in units of e and m_e; frozen:
+ * momentum never pushed (lab-immobile ions drift at -beta_R in the RRF and carry their own
+ * current j_i = v_R rho_i, deposited with the same weighting).  capacity: maximum particles
+ * held (>= n of the load).  origin: grid coordinate (cells) of the loaded positions' zero.
+ * match_undulator (lab frame only): the beam is already inside the undulator — before the
+ * transform, u_x += -(q/m) A_x(z_lab) at the event's lab coordinate z + gamma_R origin_z dz
+ * and u_z is lowered so that the lab energy is unchanged. */
+typedef struct {
+    double q, m;
+    int frozen;
+    int64_t capacity;
+    double origin[3];
+    int match_undulator;
+} pic_species;
+
+/* Create a species and load n particles (n may be 0).  x, u: host FP64 arrays [3][n]
+ * (component-major), w: host FP64 [n] weights (real particles per macroparticle,
+ * normalised) or NULL for 1.  frame PIC_FRAME_LAB: x are lab positions at lab time 0 relative
+ * to the reference point, u lab momenta; each event is Lorentz-transformed (Eq. Lor1-Lor2),
+ * its momentum boosted, and the particle drifted ballistically to t' = 0 (Eq. BGauss/Belon
+ * take the distribution at t' = 0); all in FP64 on the device.  frame PIC_FRAME_BOOSTED: x
+ * are RRF positions at t' = 0.  Grid coordinate = x/dx + origin; particles outside the active
+ * region are dropped.  Particle ids are 0..n-1 in load order.  *species_id receives the id. */
+int pic_load_species(pic_ctx *ctx, const pic_species *sp, int64_t n, const double *x,
+                     const double *u, const double *w, int frame, int *species_id);
+
+/* Static lab element transformed into the RRF.  PIC_EXT_PLANAR_UNDULATOR: lab field
+ * B_y = B0 f(z) cos(k_u z + phase), B0 = K k_u (K = e B0/(m c k_u)), k_u = 2 pi/lambda_u;
+ * f = 0 before z_start, linear to 1 over ramp_len (the entrance "gentle slope", Sec.
+ * "Electron propagation ... under external field"), 1 after; ramp_len < 0 or
+ * z_start = -inf: f = 1 everywhere.  In the RRF the element moves at -c beta_R (Eq. Vprime):
+ * the particle at RRF z', t' sees lab z = gamma_R (z' + beta_R t') and Eq. M1-M4 give
+ * B'_y = gamma_R B_y, E'_x = -beta_R B'_y.  Evaluated analytically at each particle, added to
+ * the gathered self fields.  lambda_u, z_start, ramp_len: lab, normalised. */
+typedef struct {
+    int type;
+    double K, lambda_u, phase, z_start, ramp_len;
+} pic_external;
+int pic_set_external_field(pic_ctx *ctx, const pic_external *f);
+
+/* Background plasma (Sec. "Relativistic booster frame": N'_e = gamma_R N_e, Eq. Nnormi;
+ * static lab elements move at -c beta_R, Eq. Vprime; plasma enters the window on one side
+ * and leaves on the other).  Creates two species, electrons (q = -1, m = 1) and co-located
+ * frozen ions (q = +1, same weighting), with cold momentum u'_z = -gamma_R beta_R, on a
+ * regular lattice of ppc[0]*ppc[1]*ppc[2] per cell in the transverse cell range
+ * x_range = {x0, x1, y0, y1}.  Lattice plane m sits at RRF z' = ((m + 1/2)/ppc_z) dz -
+ * beta_R t'; its lab position gamma_R (m + 1/2) dz / ppc_z sets the lab density
+ * n(z_lab) (piecewise linear through n_nodes points (z_nodes, density), zero outside) and
+ * the weight gamma_R n dx dy dz / (ppc_x ppc_y ppc_z).  Fills the window now; every later
+ * step injects the planes whose grid coordinate fell below nz - margin_hi.  Particles are
+ * ordered and numbered by (plane, y cell, x cell, y sub, x sub).  Arrays are host FP64. */
+typedef struct {
+    int ppc[3];
+    int x_range[4];
+    int n_nodes;
+    const double *z_nodes;
+    const double *density;
+    int64_t capacity;   /* per species; 0: computed from the window and the sort cadence */
+} pic_plasma;
+int pic_set_plasma(pic_ctx *ctx, const pic_plasma *p, int *electron_id, int *ion_id);
+
+/* Advance n steps (Sec. "Relativistic booster frame": leap-frog push and current weighting
+ * for Eq. Max3-Max4, Maxwell Eq. Max1-Max2).  Per step: every `sort_every` steps a per-tile
+ * counting sort of each species by cell; per species a fused kernel gathers E^n, B^n (same
+ * shape as the deposit, each component at its Yee point) plus the external field at t'_n,
+ * pushes u^{n-1/2} -> u^{n+1/2} (Boris; frozen species skip it), moves x^n -> x^{n+1} and
+ * deposits the Esirkepov current J^{n+1/2}; then B^{n+1/2} = B^n - dt/2 curl E^n,
+ * E^{n+1} = E^n + dt (curl B^{n+1/2} - J), B^{n+1} = B^{n+1/2} - dt/2 curl E^{n+1} (with CPML);
+ * then the window shifts due by step n+1 and plasma planes entering the front are injected.
+ * Asynchronous on the context stream. */
+int pic_step(pic_ctx *ctx, int64_t n);
+
+/* Wait for the context stream; returns PIC_ERR_DEVICE if a kernel raised the error word. */
+int pic_sync(pic_ctx *ctx);
+
+/* Force a per-tile sort of every species now (the sort also compacts dummy particles). */
+int pic_sort(pic_ctx *ctx);
+
+/* Copy one grid component (PIC_EX..PIC_JZ; J is the current of the last step) or the charge
+ * density PIC_RHO (deposited now from every species with the particle shape) into dst
+ * (host or device, n = nx*ny*nz floats).  Synchronous. */
+int pic_get_fields(pic_ctx *ctx, int which, float *dst, size_t n);
+
+/* Overwrite one grid component (PIC_EX..PIC_JZ) from src (host or device, n = nx*ny*nz
+ * floats), e.g. to restart from saved fields.  Asynchronous on the context stream for device
+ * sources; synchronous for host sources. */
+int pic_set_fields(pic_ctx *ctx, int which, const float *src, size_t n);
+
+/* Copy the live particles of a species to host arrays of capacity `cap`: cell indices
+ * [3][cap] (int32 i, j, k), in-cell offsets [3][cap] (float, [0,1)), momenta [3][cap], weights
+ * [cap] and ids [cap], in storage order (tile-sorted order after a sort).  Any output pointer
+ * may be NULL.  *n_out receives the number of live particles (PIC_ERR_CAPACITY if > cap).
+ * Synchronous. */
+int pic_get_particles(pic_ctx *ctx, int species_id, int64_t cap, int64_t *n_out, int32_t *cell,
+                      float *off, float *u, float *w, int64_t *id);
+
+/* FP64 beam diagnostics (the benchmark spec precision split: FP64 for back-transformed diagnostics
+ * and conservation sums).  frame PIC_FRAME_BOOSTED: at t' = step dt, positions in
+ * normalised RRF length (z' absolute, window shifts included).  PIC_FRAME_LAB: each
+ * particle's RRF event and momentum are transformed back (inverse Eq. Lor1-Lor2) and drifted
+ * ballistically to the weighted mean lab time (one RRF instant spans the lab times of
+ * Eq. DT).  bunching = |sum w exp(-i k z)| / sum w at wavenumber k_bunch of that frame.
+ * Normalised emittance sqrt(<dx^2><du^2> - <dx du>^2) (central, weighted); relative energy
+ * spread std(gamma)/mean(gamma); kinetic energy sum w m (gamma - 1); field energy
+ * (1/2) sum (E^2 + B^2) dV over the grid.  Synchronous. */
+typedef struct {
+    double count, sum_w, charge;
+    double mean[3], rms[3], mean_u[3];
+    double mean_gamma, rel_energy_spread;
+    double emit_n[2];
+    double bunching, kinetic_energy, mean_t, field_energy;
+} pic_moments;
+int pic_get_moments(pic_ctx *ctx, int species_id, int frame, double k_bunch, pic_moments *out);
+
+/* Step count, window shifts and last injected plasma plane of the context: out[3]. */
+int pic_get_time(pic_ctx *ctx, int64_t out[3]);
+
+/* Number of live particles of a species (synchronous; dummy particles not yet compacted by
+ * a sort are not counted). */
+int pic_get_count(pic_ctx *ctx, int species_id, int64_t *n_out);
+
+/* Release every device allocation of the context.  NULL is accepted. */
+int pic_destroy(pic_ctx *ctx);
+
+/* Message of the last error of ctx (of the last failed pic_create when ctx is NULL).  The
+ * string is owned by the library and valid until the next call on ctx. */
+const char *pic_last_error(const pic_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBPIC_H */

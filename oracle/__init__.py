@@ -77,7 +77,7 @@ def lib():
                 "osim_set_external": (None, [vp, i, d, d, d, d, d]),
                 "osim_external_at": (None, [vp, d, d, pd, pd]),
                 "osim_undulator_Ax": (d, [vp, d]),
-                "osim_set_plasma": (None, [vp, i, i, pi, pi, i, pd, pd]),
+                "osim_set_plasma": (None, [vp, i, i, pi, pi, i, pd, pd, i]),
                 "osim_step": (None, [vp, l]),
                 "osim_fdtd": (None, [vp]),
                 "osim_dropped": (l, [vp]),
@@ -264,12 +264,13 @@ class Sim:
     def undulator_Ax(self, zlab):
         return self.L.osim_undulator_Ax(self.h, float(zlab))
 
-    def set_plasma(self, sp_e, sp_i, ppc, xrange, z_nodes, n_nodes):
+    def set_plasma(self, sp_e, sp_i, ppc, xrange, z_nodes, n_nodes, fill=True):
         ppc = np.ascontiguousarray(ppc, np.int32)
         xr = np.ascontiguousarray(xrange, np.int32)
         zn = _f64(z_nodes)
         dn = _f64(n_nodes)
-        self.L.osim_set_plasma(self.h, sp_e, sp_i, _pi(ppc), _pi(xr), zn.size, _pd(zn), _pd(dn))
+        self.L.osim_set_plasma(self.h, sp_e, sp_i, _pi(ppc), _pi(xr), zn.size, _pd(zn), _pd(dn),
+                               int(bool(fill)))
 
     def step(self, n=1):
         self.L.osim_step(self.h, int(n))

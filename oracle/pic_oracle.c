@@ -540,9 +540,10 @@ static void o_inject_planes(osim *s, long m0, long m1)
 /* Background plasma: electrons (species sp_e) and co-located ions (sp_i, same weighting,
  * Sec. "Relativistic booster frame"), lab profile (z nodes, density nodes), p_x*p_y*p_z
  * particles per cell on a regular lattice in the transverse cell range xr = {x0,x1,y0,y1}.
- * Fills the window at the current time; later steps inject planes entering the front. */
+ * Fills the window at the current time (fill != 0); later steps inject planes entering the
+ * front. */
 void osim_set_plasma(void *h, int sp_e, int sp_i, const int *ppc, const int *xr, int nprof,
-                     const double *zn, const double *dn)
+                     const double *zn, const double *dn, int fill)
 {
     osim *s = (osim *)h;
     s->plasma = 1;
@@ -556,6 +557,7 @@ void osim_set_plasma(void *h, int sp_e, int sp_i, const int *ppc, const int *xr,
     s->nprof_v = (double *)malloc(nprof * sizeof(double));
     memcpy(s->zprof, zn, nprof * sizeof(double));
     memcpy(s->nprof_v, dn, nprof * sizeof(double));
+    if (!fill) return; /* parameters only: the caller loads an existing plasma state */
     double lo = (double)o_margin_lo(s->order) + (double)s->shifts + s->bR * (double)s->step * s->dt / s->d[2];
     long m0 = (long)ceil((double)s->ppc[2] * lo - 0.5);
     long m1 = o_plane_max(s, s->step, s->shifts);

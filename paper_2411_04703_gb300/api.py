@@ -1,0 +1,343 @@
+"""Thin ctypes binding of the gbpic C-ABI (include/gbpic.h).
+
+Argument marshalling only: every step of the PIC path runs in the CUDA kernels of
+``libgbpic.so``.  PyTorch supplies device memory (its caching allocator, through the
+``pic_device`` callbacks) and the CUDA stream.  There is no CPU fallback: if the
+library or a GPU is missing, constructing :class:`Sim` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+PIC_OK = 0
+PIC_BC_PERIODIC, PIC_BC_PML, PIC_BC_OPEN = 0, 1, 2
+PIC_FRAME_LAB, PIC_FRAME_BOOSTED = 0, 1
+PIC_EX, PIC_EY, PIC_EZ, PIC_BX, PIC_BY, PIC_BZ, PIC_JX, PIC_JY, PIC_JZ, PIC_RHO = range(10)
+PIC_EXT_NONE, PIC_EXT_PLANAR_UNDULATOR = 0, 1
+ERRORS = {-1: "PIC_ERR_ARG", -2: "PIC_ERR_CUDA", -3: "PIC_ERR_ALLOC", -4: "PIC_ERR_STATE",
+          -5: "PIC_ERR_DEVICE", -6: "PIC_ERR_CAPACITY"}
+MOMENT_NAMES = [
+    "count", "sum_w", "charge", "mean_x", "mean_y", "mean_z", "rms_x", "rms_y", "rms_z",
+    "mean_ux", "mean_uy", "mean_uz", "mean_gamma", "rel_energy_spread", "emit_nx",
+    "emit_ny", "bunching", "kinetic_energy", "mean_t", "field_energy",
+]
+
+
+class PicError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class pic_grid(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int)]
+
+
+class pic_boundaries(C.Structure):
+    _fields_ = [("face", (C.c_int * 2) * 3), ("pml_cells", C.c_int), ("moving_window", C.c_int),
+                ("window_v", C.c_double)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
+
+
+class pic_device(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", C.c_void_p), ("stream", C.c_void_p),
+                ("device", C.c_int)]
+
+
+class pic_tuning(C.Structure):
+    _fields_ = [("tile", C.c_int * 3), ("sort_every", C.c_int), ("margin", C.c_int)]
+
+
+class pic_species(C.Structure):
+    _fields_ = [("q", C.c_double), ("m", C.c_double), ("frozen", C.c_int), ("capacity", C.c_int64),
+                ("origin", C.c_double * 3), ("match_undulator", C.c_int)]
+
+
+class pic_external(C.Structure):
+    _fields_ = [("type", C.c_int), ("K", C.c_double), ("lambda_u", C.c_double), ("phase", C.c_double),
+                ("z_start", C.c_double), ("ramp_len", C.c_double)]
+
+
+class pic_plasma(C.Structure):
+    _fields_ = [("ppc", C.c_int * 3), ("x_range", C.c_int * 4), ("n_nodes", C.c_int),
+                ("z_nodes", C.POINTER(C.c_double)), ("density", C.POINTER(C.c_double)),
+                ("capacity", C.c_int64)]
+
+
+class pic_moments(C.Structure):
+    _fields_ = [("v", C.c_double * 20)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def lib(build_if_missing: bool = True):
+    """Load libgbpic.so (building it with nvcc when missing or stale) and set signatures."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build() if build_if_missing else _build.LIB_PATH
+        if not os.path.exists(path):
+            raise RuntimeError(f"gbpic CUDA library missing at {path}; run build()")
+        L = C.CDLL(path)
+        vp, i, i64, d, sz = C.c_void_p, C.c_int, C.c_int64, C.c_double, C.c_size_t
+        P = C.POINTER
+        sigs = {
+            "pic_create": [P(vp), pic_grid, P(d), d, d, P(pic_boundaries), i, P(pic_device)],
+            "pic_set_tuning": [vp, P(pic_tuning)],
+            "pic_load_species": [vp, P(pic_species), i64, vp, vp, vp, i, P(i)],
+            "pic_set_external_field": [vp, P(pic_external)],
+            "pic_set_plasma": [vp, P(pic_plasma), P(i), P(i)],
+            "pic_step": [vp, i64],
+            "pic_sync": [vp],
+            "pic_sort": [vp],
+            "pic_get_fields": [vp, i, vp, sz],
+            "pic_set_fields": [vp, i, vp, sz],
+            "pic_get_particles": [vp, i, i64, P(i64), vp, vp, vp, vp, vp],
+            "pic_get_moments": [vp, i, i, d, P(pic_moments)],
+            "pic_get_time": [vp, P(i64)],
+            "pic_get_count": [vp, i, P(i64)],
+            "pic_destroy": [vp],
+        }
+        for name, args in sigs.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = C.c_int
+        L.pic_last_error.argtypes = [vp]
+        L.pic_last_error.restype = C.c_char_p
+        _lib = L
+        return L
+
+
+def _ptr(a) -> Optional[int]:
+    """Raw address of a numpy array or torch tensor (host or device), or None."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return int(a.data_ptr())
+
+
+def _f64_c(a):
+    if isinstance(a, np.ndarray):
+        return np.ascontiguousarray(a, dtype=np.float64)
+    return a.contiguous()
+
+
+class Sim:
+    """One boosted-frame PIC simulation on one GPU (a ``pic_ctx``)."""
+
+    def __init__(self, grid, d, dt, gamma_R, bc=((0, 0), (0, 0), (0, 0)), pml=0, order=1,
+                 moving_window=False, window_v=0.0, device=0, stream=None, tuning=None,
+                 torch_allocator=True):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("gbpic needs a CUDA GPU (no CPU fallback)")
+        self.L = lib()
+        self.grid = tuple(int(v) for v in grid)
+        self.d = tuple(float(v) for v in d)
+        self.dt = float(dt)
+        self.gamma_R = float(gamma_R)
+        self.order = int(order)
+        self.device = int(device)
+        torch.cuda.set_device(self.device)
+        self._torch = torch
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        self.stream = stream
+        dev = pic_device()
+        dev.device = self.device
+        dev.stream = C.c_void_p(stream.cuda_stream)
+        self._cb = None
+        if torch_allocator:
+            live = {}
+
+            def _alloc(nbytes, user):
+                try:
+                    p = torch.cuda.caching_allocator_alloc(int(nbytes), self.device, stream)
+                    live[p] = nbytes
+                    return p
+                except Exception:
+                    return None
+
+            def _free(ptr, nbytes, user):
+                if ptr in live:
+                    del live[ptr]
+                    torch.cuda.caching_allocator_delete(ptr)
+
+            self._cb = (ALLOC_FN(_alloc), FREE_FN(_free), live)
+            dev.alloc, dev.free = self._cb[0], self._cb[1]
+        b = pic_boundaries()
+        for dd in range(3):
+            b.face[dd][0], b.face[dd][1] = int(bc[dd][0]), int(bc[dd][1])
+        b.pml_cells = int(pml)
+        b.moving_window = int(bool(moving_window))
+        b.window_v = float(window_v)
+        h = C.c_void_p()
+        darr = (C.c_double * 3)(*self.d)
+        r = self.L.pic_create(C.byref(h), pic_grid(*self.grid), darr, self.dt, self.gamma_R, C.byref(b),
+                              self.order, C.byref(dev))
+        if r != PIC_OK:
+            raise PicError(r, self.L.pic_last_error(None).decode())
+        self.h = h
+        self._dev = dev
+        if tuning is not None:
+            t = pic_tuning()
+            for dd in range(3):
+                t.tile[dd] = int(tuning.get("tile", (8, 8, 8))[dd])
+            t.sort_every = int(tuning.get("sort_every", 8))
+            t.margin = int(tuning.get("margin", 1))
+            self._check(self.L.pic_set_tuning(self.h, C.byref(t)))
+
+    # ------------------------------------------------------------------ plumbing
+    def _check(self, r):
+        if r != PIC_OK:
+            raise PicError(r, self.L.pic_last_error(self.h).decode())
+        return r
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.pic_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def ncell(self):
+        return self.grid[0] * self.grid[1] * self.grid[2]
+
+    # ------------------------------------------------------------------ set-up
+    def load_species(self, q, m, x=None, u=None, w=None, frame=PIC_FRAME_LAB, origin=(0.0, 0.0, 0.0),
+                     capacity=0, frozen=False, match_undulator=False):
+        """x, u: (3, n) FP64 (numpy, or torch on host or device); w: (n,) or None."""
+        n = 0 if x is None else int(x.shape[1])
+        xs = _f64_c(x) if n else None
+        us = _f64_c(u) if n else None
+        ws = _f64_c(w) if (n and w is not None) else None
+        sp = pic_species(float(q), float(m), int(bool(frozen)), int(max(capacity, n, 1)),
+                         (C.c_double * 3)(*[float(v) for v in origin]), int(bool(match_undulator)))
+        sid = C.c_int()
+        self._check(self.L.pic_load_species(self.h, C.byref(sp), n, _ptr(xs), _ptr(us), _ptr(ws),
+                                            int(frame), C.byref(sid)))
+        return sid.value
+
+    def set_external_field(self, K, lambda_u, phase=0.0, z_start=-math.inf, ramp_len=-1.0,
+                           kind=PIC_EXT_PLANAR_UNDULATOR):
+        f = pic_external(int(kind), float(K), float(lambda_u), float(phase), float(z_start), float(ramp_len))
+        self._check(self.L.pic_set_external_field(self.h, C.byref(f)))
+
+    def set_plasma(self, ppc, x_range, z_nodes, density, capacity=0):
+        zn = np.ascontiguousarray(z_nodes, np.float64)
+        dn = np.ascontiguousarray(density, np.float64)
+        p = pic_plasma((C.c_int * 3)(*ppc), (C.c_int * 4)(*x_range), int(zn.size),
+                       zn.ctypes.data_as(C.POINTER(C.c_double)), dn.ctypes.data_as(C.POINTER(C.c_double)),
+                       int(capacity))
+        e, i = C.c_int(), C.c_int()
+        self._check(self.L.pic_set_plasma(self.h, C.byref(p), C.byref(e), C.byref(i)))
+        return e.value, i.value
+
+    # ------------------------------------------------------------------ stepping
+    def step(self, n=1):
+        self._check(self.L.pic_step(self.h, int(n)))
+
+    def sync(self):
+        self._check(self.L.pic_sync(self.h))
+
+    def sort(self):
+        self._check(self.L.pic_sort(self.h))
+
+    # ------------------------------------------------------------------ getters
+    def get_field(self, which, out=None):
+        """Grid component as (nz, ny, nx) float32: numpy by default, or into `out`
+        (a numpy array or a CUDA tensor of ncell floats)."""
+        if out is None:
+            out = np.empty((self.grid[2], self.grid[1], self.grid[0]), np.float32)
+        self._check(self.L.pic_get_fields(self.h, int(which), _ptr(out), self.ncell))
+        return out
+
+    def set_field(self, which, src):
+        if isinstance(src, np.ndarray):
+            src = np.ascontiguousarray(src, np.float32)
+        self._check(self.L.pic_set_fields(self.h, int(which), _ptr(src), self.ncell))
+
+    def get_count(self, sid):
+        n = C.c_int64()
+        self._check(self.L.pic_get_count(self.h, int(sid), C.byref(n)))
+        return n.value
+
+    def get_particles(self, sid):
+        n = self.get_count(sid)
+        cap = max(n, 1)
+        cell = np.zeros((3, cap), np.int32)
+        off = np.zeros((3, cap), np.float32)
+        u = np.zeros((3, cap), np.float32)
+        w = np.zeros(cap, np.float32)
+        ids = np.zeros(cap, np.int64)
+        nn = C.c_int64()
+        self._check(self.L.pic_get_particles(self.h, int(sid), cap, C.byref(nn), _ptr(cell), _ptr(off),
+                                             _ptr(u), _ptr(w), _ptr(ids)))
+        k = nn.value
+        return {"cell": cell[:, :k].T.copy(), "off": off[:, :k].T.copy(), "u": u[:, :k].T.copy(),
+                "w": w[:k].copy(), "id": ids[:k].copy()}
+
+    def get_moments(self, sid, frame=PIC_FRAME_BOOSTED, k_bunch=0.0):
+        m = pic_moments()
+        self._check(self.L.pic_get_moments(self.h, int(sid), int(frame), float(k_bunch), C.byref(m)))
+        return dict(zip(MOMENT_NAMES, list(m.v)))
+
+    def get_time(self):
+        out = (C.c_int64 * 3)()
+        self._check(self.L.pic_get_time(self.h, out))
+        return tuple(int(v) for v in out)
+
+
+def resonant_wavenumber(lambda_u: float, K: float, gamma_B: float) -> float:
+    """Lab FEL resonant wavenumber 2 pi / lambda_l with lambda_l = lambda_u (1 + K^2/2)/(2 gamma^2)
+    (Eq. RadLambda), for the bunching diagnostic."""
+    return 2.0 * math.pi * 2.0 * gamma_B ** 2 / (lambda_u * (1.0 + 0.5 * K * K))
+
+
+def from_workload(w, device=0, stream=None, tuning=None, beam=True, beam_arrays=None):
+    """Create a Sim for a workload of :mod:`paper_2411_04703_gb300.workloads` and load its
+    undulator, plasma and (seeded) beam.  Returns (sim, species ids dict)."""
+    from . import workloads as W
+    t = tuning if tuning is not None else {"tile": w.tile, "sort_every": w.sort_every, "margin": 1}
+    sim = Sim(w.grid, w.d, w.dt, w.gamma_R, bc=w.bc, pml=w.pml, order=w.order,
+              moving_window=w.moving_window, window_v=w.window_v, device=device, stream=stream,
+              tuning=t)
+    ids = {}
+    if w.undulator is not None:
+        un = w.undulator
+        sim.set_external_field(un.K, un.lambda_u, un.phase, un.z_start, un.ramp)
+    if w.plasma is not None:
+        p = w.plasma
+        ids["plasma_e"], ids["plasma_i"] = sim.set_plasma(p.ppc, p.xrange, p.z_nodes, p.n_nodes)
+    if beam and w.beam is not None:
+        if beam_arrays is None:
+            beam_arrays = W.sample_beam(w)
+        x, u, wt = beam_arrays
+        b = w.beam
+        ids["beam"] = sim.load_species(b.q, b.m, x, u, wt, frame=PIC_FRAME_LAB, origin=b.origin,
+                                       match_undulator=bool(w.undulator is not None and w.undulator.match))
+    return sim, ids

@@ -1,0 +1,705 @@
+// C-ABI of the gbpic library: context, device memory, step orchestration and getters.
+// Declared and documented in include/gbpic.h.
+#include "gbpic_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+
+using namespace gbpic;
+
+namespace {
+
+thread_local std::string g_create_err;
+
+int fail(pic_ctx *c, int code, const std::string &m)
+{
+    if (c) {
+        c->msg = m;
+        if (code == PIC_ERR_CUDA || code == PIC_ERR_DEVICE) c->poisoned = true;
+    } else {
+        g_create_err = m;
+    }
+    return code;
+}
+
+int fail_cuda(pic_ctx *c, cudaError_t e, const char *what)
+{
+    return fail(c, PIC_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                                 \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) return fail_cuda(c, e_, #call);   \
+    } while (0)
+
+void *dalloc(pic_ctx *c, size_t bytes)
+{
+    bytes = std::max<size_t>(bytes, 256);
+    void *p = nullptr;
+    if (c->dev.alloc) {
+        p = c->dev.alloc(bytes, c->dev.user);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) c->allocs.emplace_back(p, bytes);
+    return p;
+}
+
+void dfree(pic_ctx *c, void *p)
+{
+    if (!p) return;
+    for (size_t i = 0; i < c->allocs.size(); i++) {
+        if (c->allocs[i].first != p) continue;
+        if (c->dev.free) c->dev.free(p, c->allocs[i].second, c->dev.user);
+        else cudaFree(p);
+        c->allocs.erase(c->allocs.begin() + i);
+        return;
+    }
+}
+
+template <class T>
+int alloc_zero(pic_ctx *c, T **out, size_t count)
+{
+    *out = static_cast<T *>(dalloc(c, count * sizeof(T)));
+    if (!*out) return fail(c, PIC_ERR_ALLOC, "device allocation of " + std::to_string(count * sizeof(T)) + " bytes failed");
+    CK(cudaMemsetAsync(*out, 0, std::max<size_t>(count * sizeof(T), 1), c->stream));
+    return PIC_OK;
+}
+
+int margin_lo(const pic_ctx *c) { return c->order == 1 ? 1 : 2; }
+int margin_hi(const pic_ctx *c) { return c->order == 1 ? 2 : 3; }
+
+// Largest plasma lattice plane whose grid coordinate at step n (after `shifts` window shifts)
+// is below nz - margin_hi: plane m sits at ((m + 1/2)/ppc_z) dz - beta_R t' in the RRF.
+int64_t plane_max(const pic_ctx *c, int64_t n, int64_t shifts)
+{
+    const double thr = (double)(c->n[2] - margin_hi(c));
+    const double xv = (double)c->ppc[2] * (thr + (double)shifts + c->bR * (double)n * c->dt / c->d[2]) - 0.5;
+    return (int64_t)std::ceil(xv) - 1;
+}
+
+int check_ctx(pic_ctx *c)
+{
+    if (!c) return PIC_ERR_ARG;
+    if (c->poisoned) return PIC_ERR_STATE;
+    return PIC_OK;
+}
+
+int make_species(pic_ctx *c, double q, double m, int frozen, int64_t cap, int *sid)
+{
+    if (c->nsp >= kMaxSpecies) return fail(c, PIC_ERR_ARG, "too many species (max 8)");
+    if (cap < 1 || cap >= (int64_t)std::numeric_limits<int>::max() - kChunk)
+        return fail(c, PIC_ERR_ARG, "species capacity out of range");
+    if (!(m > 0)) return fail(c, PIC_ERR_ARG, "species mass must be > 0");
+    Species &s = c->sp[c->nsp];
+    s = Species();
+    s.q = q;
+    s.m = m;
+    s.frozen = frozen ? 1 : 0;
+    s.cap = cap;
+    s.max_items = c->ntiles + cap / kChunk + 2;
+    int r;
+    if ((r = alloc_zero(c, &s.pos, cap)) || (r = alloc_zero(c, &s.mom, cap)) || (r = alloc_zero(c, &s.pos2, cap)) ||
+        (r = alloc_zero(c, &s.mom2, cap)) || (r = alloc_zero(c, &s.id, cap)) || (r = alloc_zero(c, &s.id2, cap)) ||
+        (r = alloc_zero(c, &s.count, 4)) || (r = alloc_zero(c, &s.rank, cap)) ||
+        (r = alloc_zero(c, &s.items, s.max_items)) || (r = alloc_zero(c, &s.cell_start, c->n_keys + 1)) ||
+        (r = alloc_zero(c, &s.chunk_start, c->ntiles + 1)))
+        return r;
+    *sid = c->nsp++;
+    return PIC_OK;
+}
+
+void set_tiles(pic_ctx *c)
+{
+    c->ntiles = 1;
+    for (int d = 0; d < 3; d++) {
+        c->nt[d] = (c->n[d] + c->T[d] - 1) / c->T[d];
+        c->ntiles *= c->nt[d];
+    }
+    c->n_keys = (int64_t)c->ntiles * c->T[0] * c->T[1] * c->T[2];
+}
+
+int alloc_tile_scratch(pic_ctx *c)
+{
+    if (c->hist_tmp) dfree(c, c->hist_tmp);
+    c->hist_tmp_n = scan_scratch_size(std::max<int64_t>(c->n_keys + 1, c->ntiles + 1));
+    return alloc_zero(c, &c->hist_tmp, c->hist_tmp_n);
+}
+
+double shifts_due(const pic_ctx *c, int64_t n) { return std::floor(c->vw * (double)n * c->dt / c->d[2]); }
+
+int inject_due(pic_ctx *c)
+{
+    const int64_t m1 = plane_max(c, c->step, c->shifts);
+    if (m1 <= c->m_last) return PIC_OK;
+    const int64_t per_plane = (int64_t)(c->xr[1] - c->xr[0]) * (c->xr[3] - c->xr[2]) * c->ppc[0] * c->ppc[1];
+    const int64_t add = (m1 - c->m_last) * per_plane;
+    for (int si : {c->sp_e, c->sp_i}) {
+        Species &s = c->sp[si];
+        if (s.bound + add > s.cap) {
+            CK(cudaStreamSynchronize(c->stream));
+            int cnt = 0;
+            CK(cudaMemcpy(&cnt, s.count, sizeof(int), cudaMemcpyDeviceToHost));
+            s.bound = cnt;
+            if (s.bound + add > s.cap)
+                return fail(c, PIC_ERR_CAPACITY, "plasma species capacity exhausted by injection");
+        }
+    }
+    CK(launch_inject(c, c->m_last + 1, m1));
+    c->m_last = m1;
+    return PIC_OK;
+}
+
+ExtDev ext_step(const pic_ctx *c)
+{
+    ExtDev x{};
+    x.type = c->ext_type;
+    if (!x.type) return x;
+    const double kp = c->ku * c->gR;              // k'_u
+    const double tp = (double)c->step * c->dt;
+    const double two_pi = 2.0 * M_PI;
+    x.B0g = (float)(c->gR * c->B0);
+    x.beta_R = (float)c->bR;
+    x.kdz = (float)(kp * c->d[2]);
+    x.theta = (float)std::fmod(kp * ((double)c->shifts * c->d[2] + c->bR * tp) + c->phase0, two_pi);
+    x.phase_tab = c->phase_tab;
+    if (std::isfinite(c->z_start) && c->ramp >= 0.0) {
+        const double a = c->gR * c->d[2];
+        const double b = c->gR * ((double)c->shifts * c->d[2] + c->bR * tp) - c->z_start;
+        if (c->ramp > 0.0) {
+            x.ramp_mode = 1;
+            x.ramp_a = (float)(a / c->ramp);
+            x.ramp_b = (float)(b / c->ramp);
+        } else {
+            x.ramp_mode = 2;
+            x.ramp_a = (float)a;
+            x.ramp_b = (float)b;
+        }
+    }
+    return x;
+}
+
+}  // namespace
+
+namespace gbpic {
+
+GridDev grid_dev(const pic_ctx *c)
+{
+    GridDev g{};
+    for (int d = 0; d < 3; d++) {
+        g.n[d] = c->n[d];
+        g.periodic[d] = c->bc[d][0] == PIC_BC_PERIODIC;
+        g.d[d] = (float)c->d[d];
+        g.dt_over_d[d] = (float)(c->dt / c->d[d]);
+    }
+    g.dt = (float)c->dt;
+    g.mlo = margin_lo(c);
+    g.mhi = margin_hi(c);
+    g.ncell = c->ncell;
+    return g;
+}
+
+TileDev tile_dev(const pic_ctx *c, const Species &s)
+{
+    TileDev t{};
+    for (int d = 0; d < 3; d++) {
+        t.T[d] = c->T[d];
+        t.nt[d] = c->nt[d];
+    }
+    t.tile_cells = c->T[0] * c->T[1] * c->T[2];
+    t.M = c->M;
+    t.hl = margin_lo(c);
+    for (int d = 0; d < 3; d++) t.R[d] = c->T[d] + 2 * c->M + margin_lo(c) + margin_hi(c);
+    t.cell_start = s.cell_start;
+    t.items = s.items;
+    return t;
+}
+
+SpeciesDev species_dev(const pic_ctx *c, const Species &s)
+{
+    SpeciesDev d{};
+    d.pos = s.pos;
+    d.mom = s.mom;
+    d.id = s.id;
+    d.count = s.count;
+    d.h_qm = (float)(0.5 * s.q / s.m * c->dt);
+    const double V = c->d[0] * c->d[1] * c->d[2];
+    for (int k = 0; k < 3; k++) d.cf[k] = (float)(-s.q * c->d[k] / (c->dt * V));
+    d.frozen = s.frozen;
+    d.cap = (int)s.cap;
+    return d;
+}
+
+PmlDev pml_dev(const pic_ctx *c)
+{
+    PmlDev p{};
+    p.on = c->psiE != nullptr;
+    if (!p.on) return p;
+    for (int d = 0; d < 3; d++) {
+        p.bE[d] = c->pml_coef + d * c->nmax;
+        p.bB[d] = c->pml_coef + (3 + d) * c->nmax;
+    }
+    p.psiE = c->psiE;
+    p.psiB = c->psiB;
+    return p;
+}
+
+}  // namespace gbpic
+
+extern "C" {
+
+int pic_create(pic_ctx **out, pic_grid grid, const double dx[3], double dt, double gamma_boost,
+               const pic_boundaries *bc, int shape_order, const pic_device *dev)
+{
+    if (!out) return fail(nullptr, PIC_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!dx || !bc) return fail(nullptr, PIC_ERR_ARG, "dx and bc are required");
+    const int n[3] = {grid.nx, grid.ny, grid.nz};
+    if (n[0] < 1 || n[1] < 1 || n[2] < 1 || n[0] > 1024 || n[1] > 1024 || n[2] > 2048)
+        return fail(nullptr, PIC_ERR_ARG, "grid must be 1..1024 x 1..1024 x 1..2048 cells");
+    if (shape_order != 1 && shape_order != 2) return fail(nullptr, PIC_ERR_ARG, "shape_order must be 1 (CIC) or 2 (TSC)");
+    double inv2 = 0;
+    for (int d = 0; d < 3; d++) {
+        if (!(dx[d] > 0)) return fail(nullptr, PIC_ERR_ARG, "cell sizes must be > 0");
+        inv2 += 1.0 / (dx[d] * dx[d]);
+    }
+    if (!(dt > 0) || !(dt < 1.0 / std::sqrt(inv2))) return fail(nullptr, PIC_ERR_ARG, "dt must satisfy 0 < dt < Courant limit");
+    if (!(gamma_boost >= 1.0)) return fail(nullptr, PIC_ERR_ARG, "gamma_boost must be >= 1");
+    bool any_pml = false;
+    for (int d = 0; d < 3; d++) {
+        for (int f = 0; f < 2; f++) {
+            const int b = bc->face[d][f];
+            if (b != PIC_BC_PERIODIC && b != PIC_BC_PML && b != PIC_BC_OPEN) return fail(nullptr, PIC_ERR_ARG, "unknown boundary");
+            any_pml = any_pml || b == PIC_BC_PML;
+        }
+        if ((bc->face[d][0] == PIC_BC_PERIODIC) != (bc->face[d][1] == PIC_BC_PERIODIC))
+            return fail(nullptr, PIC_ERR_ARG, "a periodic dimension must be periodic on both faces");
+        const int need = shape_order == 1 ? 4 : 6;
+        if (bc->face[d][0] != PIC_BC_PERIODIC && n[d] < need) return fail(nullptr, PIC_ERR_ARG, "non-periodic dim too small");
+    }
+    if (any_pml) {
+        if (bc->pml_cells < 1) return fail(nullptr, PIC_ERR_ARG, "pml_cells must be >= 1 with a PML face");
+        for (int d = 0; d < 3; d++)
+            if ((bc->face[d][0] == PIC_BC_PML || bc->face[d][1] == PIC_BC_PML) && 2 * bc->pml_cells >= n[d])
+                return fail(nullptr, PIC_ERR_ARG, "PML layers thicker than half the grid");
+    }
+    if (bc->moving_window) {
+        if (bc->face[2][0] == PIC_BC_PERIODIC) return fail(nullptr, PIC_ERR_ARG, "moving window needs a non-periodic z");
+        if (!(bc->window_v > 0) || !(bc->window_v * dt < dx[2])) return fail(nullptr, PIC_ERR_ARG, "window_v must give < 1 shift per step");
+    }
+
+    pic_ctx *c = new pic_ctx();
+    if (dev) c->dev = *dev;
+    if (cudaSetDevice(c->dev.device) != cudaSuccess) {
+        delete c;
+        return fail(nullptr, PIC_ERR_CUDA, "cudaSetDevice failed");
+    }
+    if (c->dev.stream) {
+        c->stream = (cudaStream_t)c->dev.stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete c;
+            return fail(nullptr, PIC_ERR_CUDA, "cudaStreamCreate failed");
+        }
+        c->own_stream = true;
+    }
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->dev.device);
+    for (int d = 0; d < 3; d++) {
+        c->n[d] = n[d];
+        c->d[d] = dx[d];
+        c->bc[d][0] = bc->face[d][0];
+        c->bc[d][1] = bc->face[d][1];
+    }
+    c->dt = dt;
+    c->gR = gamma_boost;
+    c->bR = std::sqrt(1.0 - 1.0 / (gamma_boost * gamma_boost));
+    c->pml = any_pml ? bc->pml_cells : 0;
+    c->moving = bc->moving_window ? 1 : 0;
+    c->vw = bc->window_v;
+    c->order = shape_order;
+    c->ncell = (int64_t)n[0] * n[1] * n[2];
+    c->nmax = std::max({n[0], n[1], n[2]});
+    set_tiles(c);
+
+    auto bail = [&](int r) {
+        std::string m = c->msg;
+        pic_destroy(c);
+        return fail(nullptr, r, m);
+    };
+    int r;
+    if ((r = alloc_zero(c, &c->E, 3 * c->ncell)) || (r = alloc_zero(c, &c->B, 3 * c->ncell)) ||
+        (r = alloc_zero(c, &c->J, 3 * c->ncell)) || (r = alloc_zero(c, &c->err, 4)) ||
+        (r = alloc_zero(c, &c->work, kMaxSpecies)) || (r = alloc_zero(c, &c->red, 512 * 16 + 1024)) ||
+        (r = alloc_zero(c, &c->shift_tab, 24)) || (r = alloc_tile_scratch(c)))
+        return bail(r);
+    if (any_pml) {
+        if ((r = alloc_zero(c, &c->psiE, 6 * c->ncell)) || (r = alloc_zero(c, &c->psiB, 6 * c->ncell)) ||
+            (r = alloc_zero(c, &c->pml_coef, 6 * c->nmax)))
+            return bail(r);
+        // CPML conductivity: cubic grading over pml_cells, normal reflection 1e-8
+        std::vector<float> coef(6 * c->nmax, 1.f);
+        const double L = (double)c->pml;
+        for (int d = 0; d < 3; d++) {
+            const double smax = 4.0 * (-std::log(1e-8)) / (2.0 * L * c->d[d]);
+            for (int i = 0; i < n[d]; i++) {
+                for (int half = 0; half < 2; half++) {
+                    const double pos = i + 0.5 * half;
+                    double depth = 0.0;
+                    if (c->bc[d][0] == PIC_BC_PML && pos < L) depth = L - pos;
+                    if (c->bc[d][1] == PIC_BC_PML && pos > (n[d] - 1) - L) depth = std::max(depth, pos - ((n[d] - 1) - L));
+                    const double rr = depth / L;
+                    const double sig = depth > 0 ? smax * rr * rr * rr : 0.0;
+                    if (half == 0) coef[d * c->nmax + i] = (float)std::exp(-sig * c->dt);
+                    else coef[(3 + d) * c->nmax + i] = (float)std::exp(-sig * 0.5 * c->dt);
+                }
+            }
+        }
+        if (cudaMemcpy(c->pml_coef, coef.data(), coef.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+            return bail(fail_cuda(c, cudaGetLastError(), "copy PML coefficients"));
+    }
+    {
+        std::vector<float *> tab;
+        for (int q = 0; q < 3; q++) {
+            tab.push_back(c->E + q * c->ncell);
+            tab.push_back(c->B + q * c->ncell);
+            tab.push_back(c->J + q * c->ncell);
+        }
+        if (c->psiE)
+            for (int q = 0; q < 6; q++) {
+                tab.push_back(c->psiE + q * c->ncell);
+                tab.push_back(c->psiB + q * c->ncell);
+            }
+        c->shift_n = (int)tab.size();
+        if (cudaMemcpy(c->shift_tab, tab.data(), tab.size() * sizeof(float *), cudaMemcpyHostToDevice) != cudaSuccess)
+            return bail(fail_cuda(c, cudaGetLastError(), "copy shift table"));
+    }
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return bail(fail_cuda(c, cudaGetLastError(), "create sync"));
+    *out = c;
+    return PIC_OK;
+}
+
+int pic_set_tuning(pic_ctx *c, const pic_tuning *t)
+{
+    int r = check_ctx(c);
+    if (r) return r;
+    if (!t) return fail(c, PIC_ERR_ARG, "tuning is NULL");
+    if (c->nsp > 0) return fail(c, PIC_ERR_STATE, "set tuning before creating species");
+    for (int d = 0; d < 3; d++)
+        if (t->tile[d] < 2 || t->tile[d] > 16) return fail(c, PIC_ERR_ARG, "tile sizes must be 2..16");
+    if (t->sort_every < 1) return fail(c, PIC_ERR_ARG, "sort_every must be >= 1");
+    if (t->margin < 0 || t->margin > 2) return fail(c, PIC_ERR_ARG, "margin must be 0..2");
+    int R3 = 1;
+    for (int d = 0; d < 3; d++) R3 *= t->tile[d] + 2 * t->margin + margin_lo(c) + margin_hi(c);
+    if ((size_t)R3 * 9 * sizeof(float) > 200 * 1024) return fail(c, PIC_ERR_ARG, "tile region exceeds shared memory");
+    for (int d = 0; d < 3; d++) c->T[d] = t->tile[d];
+    c->sort_every = t->sort_every;
+    c->M = t->margin;
+    set_tiles(c);
+    return alloc_tile_scratch(c);
+}
+
+int pic_load_species(pic_ctx *c, const pic_species *sp, int64_t n, const double *x, const double *u,
+                     const double *w, int frame, int *species_id)
+{
+    int r = check_ctx(c);
+    if (r) return r;
+    if (!sp || !species_id || n < 0) return fail(c, PIC_ERR_ARG, "invalid species arguments");
+    if (n > 0 && (!x || !u)) return fail(c, PIC_ERR_ARG, "x and u are required when n > 0");
+    if (frame != PIC_FRAME_LAB && frame != PIC_FRAME_BOOSTED) return fail(c, PIC_ERR_ARG, "unknown frame");
+    const int64_t cap = std::max<int64_t>(sp->capacity, std::max<int64_t>(n, 1));
+    int sid;
+    if ((r = make_species(c, sp->q, sp->m, sp->frozen, cap, &sid))) return r;
+    Species &s = c->sp[sid];
+    double *dx = nullptr, *du = nullptr, *dw = nullptr;
+    if (n > 0) {
+        dx = static_cast<double *>(dalloc(c, sizeof(double) * 3 * n));
+        du = static_cast<double *>(dalloc(c, sizeof(double) * 3 * n));
+        if (w) dw = static_cast<double *>(dalloc(c, sizeof(double) * n));
+        if (!dx || !du || (w && !dw)) return fail(c, PIC_ERR_ALLOC, "staging allocation failed");
+        CK(cudaMemcpyAsync(dx, x, sizeof(double) * 3 * n, cudaMemcpyDefault, c->stream));
+        CK(cudaMemcpyAsync(du, u, sizeof(double) * 3 * n, cudaMemcpyDefault, c->stream));
+        if (w) CK(cudaMemcpyAsync(dw, w, sizeof(double) * n, cudaMemcpyDefault, c->stream));
+    }
+    CK(launch_load(c, sid, n, dx, du, dw, frame, sp->origin, sp->match_undulator, s.next_id));
+    s.next_id += n;
+    s.bound += n;
+    if (n > 0) {
+        CK(cudaStreamSynchronize(c->stream));
+        dfree(c, dx);
+        dfree(c, du);
+        dfree(c, dw);
+    }
+    *species_id = sid;
+    return PIC_OK;
+}
+
+int pic_set_external_field(pic_ctx *c, const pic_external *f)
+{
+    int r = check_ctx(c);
+    if (r) return r;
+    if (!f) return fail(c, PIC_ERR_ARG, "external field is NULL");
+    if (f->type == PIC_EXT_NONE) {
+        c->ext_type = 0;
+        return PIC_OK;
+    }
+    if (f->type != PIC_EXT_PLANAR_UNDULATOR) return fail(c, PIC_ERR_ARG, "unknown external field type");
+    if (!(f->lambda_u > 0)) return fail(c, PIC_ERR_ARG, "lambda_u must be > 0");
+    c->ext_type = f->type;
+    c->K = f->K;
+    c->lam_u = f->lambda_u;
+    c->ku = 2.0 * M_PI / f->lambda_u;
+    c->B0 = f->K * c->ku;
+    c->phase0 = f->phase;
+    c->z_start = f->z_start;
+    c->ramp = f->ramp_len;
+    if (!c->phase_tab && (r = alloc_zero(c, &c->phase_tab, c->n[2]))) return r;
+    std::vector<float> tab(c->n[2]);
+    const double kdz = c->ku * c->gR * c->d[2];
+    for (int k = 0; k < c->n[2]; k++) tab[k] = (float)std::fmod(kdz * k, 2.0 * M_PI);
+    CK(cudaMemcpyAsync(c->phase_tab, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return PIC_OK;
+}
+
+int pic_set_plasma(pic_ctx *c, const pic_plasma *p, int *electron_id, int *ion_id)
+{
+    int r = check_ctx(c);
+    if (r) return r;
+    if (!p || !electron_id || !ion_id) return fail(c, PIC_ERR_ARG, "plasma arguments are NULL");
+    if (c->plasma) return fail(c, PIC_ERR_STATE, "plasma already set");
+    for (int d = 0; d < 3; d++)
+        if (p->ppc[d] < 1 || p->ppc[d] > 16) return fail(c, PIC_ERR_ARG, "ppc must be 1..16 per dim");
+    if (p->x_range[0] < 0 || p->x_range[1] > c->n[0] || p->x_range[0] >= p->x_range[1] || p->x_range[2] < 0 ||
+        p->x_range[3] > c->n[1] || p->x_range[2] >= p->x_range[3])
+        return fail(c, PIC_ERR_ARG, "x_range outside the grid");
+    if (p->n_nodes < 1 || !p->z_nodes || !p->density) return fail(c, PIC_ERR_ARG, "density profile required");
+    for (int d = 0; d < 3; d++) c->ppc[d] = p->ppc[d];
+    for (int k = 0; k < 4; k++) c->xr[k] = p->x_range[k];
+    const int64_t per_plane = (int64_t)(c->xr[1] - c->xr[0]) * (c->xr[3] - c->xr[2]) * c->ppc[0] * c->ppc[1];
+    int64_t cap = p->capacity;
+    if (cap <= 0) {
+        const double planes_window = (double)c->n[2] * c->ppc[2] + 2;
+        const double rate = c->ppc[2] * (c->bR + c->vw) * c->dt / c->d[2] + 1e-9;
+        cap = (int64_t)(per_plane * (planes_window + rate * (c->sort_every + 2) * 2 + 8));
+    }
+    int se, si;
+    if ((r = make_species(c, -1.0, 1.0, 0, cap, &se))) return r;
+    if ((r = make_species(c, 1.0, 1836.15267343, 1, cap, &si))) return r;
+    c->nprof = p->n_nodes;
+    c->prof_z.assign(p->z_nodes, p->z_nodes + p->n_nodes);
+    c->prof_n.assign(p->density, p->density + p->n_nodes);
+    if ((r = alloc_zero(c, &c->prof, 2 * (size_t)p->n_nodes))) return r;
+    std::vector<double> pr(2 * p->n_nodes);
+    for (int i = 0; i < p->n_nodes; i++) {
+        pr[i] = p->z_nodes[i];
+        pr[p->n_nodes + i] = p->density[i];
+    }
+    CK(cudaMemcpyAsync(c->prof, pr.data(), pr.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    c->plasma = 1;
+    c->sp_e = se;
+    c->sp_i = si;
+    const double lo = (double)margin_lo(c) + (double)c->shifts + c->bR * (double)c->step * c->dt / c->d[2];
+    const int64_t m0 = (int64_t)std::ceil((double)c->ppc[2] * lo - 0.5);
+    const int64_t m1 = plane_max(c, c->step, c->shifts);
+    if ((m1 - m0 + 1) * per_plane > cap) return fail(c, PIC_ERR_CAPACITY, "plasma capacity below the window fill");
+    CK(launch_inject(c, m0, m1));
+    c->m_last = m1;
+    CK(cudaStreamSynchronize(c->stream));
+    *electron_id = se;
+    *ion_id = si;
+    return PIC_OK;
+}
+
+int pic_step(pic_ctx *c, int64_t nsteps)
+{
+    int r = check_ctx(c);
+    if (r) return r;
+    if (nsteps < 0) return fail(c, PIC_ERR_ARG, "negative step count");
+    for (int64_t it = 0; it < nsteps; it++) {
+        if (c->step % c->sort_every == 0)
+            for (int si = 0; si < c->nsp; si++) CK(launch_sort(c, si));
+        CK(cudaMemsetAsync(c->J, 0, sizeof(float) * 3 * c->ncell, c->stream));
+        CK(cudaMemsetAsync(c->work, 0, sizeof(int) * kMaxSpecies, c->stream));
+        const ExtDev ext = ext_step(c);
+        for (int si = 0; si < c->nsp; si++) CK(launch_push(c, si, ext));
+        CK(launch_fdtd_b(c, (float)(0.5 * c->dt)));
+        CK(launch_fdtd_e(c));
+        CK(launch_fdtd_b(c, (float)(0.5 * c->dt)));
+        c->step++;
+        if (c->moving) {
+            const int64_t due = (int64_t)shifts_due(c, c->step);
+            while (c->shifts < due) {
+                CK(launch_shift_fields(c));
+                for (int si = 0; si < c->nsp; si++) CK(launch_shift_particles(c, si));
+                c->shifts++;
+            }
+        }
+        if (c->plasma && (r = inject_due(c))) return r;
+    }
+    return PIC_OK;
+}
+
+int pic_sync(pic_ctx *c)
+{
+    if (!c) return PIC_ERR_ARG;
+    if (c->poisoned) return PIC_ERR_STATE;
+    CK(cudaStreamSynchronize(c->stream));
+    int e = 0;
+    CK(cudaMemcpy(&e, c->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) {
+        std::string m = "device error word 0x" + std::to_string(e) + ":";
+        if (e & ERR_INDEX) m += " stencil node outside a non-periodic grid;";
+        if (e & ERR_CAPACITY) m += " species capacity exceeded;";
+        if (e & ERR_MOVE) m += " particle moved one cell or more in a step;";
+        if (e & ERR_NAN) m += " non-finite momentum;";
+        return fail(c, PIC_ERR_DEVICE, m);
+    }
+    return PIC_OK;
+}
+
+int pic_sort(pic_ctx *c)
+{
+    int r = check_ctx(c);
+    if (r) return r;
+    for (int si = 0; si < c->nsp; si++) CK(launch_sort(c, si));
+    return PIC_OK;
+}
+
+int pic_get_fields(pic_ctx *c, int which, float *dst, size_t n)
+{
+    int r = check_ctx(c);
+    if (r) return r;
+    if (!dst || n < (size_t)c->ncell) return fail(c, PIC_ERR_ARG, "destination smaller than the grid");
+    const float *src = nullptr;
+    if (which >= PIC_EX && which <= PIC_EZ) src = c->E + (which - PIC_EX) * c->ncell;
+    else if (which >= PIC_BX && which <= PIC_BZ) src = c->B + (which - PIC_BX) * c->ncell;
+    else if (which >= PIC_JX && which <= PIC_JZ) src = c->J + (which - PIC_JX) * c->ncell;
+    else if (which == PIC_RHO) {
+        if (!c->rho && (r = alloc_zero(c, &c->rho, c->ncell))) return r;
+        CK(launch_rho(c, c->rho));
+        src = c->rho;
+    } else {
+        return fail(c, PIC_ERR_ARG, "unknown field");
+    }
+    CK(cudaMemcpyAsync(dst, src, sizeof(float) * c->ncell, cudaMemcpyDefault, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return PIC_OK;
+}
+
+int pic_set_fields(pic_ctx *c, int which, const float *src, size_t n)
+{
+    int r = check_ctx(c);
+    if (r) return r;
+    if (!src || n < (size_t)c->ncell) return fail(c, PIC_ERR_ARG, "source smaller than the grid");
+    float *dst = nullptr;
+    if (which >= PIC_EX && which <= PIC_EZ) dst = c->E + (which - PIC_EX) * c->ncell;
+    else if (which >= PIC_BX && which <= PIC_BZ) dst = c->B + (which - PIC_BX) * c->ncell;
+    else if (which >= PIC_JX && which <= PIC_JZ) dst = c->J + (which - PIC_JX) * c->ncell;
+    else return fail(c, PIC_ERR_ARG, "unknown field");
+    CK(cudaMemcpyAsync(dst, src, sizeof(float) * c->ncell, cudaMemcpyDefault, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return PIC_OK;
+}
+
+int pic_get_particles(pic_ctx *c, int sid, int64_t cap, int64_t *n_out, int32_t *cell, float *off, float *u,
+                      float *w, int64_t *id)
+{
+    int r = check_ctx(c);
+    if (r) return r;
+    if (sid < 0 || sid >= c->nsp || !n_out) return fail(c, PIC_ERR_ARG, "bad species id");
+    Species &s = c->sp[sid];
+    CK(cudaStreamSynchronize(c->stream));
+    int cnt = 0;
+    CK(cudaMemcpy(&cnt, s.count, sizeof(int), cudaMemcpyDeviceToHost));
+    std::vector<float4> P(cnt), Mo(cnt);
+    std::vector<int> I(cnt);
+    if (cnt > 0) {
+        CK(cudaMemcpy(P.data(), s.pos, sizeof(float4) * cnt, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(Mo.data(), s.mom, sizeof(float4) * cnt, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(I.data(), s.id, sizeof(int) * cnt, cudaMemcpyDeviceToHost));
+    }
+    int64_t live = 0;
+    for (int p = 0; p < cnt; p++) {
+        int cb;
+        std::memcpy(&cb, &P[p].w, sizeof(int));
+        if (cb >= 0) live++;
+    }
+    *n_out = live;
+    if (live > cap) return fail(c, PIC_ERR_CAPACITY, "output capacity below the live particle count");
+    int64_t k = 0;
+    for (int p = 0; p < cnt; p++) {
+        int cb;
+        std::memcpy(&cb, &P[p].w, sizeof(int));
+        if (cb < 0) continue;
+        if (cell) {
+            cell[k] = cell_i(cb);
+            cell[cap + k] = cell_j(cb);
+            cell[2 * cap + k] = cell_k(cb);
+        }
+        if (off) {
+            off[k] = P[p].x;
+            off[cap + k] = P[p].y;
+            off[2 * cap + k] = P[p].z;
+        }
+        if (u) {
+            u[k] = Mo[p].x;
+            u[cap + k] = Mo[p].y;
+            u[2 * cap + k] = Mo[p].z;
+        }
+        if (w) w[k] = Mo[p].w;
+        if (id) id[k] = I[p];
+        k++;
+    }
+    return PIC_OK;
+}
+
+int pic_get_moments(pic_ctx *c, int sid, int frame, double k_bunch, pic_moments *out)
+{
+    int r = check_ctx(c);
+    if (r) return r;
+    if (sid < 0 || sid >= c->nsp || !out) return fail(c, PIC_ERR_ARG, "bad species id");
+    if (frame != PIC_FRAME_LAB && frame != PIC_FRAME_BOOSTED) return fail(c, PIC_ERR_ARG, "unknown frame");
+    double v[20];
+    CK(launch_moments(c, sid, frame == PIC_FRAME_LAB ? PIC_FRAME_LAB : PIC_FRAME_BOOSTED, k_bunch, v));
+    CK(launch_field_energy(c, &v[19]));
+    static_assert(sizeof(pic_moments) == 20 * sizeof(double), "pic_moments layout");
+    std::memcpy(out, v, sizeof(v));
+    return PIC_OK;
+}
+
+int pic_get_time(pic_ctx *c, int64_t out[3])
+{
+    if (!c || !out) return PIC_ERR_ARG;
+    out[0] = c->step;
+    out[1] = c->shifts;
+    out[2] = c->m_last;
+    return PIC_OK;
+}
+
+int pic_get_count(pic_ctx *c, int sid, int64_t *n_out)
+{
+    return pic_get_particles(c, sid, std::numeric_limits<int64_t>::max(), n_out, nullptr, nullptr, nullptr,
+                             nullptr, nullptr);
+}
+
+int pic_destroy(pic_ctx *c)
+{
+    if (!c) return PIC_OK;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    while (!c->allocs.empty()) dfree(c, c->allocs.back().first);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return PIC_OK;
+}
+
+const char *pic_last_error(const pic_ctx *c)
+{
+    return c ? c->msg.c_str() : g_create_err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,187 @@
+// Internal declarations of the gbpic CUDA library (sm_103a).  Device-side parameter blocks,
+// the context structure and the kernel launchers used by the C-ABI in api.cu.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/gbpic.h"
+
+namespace gbpic {
+
+constexpr int kMaxSpecies = 8;
+constexpr int kChunk = 2048;         // particles per work item of the particle kernel
+constexpr int kPushThreads = 256;
+
+// Error bits of the device error word.
+enum : int {
+    ERR_INDEX = 1,      // a slow-path stencil node fell outside a non-periodic grid
+    ERR_CAPACITY = 2,   // an append (load / injection) exceeded the species capacity
+    ERR_MOVE = 4,       // a particle moved one cell or more in one step (Courant violated)
+    ERR_NAN = 8,        // non-finite momentum produced by the push
+};
+
+// Cell index packed into 32 bits: i | j << 10 | k << 20; -1 marks a dummy particle.
+__host__ __device__ __forceinline__ int pack_cell(int i, int j, int k) { return i | (j << 10) | (k << 20); }
+__host__ __device__ __forceinline__ int cell_i(int c) { return c & 1023; }
+__host__ __device__ __forceinline__ int cell_j(int c) { return (c >> 10) & 1023; }
+__host__ __device__ __forceinline__ int cell_k(int c) { return c >> 20; }
+
+struct GridDev {
+    int n[3];
+    int periodic[3];
+    float d[3];
+    float dt;
+    float dt_over_d[3];
+    int mlo, mhi;        // particle margins of the non-periodic dims
+    long long ncell;
+};
+
+struct PmlDev {
+    int on;
+    const float *bE[3];   // exp(-sigma(node) dt) per dim, size n[d]
+    const float *bB[3];   // exp(-sigma(node + 1/2) dt/2) per dim, size n[d]
+    float *psiE;          // [6][ncell]: (Ex,y) (Ex,z) (Ey,z) (Ey,x) (Ez,x) (Ez,y)
+    float *psiB;          // [6][ncell]: same order for B
+};
+
+struct ExtDev {
+    int type;             // PIC_EXT_*
+    float B0g;            // gamma_R B0 (RRF amplitude of B'_y)
+    float beta_R;
+    float kdz;            // k'_u dz: phase advance per cell along z
+    float theta;          // phase of the step: k'_u (shifts dz + beta_R t') + phase, mod 2 pi
+    const float *phase_tab;  // (k'_u dz k) mod 2 pi for k = 0 .. nz-1
+    int ramp_mode;        // 0: f = 1; 1: linear ramp; 2: step
+    float ramp_a, ramp_b; // ramp argument r = ramp_a (k + off_z) + ramp_b
+};
+
+struct SpeciesDev {
+    float4 *pos;          // (off_x, off_y, off_z, cell bits)
+    float4 *mom;          // (u_x, u_y, u_z, w)
+    int *id;
+    int *count;           // [0] total slots in use, [1] sorted prefix, [2] tile work items
+    float h_qm;           // 0.5 (q/m) dt
+    float cf[3];          // -q d_c / (dt V): current of unit weight per unit W
+    int frozen;
+    int cap;
+};
+
+struct TileDev {
+    int T[3];             // tile size (cells)
+    int nt[3];            // tiles per dim
+    int tile_cells;
+    int M;                // allowed drift outside the tile between sorts (cells)
+    int hl;               // stencil reach below the particle cell (1 CIC, 2 TSC)
+    int R[3];             // shared-memory region size per dim
+    const int *cell_start;   // [n_keys + 1]: first sorted slot of each key
+    const int2 *items;       // (tile, chunk) work items
+};
+
+struct FieldsDev {
+    float *E, *B, *J;     // [3][ncell] each
+};
+
+// ------------------------------------------------------------------------- host context
+struct Species {
+    double q = -1, m = 1;
+    int frozen = 0;
+    int64_t cap = 0;
+    float4 *pos = nullptr, *mom = nullptr, *pos2 = nullptr, *mom2 = nullptr;
+    int *id = nullptr, *id2 = nullptr;
+    int *count = nullptr;     // device [4]
+    int *rank = nullptr;      // device [cap] sort scratch
+    int2 *items = nullptr;    // device work items
+    int64_t max_items = 0;
+    int *cell_start = nullptr;  // device [n_keys + 1]
+    int *chunk_start = nullptr; // device [ntiles + 1]
+    int64_t bound = 0;        // host upper bound of count[0]
+    int64_t next_id = 0;
+};
+
+}  // namespace gbpic
+
+struct pic_ctx {
+    pic_device dev{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int num_sms = 0;
+    int n[3] = {0, 0, 0};
+    double d[3] = {0, 0, 0};
+    double dt = 0, gR = 1, bR = 0;
+    int bc[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+    int pml = 0;
+    int moving = 0;
+    double vw = 0;
+    int order = 1;
+    int64_t ncell = 0;
+    float *E = nullptr, *B = nullptr, *J = nullptr, *rho = nullptr;
+    float *psiE = nullptr, *psiB = nullptr;
+    float *pml_coef = nullptr;   // bE[3][nmax], bB[3][nmax]
+    float **shift_tab = nullptr; // device table of the arrays the moving window shifts
+    int shift_n = 0;
+    int nmax = 0;
+    // external field
+    int ext_type = 0;
+    double K = 0, lam_u = 0, ku = 0, B0 = 0, phase0 = 0, z_start = 0, ramp = -1;
+    float *phase_tab = nullptr;
+    // plasma
+    int plasma = 0, sp_e = -1, sp_i = -1, ppc[3] = {1, 1, 1}, xr[4] = {0, 0, 0, 0};
+    double *prof = nullptr;   // device [2][nprof]
+    int nprof = 0;
+    std::vector<double> prof_z, prof_n;
+    // tiles
+    int T[3] = {8, 8, 8};
+    int sort_every = 8;
+    int M = 1;
+    int nt[3] = {1, 1, 1};
+    int ntiles = 1;
+    int64_t n_keys = 1;
+    int *hist_tmp = nullptr;      // scan scratch
+    int64_t hist_tmp_n = 0;
+    // time
+    int64_t step = 0, shifts = 0, m_last = -1;
+    // bookkeeping
+    int *err = nullptr;           // device error word
+    int *work = nullptr;          // device work counters [kMaxSpecies]
+    double *red = nullptr;        // reduction partials
+    double *red_out = nullptr;
+    int nsp = 0;
+    gbpic::Species sp[gbpic::kMaxSpecies];
+    std::string msg;
+    bool poisoned = false;
+    std::vector<std::pair<void *, size_t>> allocs;   // every device allocation of the context
+};
+
+namespace gbpic {
+
+GridDev grid_dev(const pic_ctx *c);
+TileDev tile_dev(const pic_ctx *c, const Species &s);
+SpeciesDev species_dev(const pic_ctx *c, const Species &s);
+ExtDev ext_dev(const pic_ctx *c);
+PmlDev pml_dev(const pic_ctx *c);
+
+// k_push.cu
+cudaError_t launch_push(pic_ctx *c, int si, const ExtDev &ext);
+cudaError_t launch_rho(pic_ctx *c, float *rho);
+// k_fields.cu
+cudaError_t launch_fdtd_b(pic_ctx *c, float dtt);
+cudaError_t launch_fdtd_e(pic_ctx *c);
+cudaError_t launch_shift_fields(pic_ctx *c);
+cudaError_t launch_field_energy(pic_ctx *c, double *out_host);
+// k_sort.cu
+cudaError_t launch_sort(pic_ctx *c, int si);
+cudaError_t exclusive_scan(pic_ctx *c, int *data, int64_t n);
+int64_t scan_scratch_size(int64_t n);
+// k_init.cu
+cudaError_t launch_load(pic_ctx *c, int si, int64_t n, const double *dx, const double *du,
+                        const double *dw, int frame, const double origin[3], int match,
+                        int64_t id_base);
+cudaError_t launch_inject(pic_ctx *c, int64_t m0, int64_t m1);
+cudaError_t launch_shift_particles(pic_ctx *c, int si);
+cudaError_t launch_moments(pic_ctx *c, int si, int frame, double k, double *out20);
+
+}  // namespace gbpic

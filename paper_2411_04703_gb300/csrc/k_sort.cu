@@ -1,0 +1,174 @@
+// Counting sort of a species by tile-major cell key (locality for the particle kernel) and
+// construction of its (tile, chunk) work items.  Key of a cell: tiles of Tx*Ty*Tz cells in
+// x-fastest order, cells inside a tile x-fastest; dummy particles get the extra key n_keys
+// and are dropped (compaction).  Histogram with global atomics -> exclusive scan ->
+// scatter.  The order among particles of one cell is not fixed (atomic ranks).
+#include "gbpic_internal.cuh"
+
+namespace gbpic {
+namespace {
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanSeg = 2 * kScanThreads;
+
+__device__ __forceinline__ int tile_key(int cell, const TileDev &t)
+{
+    const int i = cell_i(cell), j = cell_j(cell), k = cell_k(cell);
+    const int tile = ((k / t.T[2]) * t.nt[1] + j / t.T[1]) * t.nt[0] + i / t.T[0];
+    const int local = ((k % t.T[2]) * t.T[1] + j % t.T[1]) * t.T[0] + i % t.T[0];
+    return tile * t.tile_cells + local;
+}
+
+__global__ void k_sort_count(SpeciesDev sp, TileDev t, int n_keys, int *hist, int *rank)
+{
+    const int n = sp.count[0];
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        const int cell = __float_as_int(sp.pos[p].w);
+        const int key = cell < 0 ? n_keys : tile_key(cell, t);
+        rank[p] = atomicAdd(hist + key, 1);
+    }
+}
+
+__global__ void k_sort_scatter(SpeciesDev sp, TileDev t, int n_keys, const int *start, const int *rank,
+                               float4 *pos2, float4 *mom2, int *id2)
+{
+    const int n = sp.count[0];
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        const float4 P = sp.pos[p];
+        const int cell = __float_as_int(P.w);
+        if (cell < 0) continue;
+        const int dst = start[tile_key(cell, t)] + rank[p];
+        pos2[dst] = P;
+        mom2[dst] = sp.mom[p];
+        id2[dst] = sp.id[p];
+    }
+}
+
+__global__ void k_tile_chunks(const int *start, int tile_cells, int ntiles, int *chunk_count)
+{
+    const int tl = blockIdx.x * blockDim.x + threadIdx.x;
+    if (tl > ntiles) return;
+    if (tl == ntiles) { chunk_count[tl] = 0; return; }
+    const int cnt = start[(tl + 1) * tile_cells] - start[tl * tile_cells];
+    chunk_count[tl] = (cnt + kChunk - 1) / kChunk;
+}
+
+__global__ void k_fill_items(const int *chunk_start, int ntiles, int2 *items, int *count, const int *start,
+                             int n_keys)
+{
+    const int tl = blockIdx.x * blockDim.x + threadIdx.x;
+    if (tl < ntiles) {
+        const int b = chunk_start[tl], e = chunk_start[tl + 1];
+        for (int c = b; c < e; c++) items[c] = make_int2(tl, c - b);
+    }
+    if (tl == 0) {
+        count[0] = start[n_keys];
+        count[1] = start[n_keys];
+        count[2] = chunk_start[ntiles];
+    }
+}
+
+// Block-wide exclusive scan of kScanSeg ints per block; the block total goes to sums.
+__global__ void __launch_bounds__(kScanThreads) k_scan_blocks(int *data, long long n, int *sums)
+{
+    __shared__ int warp_tot[32];
+    const long long i0 = (long long)blockIdx.x * kScanSeg + 2 * threadIdx.x;
+    const int a = i0 < n ? data[i0] : 0;
+    const int b = i0 + 1 < n ? data[i0 + 1] : 0;
+    int v = a + b;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+    }
+    if (lane == 31) warp_tot[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        int w = warp_tot[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        warp_tot[lane] = w;   // inclusive over warps
+    }
+    __syncthreads();
+    const int incl = v + (wid > 0 ? warp_tot[wid - 1] : 0);
+    const int excl = incl - (a + b);
+    if (i0 < n) data[i0] = excl;
+    if (i0 + 1 < n) data[i0 + 1] = excl + a;
+    if (threadIdx.x == kScanThreads - 1 && sums) sums[blockIdx.x] = incl;
+}
+
+__global__ void k_scan_add(int *data, long long n, const int *offs)
+{
+    const int add = offs[blockIdx.x];
+    const long long i0 = (long long)blockIdx.x * kScanSeg + threadIdx.x;
+    if (i0 < n) data[i0] += add;
+    if (i0 + kScanThreads < n) data[i0 + kScanThreads] += add;
+}
+
+cudaError_t scan_rec(cudaStream_t st, int *data, long long n, int *scratch)
+{
+    const long long nb = (n + kScanSeg - 1) / kScanSeg;
+    if (nb <= 1) {
+        k_scan_blocks<<<1, kScanThreads, 0, st>>>(data, n, nullptr);
+        return cudaGetLastError();
+    }
+    k_scan_blocks<<<(unsigned)nb, kScanThreads, 0, st>>>(data, n, scratch);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = scan_rec(st, scratch, nb, scratch + nb);
+    if (e != cudaSuccess) return e;
+    k_scan_add<<<(unsigned)nb, kScanThreads, 0, st>>>(data, n, scratch);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// Scratch ints needed by exclusive_scan for n elements.
+int64_t scan_scratch_size(int64_t n)
+{
+    int64_t tot = 0;
+    while (n > kScanSeg) {
+        n = (n + kScanSeg - 1) / kScanSeg;
+        tot += n;
+    }
+    return tot + 16;
+}
+
+cudaError_t exclusive_scan(pic_ctx *c, int *data, int64_t n)
+{
+    if (scan_scratch_size(n) > c->hist_tmp_n) return cudaErrorInvalidValue;
+    return scan_rec(c->stream, data, n, c->hist_tmp);
+}
+
+cudaError_t launch_sort(pic_ctx *c, int si)
+{
+    Species &s = c->sp[si];
+    TileDev t = tile_dev(c, s);
+    SpeciesDev sd = species_dev(c, s);
+    const int n_keys = (int)c->n_keys;
+    cudaError_t e = cudaMemsetAsync(s.cell_start, 0, sizeof(int) * (c->n_keys + 1), c->stream);
+    if (e != cudaSuccess) return e;
+    const int grid = c->num_sms * 8;
+    k_sort_count<<<grid, 256, 0, c->stream>>>(sd, t, n_keys, s.cell_start, s.rank);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = exclusive_scan(c, s.cell_start, c->n_keys + 1)) != cudaSuccess) return e;
+    k_sort_scatter<<<grid, 256, 0, c->stream>>>(sd, t, n_keys, s.cell_start, s.rank, s.pos2, s.mom2, s.id2);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_tile_chunks<<<(c->ntiles + 1 + 255) / 256, 256, 0, c->stream>>>(s.cell_start, t.tile_cells, c->ntiles,
+                                                                       s.chunk_start);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = exclusive_scan(c, s.chunk_start, c->ntiles + 1)) != cudaSuccess) return e;
+    k_fill_items<<<(c->ntiles + 255) / 256, 256, 0, c->stream>>>(s.chunk_start, c->ntiles, s.items, s.count,
+                                                                  s.cell_start, n_keys);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    std::swap(s.pos, s.pos2);
+    std::swap(s.mom, s.mom2);
+    std::swap(s.id, s.id2);
+    return cudaSuccess;
+}
+
+}  // namespace gbpic

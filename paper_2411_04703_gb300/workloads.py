@@ -201,10 +201,12 @@ def mini_vacuum(order=1, seed=11):
 
 
 def mini_plasma(seed=12, grid=(28, 26, 52), n_beam=4000, steps=20):
-    w = plasma_buncher(grid=grid, n_beam=n_beam, steps=steps, seed=seed, pml=4,
-                       name=f"mini plasma buncher {grid[0]}x{grid[1]}x{grid[2]}")
-    # shorter cells and a faster window so that the window shifts within a short test
-    w.window_v = 0.995018674132024
+    """Plasma-buncher physics on a small grid: 5 um longitudinal cells (the window shifts
+    every ~6 steps), 1x2x2 particles per cell, a short beam (1 um lab, ~8 cells in the RRF)."""
+    w = plasma_buncher(grid=grid, n_beam=n_beam, steps=steps, seed=seed, pml=4, ppc=(1, 2, 2),
+                       dz_m=5e-6, name=f"mini plasma buncher {grid[0]}x{grid[1]}x{grid[2]}")
+    w.beam.sigma_z = 1e-6 / w.length_unit_m
+    w.beam.origin = (grid[0] / 2, grid[1] / 2, 0.6 * grid[2])
     return w
 
 
