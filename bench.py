@@ -1,0 +1,329 @@
+#!/usr/bin/env python3
+"""Throughput of the boosted-frame PIC step on GB300.
+
+Workload: the plasma buncher (128 x 128 x 512 Yee grid, transverse PML, longitudinal moving
+window, boost 20, 4,194,304 beam electrons of lab gamma 400, cold lab-static plasma of
+1e15 cm^-3 at 8 particles per cell with frozen neutralising ions, TSC shape).  One step =
+tile sort (every 8 steps) + gather + push + Esirkepov deposit of every species + FDTD with
+CPML + window shift / plasma injection when due.  Metric: pushed macroparticle-steps per
+second (beam + plasma electrons; frozen ions are deposited every step but not counted).
+
+Default (--impl gbpic): the CUDA path through the C-ABI, timed with CUDA events on the
+context's stream over exactly K steps after W warm-up steps, barrier + synchronize on both
+sides, max over ranks.  N > 1 ranks run independent replicas (weak scaling).  The JSON line
+also carries the roofline of the dominant kernel (from the library's per-launch CUDA-event
+trace), the FP64 oracle timed on the host cores on a bounded sample (cpu_baseline), the
+end-to-end figure through the C-ABI with host buffers (e2e), clocks sampled during the timed
+region and the number of kernels launched.
+
+--impl reference: the FP64 CPU oracle, as it stands, on a bounded sample of the same workload
+(the only other place this script runs the oracle).
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s (gather+push+deposit+FDTD) FP32 vs FP64 at tol; adjoint/fwd ratio"
+UNIT = "particle-steps/s"
+HBM_FALLBACK = 6800.0
+# algorithmic bytes (FP32 storage): per pushed particle r+w of cell 4 + offset 12 + momentum 12
+# plus the weight read 4; per frozen particle r+w of cell + offset; per cell E,B read by the
+# gather (24) and J written by the deposit (12)
+BYTES_PUSHED = 60.0
+BYTES_FROZEN = 36.0
+BYTES_CELL_PUSH = 36.0
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK, "fallback"
+
+
+def env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if parts[5 + k].lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_sample(steps, warmup, seed=2):
+    """FP64 oracle on a bounded sample of the workload: a 32 x 32 x 128 sub-box with the same
+    cells, plasma density, particles per cell, beam density, boundaries and window."""
+    import oracle
+    from paper_2411_04703_gb300 import workloads as W
+    oracle.build()
+    w = W.plasma_buncher(grid=(32, 32, 128), n_beam=65536, seed=seed)
+    o = oracle.Sim(w.grid, w.d, w.dt, w.gamma_R, bc=w.bc, pml=w.pml, order=w.order,
+                   moving_window=w.moving_window, window_v=w.window_v)
+    se = o.add_species(-1.0, 1.0)
+    si = o.add_species(1.0, 1836.15267343, frozen=True)
+    sb = o.add_species(-1.0, 1.0)
+    p = w.plasma
+    o.set_plasma(se, si, p.ppc, p.xrange, p.z_nodes, p.n_nodes)
+    x, u, wt = W.sample_beam(w)
+    o.load(sb, x, u, wt, frame=0, origin=w.beam.origin)
+    if warmup:
+        o.step(warmup)
+    n0 = o.count(se) + o.count(sb)
+    t0 = time.perf_counter()
+    o.step(steps)
+    t = time.perf_counter() - t0
+    n1 = o.count(se) + o.count(sb)
+    value = 0.5 * (n0 + n1) * steps / t
+    sample = (f"FP64 oracle, 32x32x128 sub-box of the plasma buncher (8 ppc plasma + frozen ions, "
+              f"{o.count(sb)} beam), {steps} steps after {warmup} warm-up, single thread")
+    return value, t, sample
+
+
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return 0
+    steps = args.steps
+    value, t, sample = oracle_sample(steps, args.warmup)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t / steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "plasma buncher 128x128x512 (bounded sample 32x32x128), TSC, PML, moving window",
+                   "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def aggregate(psteps, ms, world, device="cpu"):
+    """Whole-job figures of independent replicas: particle-steps summed over ranks, timed
+    milliseconds maxed over ranks (the slowest rank bounds the job)."""
+    if world <= 1:
+        return float(psteps), float(ms)
+    import torch
+    import torch.distributed as dist
+    a = torch.tensor([float(psteps)], dtype=torch.float64, device=device)
+    b = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(a, op=dist.ReduceOp.SUM)
+    dist.all_reduce(b, op=dist.ReduceOp.MAX)
+    return float(a[0]), float(b[0])
+
+
+def run_gbpic(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2411_04703_gb300 import api, workloads as W
+
+    rank, world, local = env_rank()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    grid = tuple(int(v) for v in args.grid.split(","))
+    nb = args.beam or int(round(4194304 * (grid[0] * grid[1] * grid[2]) / (128 * 128 * 512)))
+    w = W.plasma_buncher(grid=grid, n_beam=nb, seed=2 + rank)
+    if grid != (128, 128, 512):
+        w.name = f"plasma buncher {grid[0]}x{grid[1]}x{grid[2]} (reduced), {nb} beam + 8 ppc plasma, TSC"
+    beam = W.sample_beam(w)
+    sim, ids = api.from_workload(w, device=local, beam_arrays=beam)
+    sim.trace_enable(True)
+    if args.warmup:
+        sim.step(args.warmup)
+    sim.sync()
+    sim.trace_read()
+    pushed = [ids["beam"], ids["plasma_e"]]
+    n0 = sum(sim.get_count(s) for s in pushed)
+    frozen0 = sim.get_count(ids["plasma_i"])
+    stream = sim.stream
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(args.steps)
+    e1.record(stream)
+    sim.sync()
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    tr = sim.trace_read()
+    n1 = sum(sim.get_count(s) for s in pushed)
+    frozen1 = sim.get_count(ids["plasma_i"])
+    psteps = 0.5 * (n0 + n1) * args.steps
+    psteps_all, ms_max = aggregate(psteps, ms, world, dev)
+    value = psteps_all / (ms_max / 1000.0)
+
+    # roofline of the dominant kernel class (live CUDA-event trace of the timed region)
+    hbm, peak_kind = peaks()
+    ncell = w.ncell
+    n_beam = sim.get_count(ids["beam"])
+    n_e = 0.5 * (n0 + n1) - n_beam
+    classes = tr["ms"]
+    dom = max(("push", "push_frozen", "fields", "sort"), key=lambda k: classes[k])
+    if dom == "push":
+        launches = tr["events"]["push"]
+        bytes_per = ((n_e + n_beam) * BYTES_PUSHED + 2 * ncell * BYTES_CELL_PUSH) / 2.0
+    elif dom == "push_frozen":
+        launches = tr["events"]["push_frozen"]
+        bytes_per = 0.5 * (frozen0 + frozen1) * BYTES_FROZEN + ncell * 12.0
+    elif dom == "fields":
+        launches = tr["events"]["fields"]
+        bytes_per = ncell * (36.0 + 48.0 + 36.0)
+    else:
+        launches = tr["events"]["sort"]
+        bytes_per = 3 * (n0 + frozen0) * 36.0
+    avg_ms = classes[dom] / max(launches, 1)
+    achieved = bytes_per / (avg_ms / 1000.0) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": None,
+                "kernel": {"push": "k_push<TSC, mobile> (beam + plasma electrons)",
+                           "push_frozen": "k_push<TSC, frozen> (ions)", "fields": "k_fdtd_b/e",
+                           "sort": "tile sort"}[dom],
+                "peak_kind": f"{peak_kind} (hbm_gbs)",
+                "avg_launch_ms": avg_ms,
+                "algorithmic_bytes_per_launch": bytes_per,
+                "time_share": {k: v / max(sum(classes.values()), 1e-9) for k, v in classes.items() if v > 0}}
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+
+    # end to end through the C-ABI with host buffers: beam H2D from pinned memory, K steps,
+    # moments D2H, on a fresh context (allocation and plasma fill are set-up, not timed)
+    e2e = None
+    if not args.no_e2e:
+        x, u, wt = beam
+        xh = torch.from_numpy(x).pin_memory()
+        uh = torch.from_numpy(u).pin_memory()
+        wh = torch.from_numpy(wt).pin_memory()
+        sim2, ids2 = api.from_workload(w, device=local, beam=False)
+        sim2.sync()
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b = w.beam
+        sb = sim2.load_species(b.q, b.m, xh, uh, wh, frame=api.PIC_FRAME_LAB, origin=b.origin)
+        ne0 = sim2.get_count(sb) + sim2.get_count(ids2["plasma_e"])
+        sim2.step(args.steps)
+        mom = sim2.get_moments(sb, api.PIC_FRAME_LAB, k_bunch=0.0)
+        t_e2e = time.perf_counter() - t0
+        ne1 = int(mom["count"]) + sim2.get_count(ids2["plasma_e"])
+        barrier()
+        h2d = (xh.numel() + uh.numel() + wh.numel()) * 8
+        e2e = {"value": 0.5 * (ne0 + ne1) * args.steps * world / t_e2e, "unit": UNIT,
+               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": 8 * 20 / args.steps,
+               "seconds": t_e2e}
+        sim2.close()
+        del sim2
+        torch.cuda.empty_cache()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cv, ct, sample = oracle_sample(3, 0)
+        cpu = {"value": cv, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "grid": list(w.grid), "beam": w.beam.n,
+                       "plasma_electrons": int(n_e), "frozen_ions": int(0.5 * (frozen0 + frozen1)),
+                       "shape": "TSC", "boundaries": "transverse CPML 10 cells, moving window",
+                       "tile": list(w.tile), "sort_every": w.sort_every,
+                       "l2": "inputs larger than L2 (particle state ~9 GB, fields 0.3 GB)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+            "gpu_launches": int(tr["kernels"]),
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["gbpic", "reference"], default="gbpic")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--grid", default="128,128,512",
+                    help="plasma-buncher grid (a smaller one, e.g. 64,64,128, for profiling captures)")
+    ap.add_argument("--beam", type=int, default=0, help="beam macroparticles (0: scaled with the grid)")
+    args = ap.parse_args()
+    if args.warmup < 0 or args.steps < 1:
+        raise SystemExit("need --steps >= 1 and --warmup >= 0")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gbpic(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -225,6 +225,20 @@ int pic_get_time(pic_ctx *ctx, int64_t out[3]);
  * a sort are not counted). */
 int pic_get_count(pic_ctx *ctx, int species_id, int64_t *n_out);
 
+/* Tracing: per-kernel-class device time from CUDA events recorded on the context stream
+ * around every launch group of pic_step / pic_sort, and the number of kernels launched.
+ * Classes: 0 tile sort, 1 particle kernel of mobile species, 2 particle kernel of frozen
+ * species, 3 field update (FDTD + CPML), 4 moving-window shift, 5 plasma injection, 6 other.
+ * pic_trace_read synchronises the stream, returns the figures accumulated since the last read
+ * (events[k]: timed launch groups of class k) and resets them.  Disabled by default. */
+typedef struct {
+    double ms[8];
+    int64_t events[8];
+    int64_t kernels;
+} pic_trace;
+int pic_trace_enable(pic_ctx *ctx, int on);
+int pic_trace_read(pic_ctx *ctx, pic_trace *out);
+
 /* Release every device allocation of the context.  NULL is accepted. */
 int pic_destroy(pic_ctx *ctx);
 

@@ -75,6 +75,13 @@ class pic_plasma(C.Structure):
                 ("capacity", C.c_int64)]
 
 
+class pic_trace(C.Structure):
+    _fields_ = [("ms", C.c_double * 8), ("events", C.c_int64 * 8), ("kernels", C.c_int64)]
+
+
+TRACE_CLASSES = ["sort", "push", "push_frozen", "fields", "window", "inject", "other", "unused"]
+
+
 class pic_moments(C.Structure):
     _fields_ = [("v", C.c_double * 20)]
 
@@ -115,6 +122,8 @@ def lib(build_if_missing: bool = True):
             "pic_get_time": [vp, P(i64)],
             "pic_get_count": [vp, i, P(i64)],
             "pic_destroy": [vp],
+            "pic_trace_enable": [vp, i],
+            "pic_trace_read": [vp, P(pic_trace)],
         }
         for name, args in sigs.items():
             fn = getattr(L, name)
@@ -161,6 +170,10 @@ class Sim:
         self._torch = torch
         if stream is None:
             stream = torch.cuda.current_stream(self.device)
+            if stream.cuda_stream == 0:
+                # the legacy null stream cannot be handed over (NULL means "make your own" in
+                # the C-ABI); use a dedicated torch stream so torch events see the work
+                stream = torch.cuda.Stream(self.device)
         self.stream = stream
         dev = pic_device()
         dev.device = self.device
@@ -305,6 +318,16 @@ class Sim:
         m = pic_moments()
         self._check(self.L.pic_get_moments(self.h, int(sid), int(frame), float(k_bunch), C.byref(m)))
         return dict(zip(MOMENT_NAMES, list(m.v)))
+
+    def trace_enable(self, on=True):
+        self._check(self.L.pic_trace_enable(self.h, int(bool(on))))
+
+    def trace_read(self):
+        t = pic_trace()
+        self._check(self.L.pic_trace_read(self.h, C.byref(t)))
+        return {"ms": {TRACE_CLASSES[k]: t.ms[k] for k in range(7)},
+                "events": {TRACE_CLASSES[k]: int(t.events[k]) for k in range(7)},
+                "kernels": int(t.kernels)}
 
     def get_time(self):
         out = (C.c_int64 * 3)()

@@ -133,6 +133,37 @@ int alloc_tile_scratch(pic_ctx *c)
 
 double shifts_due(const pic_ctx *c, int64_t n) { return std::floor(c->vw * (double)n * c->dt / c->d[2]); }
 
+// Tracing: a pair of events around a launch group of class cls.
+cudaEvent_t take_event(pic_ctx *c)
+{
+    if (!c->ev_pool.empty()) {
+        cudaEvent_t e = c->ev_pool.back();
+        c->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+struct TraceScope {
+    pic_ctx *c;
+    int cls;
+    cudaEvent_t a = nullptr;
+    TraceScope(pic_ctx *cc, int k) : c(cc), cls(k) {
+        if (c->trace_on && (a = take_event(c))) cudaEventRecord(a, c->stream);
+    }
+    ~TraceScope() {
+        if (!a) return;
+        cudaEvent_t b = take_event(c);
+        if (!b) { c->ev_pool.push_back(a); return; }
+        cudaEventRecord(b, c->stream);
+        c->ev_pending.push_back({cls, {a, b}});
+    }
+};
+
+enum { TR_SORT = 0, TR_PUSH = 1, TR_PUSH_FROZEN = 2, TR_FIELDS = 3, TR_WINDOW = 4, TR_INJECT = 5, TR_OTHER = 6 };
+
 int inject_due(pic_ctx *c)
 {
     const int64_t m1 = plane_max(c, c->step, c->shifts);
@@ -150,7 +181,10 @@ int inject_due(pic_ctx *c)
                 return fail(c, PIC_ERR_CAPACITY, "plasma species capacity exhausted by injection");
         }
     }
-    CK(launch_inject(c, c->m_last + 1, m1));
+    {
+        TraceScope ts(c, TR_INJECT);
+        CK(launch_inject(c, c->m_last + 1, m1));
+    }
     c->m_last = m1;
     return PIC_OK;
 }
@@ -521,19 +555,28 @@ int pic_step(pic_ctx *c, int64_t nsteps)
     if (r) return r;
     if (nsteps < 0) return fail(c, PIC_ERR_ARG, "negative step count");
     for (int64_t it = 0; it < nsteps; it++) {
-        if (c->step % c->sort_every == 0)
+        if (c->step % c->sort_every == 0) {
+            TraceScope ts(c, TR_SORT);
             for (int si = 0; si < c->nsp; si++) CK(launch_sort(c, si));
+        }
         CK(cudaMemsetAsync(c->J, 0, sizeof(float) * 3 * c->ncell, c->stream));
         CK(cudaMemsetAsync(c->work, 0, sizeof(int) * kMaxSpecies, c->stream));
         const ExtDev ext = ext_step(c);
-        for (int si = 0; si < c->nsp; si++) CK(launch_push(c, si, ext));
-        CK(launch_fdtd_b(c, (float)(0.5 * c->dt)));
-        CK(launch_fdtd_e(c));
-        CK(launch_fdtd_b(c, (float)(0.5 * c->dt)));
+        for (int si = 0; si < c->nsp; si++) {
+            TraceScope ts(c, c->sp[si].frozen ? TR_PUSH_FROZEN : TR_PUSH);
+            CK(launch_push(c, si, ext));
+        }
+        {
+            TraceScope ts(c, TR_FIELDS);
+            CK(launch_fdtd_b(c, (float)(0.5 * c->dt)));
+            CK(launch_fdtd_e(c));
+            CK(launch_fdtd_b(c, (float)(0.5 * c->dt)));
+        }
         c->step++;
         if (c->moving) {
             const int64_t due = (int64_t)shifts_due(c, c->step);
             while (c->shifts < due) {
+                TraceScope ts(c, TR_WINDOW);
                 CK(launch_shift_fields(c));
                 for (int si = 0; si < c->nsp; si++) CK(launch_shift_particles(c, si));
                 c->shifts++;
@@ -566,6 +609,7 @@ int pic_sort(pic_ctx *c)
 {
     int r = check_ctx(c);
     if (r) return r;
+    TraceScope ts(c, TR_SORT);
     for (int si = 0; si < c->nsp; si++) CK(launch_sort(c, si));
     return PIC_OK;
 }
@@ -687,10 +731,49 @@ int pic_get_count(pic_ctx *c, int sid, int64_t *n_out)
                              nullptr, nullptr);
 }
 
+int pic_trace_enable(pic_ctx *c, int on)
+{
+    int r = check_ctx(c);
+    if (r) return r;
+    c->trace_on = on != 0;
+    return PIC_OK;
+}
+
+int pic_trace_read(pic_ctx *c, pic_trace *out)
+{
+    int r = check_ctx(c);
+    if (r) return r;
+    if (!out) return fail(c, PIC_ERR_ARG, "trace output is NULL");
+    CK(cudaStreamSynchronize(c->stream));
+    for (auto &p : c->ev_pending) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, p.second.first, p.second.second));
+        c->trace_ms[p.first] += ms;
+        c->trace_n[p.first] += 1;
+        c->ev_pool.push_back(p.second.first);
+        c->ev_pool.push_back(p.second.second);
+    }
+    c->ev_pending.clear();
+    for (int k = 0; k < 8; k++) {
+        out->ms[k] = c->trace_ms[k];
+        out->events[k] = c->trace_n[k];
+        c->trace_ms[k] = 0;
+        c->trace_n[k] = 0;
+    }
+    out->kernels = c->kernels;
+    c->kernels = 0;
+    return PIC_OK;
+}
+
 int pic_destroy(pic_ctx *c)
 {
     if (!c) return PIC_OK;
     if (c->stream) cudaStreamSynchronize(c->stream);
+    for (auto &p : c->ev_pending) {
+        cudaEventDestroy(p.second.first);
+        cudaEventDestroy(p.second.second);
+    }
+    for (auto e : c->ev_pool) cudaEventDestroy(e);
     while (!c->allocs.empty()) dfree(c, c->allocs.back().first);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;

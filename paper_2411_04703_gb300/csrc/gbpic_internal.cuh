@@ -13,8 +13,8 @@
 namespace gbpic {
 
 constexpr int kMaxSpecies = 8;
-constexpr int kChunk = 2048;         // particles per work item of the particle kernel
-constexpr int kPushThreads = 256;
+constexpr int kChunk = 4096;         // particles per work item of the particle kernel
+constexpr int kPushThreads = 512;
 
 // Error bits of the device error word.
 enum : int {
@@ -154,6 +154,13 @@ struct pic_ctx {
     std::string msg;
     bool poisoned = false;
     std::vector<std::pair<void *, size_t>> allocs;   // every device allocation of the context
+    // tracing
+    bool trace_on = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
+    double trace_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int64_t trace_n[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int64_t kernels = 0;          // kernels launched since the last trace read
 };
 
 namespace gbpic {

@@ -132,6 +132,7 @@ cudaError_t launch_fdtd_b(pic_ctx *c, float dtt)
 {
     dim3 blk(32, 8, 1), grd((c->n[0] + 31) / 32, (c->n[1] + 7) / 8, c->n[2]);
     k_fdtd_b<<<grd, blk, 0, c->stream>>>(FieldsDev{c->E, c->B, c->J}, grid_dev(c), pml_dev(c), dtt);
+    c->kernels++;
     return cudaGetLastError();
 }
 
@@ -139,6 +140,7 @@ cudaError_t launch_fdtd_e(pic_ctx *c)
 {
     dim3 blk(32, 8, 1), grd((c->n[0] + 31) / 32, (c->n[1] + 7) / 8, c->n[2]);
     k_fdtd_e<<<grd, blk, 0, c->stream>>>(FieldsDev{c->E, c->B, c->J}, grid_dev(c), pml_dev(c));
+    c->kernels++;
     return cudaGetLastError();
 }
 
@@ -147,6 +149,7 @@ cudaError_t launch_shift_fields(pic_ctx *c)
     const int cols = c->n[0] * c->n[1];
     k_shift_fields<<<dim3((cols + 255) / 256, c->shift_n), 256, 0, c->stream>>>(c->shift_tab, c->shift_n, c->n[0],
                                                                                 c->n[1], c->n[2]);
+    c->kernels++;
     return cudaGetLastError();
 }
 
@@ -158,6 +161,7 @@ cudaError_t launch_field_energy(pic_ctx *c, double *out_host)
     for (int q = 0; q < 2; q++) {
         const float *a = q == 0 ? c->E : c->B;
         k_sumsq<<<blocks, 256, 0, c->stream>>>(a, 3 * c->ncell, c->red);
+        c->kernels++;
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         e = cudaMemcpyAsync(part.data(), c->red, blocks * sizeof(double), cudaMemcpyDeviceToHost, c->stream);

@@ -306,10 +306,12 @@ cudaError_t launch_load(pic_ctx *c, int si, int64_t n, const double *dx, const d
     p.id_base = (int)id_base;
     if (n > 0) {
         k_load<<<c->num_sms * 4, 256, 0, c->stream>>>(species_dev(c, s), p, dx, du, dw, c->err);
+        c->kernels++;
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     k_bump<<<1, 1, 0, c->stream>>>(s.count, n, (int)s.cap, c->err);
+    c->kernels++;
     return cudaGetLastError();
 }
 
@@ -343,6 +345,7 @@ cudaError_t launch_inject(pic_ctx *c, int64_t m0, int64_t m1)
     if (e != cudaSuccess) return e;
     k_bump<<<1, 1, 0, c->stream>>>(se.count, p.count, (int)se.cap, c->err);
     k_bump<<<1, 1, 0, c->stream>>>(si.count, p.count, (int)si.cap, c->err);
+    c->kernels += 3;
     se.next_id += p.count;
     si.next_id += p.count;
     se.bound += p.count;
@@ -353,6 +356,7 @@ cudaError_t launch_inject(pic_ctx *c, int64_t m0, int64_t m1)
 cudaError_t launch_shift_particles(pic_ctx *c, int si)
 {
     k_shift_particles<<<c->num_sms * 8, 256, 0, c->stream>>>(species_dev(c, c->sp[si]), c->order == 1 ? 1 : 2);
+    c->kernels++;
     return cudaGetLastError();
 }
 
@@ -375,6 +379,7 @@ cudaError_t launch_moments(pic_ctx *c, int si, int frame, double k, double *out)
     for (int pass = 0; pass < 3; pass++) {
         p.pass = pass;
         k_moments<<<blocks, 256, 0, c->stream>>>(species_dev(c, s), p, c->red);
+        c->kernels++;
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         e = cudaMemcpyAsync(part.data(), c->red, part.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream);

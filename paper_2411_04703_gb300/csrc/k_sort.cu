@@ -109,19 +109,22 @@ __global__ void k_scan_add(int *data, long long n, const int *offs)
     if (i0 + kScanThreads < n) data[i0 + kScanThreads] += add;
 }
 
-cudaError_t scan_rec(cudaStream_t st, int *data, long long n, int *scratch)
+cudaError_t scan_rec(cudaStream_t st, int *data, long long n, int *scratch, int64_t &kernels)
 {
     const long long nb = (n + kScanSeg - 1) / kScanSeg;
     if (nb <= 1) {
         k_scan_blocks<<<1, kScanThreads, 0, st>>>(data, n, nullptr);
+        kernels++;
         return cudaGetLastError();
     }
     k_scan_blocks<<<(unsigned)nb, kScanThreads, 0, st>>>(data, n, scratch);
+    kernels++;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    e = scan_rec(st, scratch, nb, scratch + nb);
+    e = scan_rec(st, scratch, nb, scratch + nb, kernels);
     if (e != cudaSuccess) return e;
     k_scan_add<<<(unsigned)nb, kScanThreads, 0, st>>>(data, n, scratch);
+    kernels++;
     return cudaGetLastError();
 }
 
@@ -141,7 +144,7 @@ int64_t scan_scratch_size(int64_t n)
 cudaError_t exclusive_scan(pic_ctx *c, int *data, int64_t n)
 {
     if (scan_scratch_size(n) > c->hist_tmp_n) return cudaErrorInvalidValue;
-    return scan_rec(c->stream, data, n, c->hist_tmp);
+    return scan_rec(c->stream, data, n, c->hist_tmp, c->kernels);
 }
 
 cudaError_t launch_sort(pic_ctx *c, int si)
@@ -165,6 +168,7 @@ cudaError_t launch_sort(pic_ctx *c, int si)
     k_fill_items<<<(c->ntiles + 255) / 256, 256, 0, c->stream>>>(s.chunk_start, c->ntiles, s.items, s.count,
                                                                   s.cell_start, n_keys);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    c->kernels += 4;   // count, scatter, tile_chunks, fill_items
     std::swap(s.pos, s.pos2);
     std::swap(s.mom, s.mom2);
     std::swap(s.id, s.id2);

@@ -1,0 +1,618 @@
+// Fused particle kernel of one boosted-frame PIC step (sm_103a): implementation shared by the
+// CIC (k_push1.cu) and TSC (k_push2.cu) translation units.
+//
+// Per particle: gather E^n, B^n with the particle shape at each component's Yee point, add
+// the analytic external undulator field of the RRF (Eq. M1-M4 applied to the lab field at
+// lab z = gamma_R (z' + beta_R t'), Eq. Vprime), leap-frog (Boris) push u^{n-1/2} -> u^{n+1/2},
+// move x^n -> x^{n+1} (integer cell + FP32 offset), and the Esirkepov charge-conserving current
+// J^{n+1/2} (Eq. Max3-Max4 solved by current weighting).
+//
+// Work decomposition: particles are sorted by tile; a persistent grid pulls (tile, chunk)
+// work items from an atomic counter.  For a tile item the CTA stages the E/B region of the
+// tile (+ drift margin + stencil halo) in shared memory, accumulates the current of its
+// particles in a shared-memory J region with shared atomics, and flushes the region to the
+// global J once with global atomics.  Particles that drifted beyond the margin since the last
+// sort, and appended (unsorted) particles, take the global-memory path.
+//
+// Deposit split: a particle whose nearest node (TSC) or cell (CIC) does not change in any
+// dimension during the step -- all but a few percent in a cold drifting plasma -- has its
+// Esirkepov current on a window of order+1 nodes per dimension with DS in closed form
+// (54 node updates for TSC instead of 144); the others are queued in shared memory and
+// deposited with the general window of order+2 nodes after the main loop.
+#pragma once
+
+#include "gbpic_internal.cuh"
+
+namespace gbpic {
+namespace push {
+
+constexpr int kQueue = 384;   // queued crossing particles per work item (overflow: inline)
+
+// ------------------------------------------------------------------ region geometry
+struct RegDyn {
+    int Rx, R2, R3;
+    __device__ __forceinline__ int rx() const { return Rx; }
+    __device__ __forceinline__ int r2() const { return R2; }
+    __device__ __forceinline__ int r3() const { return R3; }
+};
+template <int RX, int RY, int RZ> struct RegFix {
+    __device__ __forceinline__ static constexpr int rx() { return RX; }
+    __device__ __forceinline__ static constexpr int r2() { return RX * RY; }
+    __device__ __forceinline__ static constexpr int r3() { return RX * RY * RZ; }
+};
+
+// ------------------------------------------------------------------ shape weights
+// Shape S of order 1 (CIC) or 2 (TSC).  Gather weights on the integer nodes (unst) and on the
+// half-integer nodes m + 1/2 (stag), given the in-cell offset o of cell c: nodes start at c + s.
+//
+// General deposit weights: S0 = S(node - x^n) and DS = S(node - x^{n+1}) - S(node - x^n) on a
+// window of L nodes starting at c + st.  DS is formed without subtracting two shape values:
+// with the displacement d of the push, DS(m) = integral of S' over [t0, t0 + d] (t0 = o - m),
+// split at the knot of S that the segment crosses; S' is constant (CIC) or linear (TSC) on each
+// piece, so piece = length * S'(midpoint) is exact, and the length before the knot is taken in
+// offset space, (m + k) - o, which is exact near a crossing.  A slow component (|d| << 1 cell)
+// thus keeps full FP32 relative precision in its current.
+template <int ORDER> struct Shape;
+
+template <> struct Shape<1> {
+    static constexpr int N = 2;   // gather nodes per dim
+    static constexpr int L = 3;   // general Esirkepov window per dim
+    __device__ __forceinline__ static void unst(float o, int &s, float w[2]) {
+        s = 0; w[0] = 1.f - o; w[1] = o;
+    }
+    __device__ __forceinline__ static void stag(float o, int &s, float w[2]) {
+        const bool hi = o >= 0.5f;
+        const float f = hi ? o - 0.5f : o + 0.5f;
+        s = hi ? 0 : -1; w[0] = 1.f - f; w[1] = f;
+    }
+    __device__ __forceinline__ static float S(float t) { return fmaxf(0.f, 1.f - fabsf(t)); }
+    __device__ __forceinline__ static float dS(float t) {
+        return fabsf(t) < 1.f ? (t > 0.f ? -1.f : (t < 0.f ? 1.f : 0.f)) : 0.f;
+    }
+    __device__ __forceinline__ static float seg(float o, int m, float d) {
+        const float t0 = o - (float)m, t1 = t0 + d;
+        const float lo = fminf(t0, t1), hi = fmaxf(t0, t1);
+        const float k = ceilf(hi) - 1.f;            // largest knot below hi
+        if (!(k > lo)) return d * dS(t0 + 0.5f * d);
+        const float a = ((float)m + k) - o;
+        return a * dS(k - 0.5f * a) + (d - a) * dS(k + 0.5f * (d - a));
+    }
+    __device__ __forceinline__ static void general(float o, float d, int s, int &st, float S0[3], float DS[3]) {
+        st = min(s, 0);
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            S0[a] = S(o - (float)(st + a));
+            DS[a] = seg(o, st + a, d);
+        }
+    }
+    // the cell does not change: window {c, c+1}
+    __device__ __forceinline__ static bool stays(float o, float d, int s) { return s == 0; }
+    __device__ __forceinline__ static void simple(float o, float d, int &st, float S0[2], float DS[2]) {
+        st = 0;
+        S0[0] = 1.f - o; S0[1] = o;
+        DS[0] = -d; DS[1] = d;
+    }
+};
+
+template <> struct Shape<2> {
+    static constexpr int N = 3;
+    static constexpr int L = 4;
+    __device__ __forceinline__ static void tsc(float dl, float w[3]) {
+        const float a = 0.5f - dl, b = 0.5f + dl;
+        w[0] = 0.5f * a * a; w[1] = 0.75f - dl * dl; w[2] = 0.5f * b * b;
+    }
+    __device__ __forceinline__ static void unst(float o, int &s, float w[3]) {
+        const int b = o >= 0.5f;
+        s = b - 1; tsc(o - (float)b, w);
+    }
+    __device__ __forceinline__ static void stag(float o, int &s, float w[3]) {
+        s = -1; tsc(o - 0.5f, w);
+    }
+    __device__ __forceinline__ static float S(float t) {
+        const float a = fabsf(t);
+        return a <= 0.5f ? 0.75f - a * a : (a < 1.5f ? 0.5f * (1.5f - a) * (1.5f - a) : 0.f);
+    }
+    __device__ __forceinline__ static float dS(float t) {
+        const float a = fabsf(t);
+        const float v = a <= 0.5f ? -2.f * a : (a < 1.5f ? a - 1.5f : 0.f);
+        return t < 0.f ? -v : v;
+    }
+    __device__ __forceinline__ static float seg(float o, int m, float d) {
+        const float t0 = o - (float)m, t1 = t0 + d;
+        const float lo = fminf(t0, t1), hi = fmaxf(t0, t1);
+        const float k = ceilf(hi - 0.5f) - 0.5f;    // largest knot below hi
+        if (!(k > lo)) return d * dS(t0 + 0.5f * d);
+        const float a = ((float)m + k) - o;
+        return a * dS(k - 0.5f * a) + (d - a) * dS(k + 0.5f * (d - a));
+    }
+    __device__ __forceinline__ static void general(float o, float d, int /*s*/, int &st, float S0[4], float DS[4]) {
+        const int b0 = o >= 0.5f;
+        const int b1 = (int)floorf(o + d + 0.5f);   // nearest node of the new position, rel. to c
+        st = b0 - 1 + min(b1 - b0, 0);
+#pragma unroll
+        for (int a = 0; a < 4; a++) {
+            S0[a] = S(o - (float)(st + a));
+            DS[a] = seg(o, st + a, d);
+        }
+    }
+    // the nearest node does not change: window {b-1, b, b+1}; with dl = o - b in [-1/2, 1/2),
+    // S0 = TSC weights of dl and DS in closed form (each node stays on one polynomial piece)
+    __device__ __forceinline__ static bool stays(float o, float d, int) {
+        return (int)floorf(o + d + 0.5f) == (int)(o >= 0.5f);
+    }
+    __device__ __forceinline__ static void simple(float o, float d, int &st, float S0[3], float DS[3]) {
+        const int b = o >= 0.5f;
+        const float dl = o - (float)b;
+        st = b - 1;
+        tsc(dl, S0);
+        DS[0] = -d * (0.5f - dl - 0.5f * d);
+        DS[1] = -d * (2.f * dl + d);
+        DS[2] = d * (0.5f + dl + 0.5f * d);
+    }
+};
+
+// ------------------------------------------------------------------ field / current access
+// Shared-memory region of a tile: node (c + x) of the particle's cell c sits at local linear
+// index base + x + y Rx + z Rx Ry.
+template <class Reg> struct SmemAcc {
+    Reg reg;
+    const float *sF;
+    float *sJ;
+    int base;
+    __device__ __forceinline__ float f(int comp, int x, int y, int z) const {
+        return sF[comp * reg.r3() + base + z * reg.r2() + y * reg.rx() + x];
+    }
+    __device__ __forceinline__ void j(int comp, int x, int y, int z, float v) const {
+        atomicAdd(&sJ[comp * reg.r3() + base + z * reg.r2() + y * reg.rx() + x], v);
+    }
+};
+
+// Global-memory access with periodic wrap; outside a non-periodic face fields read as 0 and a
+// current contribution raises ERR_INDEX (particle margins make this unreachable).
+struct GlobAcc {
+    const float *E, *B;
+    float *J;
+    GridDev g;
+    int c[3];
+    int *err;
+    __device__ __forceinline__ long long node(int x, int y, int z) const {
+        int p[3] = {c[0] + x, c[1] + y, c[2] + z};
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            if (p[d] < 0 || p[d] >= g.n[d]) {
+                if (!g.periodic[d]) return -1;
+                p[d] = p[d] < 0 ? p[d] + g.n[d] : p[d] - g.n[d];
+            }
+        }
+        return ((long long)p[2] * g.n[1] + p[1]) * g.n[0] + p[0];
+    }
+    __device__ __forceinline__ float f(int comp, int x, int y, int z) const {
+        const long long ix = node(x, y, z);
+        if (ix < 0) return 0.f;
+        const float *F = comp < 3 ? E + comp * g.ncell : B + (comp - 3) * g.ncell;
+        return __ldg(F + ix);
+    }
+    __device__ __forceinline__ void j(int comp, int x, int y, int z, float v) const {
+        const long long ix = node(x, y, z);
+        if (ix < 0) { atomicOr(err, ERR_INDEX); return; }
+        atomicAdd(&J[comp * g.ncell + ix], v);
+    }
+};
+
+template <int N, class Acc>
+__device__ __forceinline__ float gather(const Acc &a, int comp, int sx, int sy, int sz,
+                                        const float *wx, const float *wy, const float *wz)
+{
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < N; k++) {
+        float sk = 0.f;
+#pragma unroll
+        for (int j = 0; j < N; j++) {
+            float sj = 0.f;
+#pragma unroll
+            for (int i = 0; i < N; i++) sj = fmaf(wx[i], a.f(comp, sx + i, sy + j, sz + k), sj);
+            sk = fmaf(wy[j], sj, sk);
+        }
+        s = fmaf(wz[k], sk, s);
+    }
+    return s;
+}
+
+// ------------------------------------------------------------------ Esirkepov
+// W_c = DS_c (S0_a S0_b + DS_a S0_b/2 + S0_a DS_b/2 + DS_a DS_b/3) for the two other dims a, b,
+// written as DS_c [A_a A_b + DS_a DS_b / 12] with A = S0 + DS/2, and J_c(node + 1/2) =
+// -q w (d_c/dt) (sum of W_c over the nodes up to this one) / V; the prefix over the last window
+// node vanishes (sum DS = 0) and is not stored.  fac = -q w d_c/(dt V).
+template <int L, class Acc>
+__device__ __forceinline__ void esirkepov(const Acc &acc, const int st[3], const float S0[3][L],
+                                          const float DS[3][L], const float fac[3], bool skip_x, bool skip_y)
+{
+    float A[3][L], Q[3][L];
+#pragma unroll
+    for (int d = 0; d < 3; d++)
+#pragma unroll
+        for (int a = 0; a < L; a++) {
+            A[d][a] = fmaf(0.5f, DS[d][a], S0[d][a]);
+            Q[d][a] = DS[d][a] * (1.f / 12.f);
+        }
+    float P[3][L - 1];
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        float run = 0.f;
+#pragma unroll
+        for (int a = 0; a < L - 1; a++) {
+            run += DS[d][a];
+            P[d][a] = fac[d] * run;
+        }
+    }
+    if (!skip_x) {
+#pragma unroll
+        for (int k = 0; k < L; k++)
+#pragma unroll
+            for (int j = 0; j < L; j++) {
+                const float Y = fmaf(A[1][j], A[2][k], Q[1][j] * DS[2][k]);
+                if (Y == 0.f) continue;
+#pragma unroll
+                for (int i = 0; i < L - 1; i++)
+                    if (P[0][i] != 0.f) acc.j(0, st[0] + i, st[1] + j, st[2] + k, P[0][i] * Y);
+            }
+    }
+    if (!skip_y) {
+#pragma unroll
+        for (int k = 0; k < L; k++)
+#pragma unroll
+            for (int i = 0; i < L; i++) {
+                const float Y = fmaf(A[2][k], A[0][i], Q[2][k] * DS[0][i]);
+                if (Y == 0.f) continue;
+#pragma unroll
+                for (int j = 0; j < L - 1; j++)
+                    if (P[1][j] != 0.f) acc.j(1, st[0] + i, st[1] + j, st[2] + k, P[1][j] * Y);
+            }
+    }
+#pragma unroll
+    for (int j = 0; j < L; j++)
+#pragma unroll
+        for (int i = 0; i < L; i++) {
+            const float Y = fmaf(A[0][i], A[1][j], Q[0][i] * DS[1][j]);
+            if (Y == 0.f) continue;
+#pragma unroll
+            for (int k = 0; k < L - 1; k++)
+                if (P[2][k] != 0.f) acc.j(2, st[0] + i, st[1] + j, st[2] + k, P[2][k] * Y);
+        }
+}
+
+// General window (order+2 nodes per dim), any move below one cell.
+template <int ORDER, class Acc>
+__device__ __forceinline__ void deposit_general(const Acc &acc, const float o[3], const float d[3],
+                                                const int s[3], const float fac[3])
+{
+    using S = Shape<ORDER>;
+    constexpr int L = S::L;
+    int st[3];
+    float S0[3][L], DS[3][L];
+#pragma unroll
+    for (int dd = 0; dd < 3; dd++) S::general(o[dd], d[dd], s[dd], st[dd], S0[dd], DS[dd]);
+    esirkepov<L>(acc, st, S0, DS, fac, d[0] == 0.f, d[1] == 0.f);
+}
+
+// Nearest node / cell unchanged in every dimension: window of order+1 nodes.
+template <int ORDER, class Acc>
+__device__ __forceinline__ void deposit_simple(const Acc &acc, const float o[3], const float d[3],
+                                               const float fac[3])
+{
+    using S = Shape<ORDER>;
+    constexpr int L = S::N;
+    int st[3];
+    float S0[3][L], DS[3][L];
+#pragma unroll
+    for (int dd = 0; dd < 3; dd++) S::simple(o[dd], d[dd], st[dd], S0[dd], DS[dd]);
+    esirkepov<L>(acc, st, S0, DS, fac, d[0] == 0.f, d[1] == 0.f);
+}
+
+// Gather, external field, Boris push and move of one particle.  On return d holds the push
+// displacement (cells), s the cell shift, o1 the new offsets and c the new cell.  Returns false
+// when the particle left through a non-periodic face (it becomes a dummy particle).
+template <int ORDER, bool FROZEN, class Acc>
+__device__ __forceinline__ bool push_move(const Acc &acc, const float o[3], int c[3], float4 &mo,
+                                          const SpeciesDev &sp, const GridDev &g, const ExtDev &ext,
+                                          int *err, float d[3], int s[3], float o1[3])
+{
+    using S = Shape<ORDER>;
+    constexpr int N = S::N;
+    float u[3] = {mo.x, mo.y, mo.z};
+    if (!FROZEN) {
+        int su[3], ss[3];
+        float wu[3][N], ws[3][N];
+#pragma unroll
+        for (int dd = 0; dd < 3; dd++) { S::unst(o[dd], su[dd], wu[dd]); S::stag(o[dd], ss[dd], ws[dd]); }
+        float E[3], B[3];
+        E[0] = gather<N>(acc, 0, ss[0], su[1], su[2], ws[0], wu[1], wu[2]);
+        E[1] = gather<N>(acc, 1, su[0], ss[1], su[2], wu[0], ws[1], wu[2]);
+        E[2] = gather<N>(acc, 2, su[0], su[1], ss[2], wu[0], wu[1], ws[2]);
+        B[0] = gather<N>(acc, 3, su[0], ss[1], ss[2], wu[0], ws[1], ws[2]);
+        B[1] = gather<N>(acc, 4, ss[0], su[1], ss[2], ws[0], wu[1], ws[2]);
+        B[2] = gather<N>(acc, 5, ss[0], ss[1], su[2], ws[0], ws[1], wu[2]);
+        if (ext.type == PIC_EXT_PLANAR_UNDULATOR) {
+            float f = 1.f;
+            if (ext.ramp_mode) {
+                const float r = fmaf(ext.ramp_a, (float)c[2] + o[2], ext.ramp_b);
+                f = ext.ramp_mode == 1 ? fminf(fmaxf(r, 0.f), 1.f) : (r >= 0.f ? 1.f : 0.f);
+            }
+            const float ph = ext.phase_tab[c[2]] + fmaf(ext.kdz, o[2], ext.theta);
+            const float By = ext.B0g * f * cosf(ph);
+            B[1] += By;
+            E[0] -= ext.beta_R * By;
+        }
+        // Boris rotation
+        const float h = sp.h_qm;
+        float um[3];
+#pragma unroll
+        for (int dd = 0; dd < 3; dd++) um[dd] = fmaf(h, E[dd], u[dd]);
+        const float ig = rsqrtf(1.f + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
+        float t[3];
+#pragma unroll
+        for (int dd = 0; dd < 3; dd++) t[dd] = h * B[dd] * ig;
+        const float s2 = 2.f / (1.f + t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+        const float up[3] = {um[0] + um[1] * t[2] - um[2] * t[1], um[1] + um[2] * t[0] - um[0] * t[2],
+                             um[2] + um[0] * t[1] - um[1] * t[0]};
+        const float sv[3] = {s2 * t[0], s2 * t[1], s2 * t[2]};
+        u[0] = um[0] + up[1] * sv[2] - up[2] * sv[1] + h * E[0];
+        u[1] = um[1] + up[2] * sv[0] - up[0] * sv[2] + h * E[1];
+        u[2] = um[2] + up[0] * sv[1] - up[1] * sv[0] + h * E[2];
+        mo.x = u[0]; mo.y = u[1]; mo.z = u[2];
+    }
+    const float ig = rsqrtf(1.f + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    if (!(ig > 0.f)) { atomicOr(err, ERR_NAN); return false; }
+    bool alive = true;
+#pragma unroll
+    for (int dd = 0; dd < 3; dd++) {
+        d[dd] = u[dd] * ig * g.dt_over_d[dd];        // displacement of the push (cells)
+        const float x1 = o[dd] + d[dd];
+        s[dd] = (int)floorf(x1);
+        o1[dd] = x1 - (float)s[dd];
+        if (o1[dd] >= 1.f) { o1[dd] = 0.f; s[dd] += 1; }
+        if (s[dd] < -1 || s[dd] > 1) { atomicOr(err, ERR_MOVE); return false; }
+        int cn = c[dd] + s[dd];
+        if (g.periodic[dd]) {
+            cn = cn < 0 ? cn + g.n[dd] : (cn >= g.n[dd] ? cn - g.n[dd] : cn);
+        } else if (cn < g.mlo || cn > g.n[dd] - 1 - g.mhi) {
+            alive = false;
+        }
+        c[dd] = cn;
+    }
+    return alive;
+}
+
+template <int ORDER>
+__device__ __forceinline__ bool stays_all(const float o[3], const float d[3], const int s[3])
+{
+    return Shape<ORDER>::stays(o[0], d[0], s[0]) && Shape<ORDER>::stays(o[1], d[1], s[1]) &&
+           Shape<ORDER>::stays(o[2], d[2], s[2]);
+}
+
+// Whole step of one particle on the global-memory path.
+template <int ORDER, bool FROZEN>
+__device__ __forceinline__ void step_global(const SpeciesDev &sp, const GridDev &g, const FieldsDev &f,
+                                            const ExtDev &ext, int *err, int p)
+{
+    float4 P = sp.pos[p];
+    const int cell = __float_as_int(P.w);
+    if (cell < 0) return;
+    float4 mo = sp.mom[p];
+    int c[3] = {cell_i(cell), cell_j(cell), cell_k(cell)};
+    const float o[3] = {P.x, P.y, P.z};
+    GlobAcc acc{f.E, f.B, f.J, g, {c[0], c[1], c[2]}, err};
+    float d[3], o1[3];
+    int s[3];
+    if (push_move<ORDER, FROZEN>(acc, o, c, mo, sp, g, ext, err, d, s, o1)) {
+        const float fac[3] = {sp.cf[0] * mo.w, sp.cf[1] * mo.w, sp.cf[2] * mo.w};
+        deposit_general<ORDER>(acc, o, d, s, fac);
+        P = make_float4(o1[0], o1[1], o1[2], __int_as_float(pack_cell(c[0], c[1], c[2])));
+        if (!FROZEN) sp.mom[p] = mo;
+    } else {
+        P.w = __int_as_float(-1);
+    }
+    sp.pos[p] = P;
+}
+
+template <int ORDER, bool FROZEN, class Reg>
+__global__ void __launch_bounds__(kPushThreads)
+k_push(SpeciesDev sp, GridDev g, TileDev t, FieldsDev f, ExtDev ext, int *work, int *err, Reg reg)
+{
+    extern __shared__ float smem[];
+    __shared__ int s_item, s_qn;
+    const int Rx = reg.rx(), R3 = reg.r3();
+    float *sF = smem;
+    float *sJ = FROZEN ? smem : smem + 6 * R3;
+    int *qb = reinterpret_cast<int *>(sJ + 3 * R3);      // queue: local base index
+    float *qd = reinterpret_cast<float *>(qb + kQueue);  // queue: o[3], d[3], w (SoA)
+    const int n_total = sp.count[0], n_sorted = sp.count[1], n_tile_items = sp.count[2];
+    const int n_items = n_tile_items + (n_total - n_sorted + kChunk - 1) / kChunk;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(work, 1);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= n_items) break;
+
+        if (item >= n_tile_items) {
+            const int p_begin = n_sorted + (item - n_tile_items) * kChunk;
+            const int p_end = min(p_begin + kChunk, n_total);
+            for (int p = p_begin + threadIdx.x; p < p_end; p += blockDim.x)
+                step_global<ORDER, FROZEN>(sp, g, f, ext, err, p);
+            continue;
+        }
+
+        const int2 wi = t.items[item];
+        const int tile = wi.x;
+        const int tx = tile % t.nt[0], ty = (tile / t.nt[0]) % t.nt[1], tz = tile / (t.nt[0] * t.nt[1]);
+        const int t0[3] = {tx * t.T[0], ty * t.T[1], tz * t.T[2]};
+        const int reg0[3] = {t0[0] - t.M - t.hl, t0[1] - t.M - t.hl, t0[2] - t.M - t.hl};
+        const int key0 = tile * t.tile_cells;
+        const int p_begin = t.cell_start[key0] + wi.y * kChunk;
+        const int p_end = min(p_begin + kChunk, t.cell_start[key0 + t.tile_cells]);
+        const int nrows = t.R[1] * t.R[2];
+        // stage E/B of the region (one warp per x-row, lanes along x), zero the J region
+        if (!FROZEN) {
+            for (int row = warp; row < 6 * nrows; row += nwarp) {
+                const int comp = row / nrows, r = row - comp * nrows;
+                const int lz = r / t.R[1], ly = r - lz * t.R[1];
+                int py = reg0[1] + ly, pz = reg0[2] + lz;
+                bool ok = true;
+                if (py < 0 || py >= g.n[1]) { if (g.periodic[1]) py = py < 0 ? py + g.n[1] : py - g.n[1]; else ok = false; }
+                if (pz < 0 || pz >= g.n[2]) { if (g.periodic[2]) pz = pz < 0 ? pz + g.n[2] : pz - g.n[2]; else ok = false; }
+                const float *F = comp < 3 ? f.E + comp * g.ncell : f.B + (comp - 3) * g.ncell;
+                const long long rowbase = ((long long)pz * g.n[1] + py) * g.n[0];
+                for (int lx = lane; lx < Rx; lx += 32) {
+                    int px = reg0[0] + lx;
+                    bool okx = ok;
+                    if (px < 0 || px >= g.n[0]) { if (g.periodic[0]) px = px < 0 ? px + g.n[0] : px - g.n[0]; else okx = false; }
+                    sF[comp * R3 + r * Rx + lx] = okx ? __ldg(F + rowbase + px) : 0.f;
+                }
+            }
+        }
+        for (int l = threadIdx.x; l < 3 * R3; l += blockDim.x) sJ[l] = 0.f;
+        if (threadIdx.x == 0) s_qn = 0;
+        __syncthreads();
+        // lanes of a warp take particles G apart (one cell apart for a sorted plasma), so a
+        // warp's shared atomics rarely hit the same address
+        const int len = p_end - p_begin;
+        const int G = (len + nwarp * 32 - 1) / (nwarp * 32);
+        for (int k_it = 0; k_it < G; k_it++) {
+            const int q = (warp * 32 + lane) * G + k_it;
+            if (q >= len) continue;
+            const int p = p_begin + q;
+            float4 P = sp.pos[p];
+            const int cell = __float_as_int(P.w);
+            if (cell < 0) continue;
+            int c[3] = {cell_i(cell), cell_j(cell), cell_k(cell)};
+            int rel[3];
+            bool fast = true;
+#pragma unroll
+            for (int dd = 0; dd < 3; dd++) {
+                int r = c[dd] - t0[dd];
+                if (g.periodic[dd]) {
+                    if (r > g.n[dd] / 2) r -= g.n[dd];
+                    else if (r < -g.n[dd] / 2) r += g.n[dd];
+                }
+                rel[dd] = r;
+                fast = fast && r >= -t.M && r < t.T[dd] + t.M;
+            }
+            if (!fast) {
+                step_global<ORDER, FROZEN>(sp, g, f, ext, err, p);
+                continue;
+            }
+            float4 mo = sp.mom[p];
+            const float o[3] = {P.x, P.y, P.z};
+            const int base = ((rel[2] + t.M + t.hl) * t.R[1] + rel[1] + t.M + t.hl) * Rx + rel[0] + t.M + t.hl;
+            SmemAcc<Reg> acc{reg, sF, sJ, base};
+            float d[3], o1[3];
+            int s[3];
+            if (push_move<ORDER, FROZEN>(acc, o, c, mo, sp, g, ext, err, d, s, o1)) {
+                const float fac[3] = {sp.cf[0] * mo.w, sp.cf[1] * mo.w, sp.cf[2] * mo.w};
+                if (stays_all<ORDER>(o, d, s)) {
+                    deposit_simple<ORDER>(acc, o, d, fac);
+                } else {
+                    const int slot = atomicAdd(&s_qn, 1);
+                    if (slot < kQueue) {
+                        qb[slot] = base;
+                        qd[0 * kQueue + slot] = o[0];
+                        qd[1 * kQueue + slot] = o[1];
+                        qd[2 * kQueue + slot] = o[2];
+                        qd[3 * kQueue + slot] = d[0];
+                        qd[4 * kQueue + slot] = d[1];
+                        qd[5 * kQueue + slot] = d[2];
+                        qd[6 * kQueue + slot] = mo.w;
+                    } else {
+                        deposit_general<ORDER>(acc, o, d, s, fac);
+                    }
+                }
+                P = make_float4(o1[0], o1[1], o1[2], __int_as_float(pack_cell(c[0], c[1], c[2])));
+                if (!FROZEN) sp.mom[p] = mo;
+            } else {
+                P.w = __int_as_float(-1);
+            }
+            sp.pos[p] = P;
+        }
+        __syncthreads();
+        // queued particles that crossed a node: general window
+        const int qn = min(s_qn, kQueue);
+        for (int q = threadIdx.x; q < qn; q += blockDim.x) {
+            const float o[3] = {qd[q], qd[kQueue + q], qd[2 * kQueue + q]};
+            const float d[3] = {qd[3 * kQueue + q], qd[4 * kQueue + q], qd[5 * kQueue + q]};
+            const float w = qd[6 * kQueue + q];
+            int s[3];
+#pragma unroll
+            for (int dd = 0; dd < 3; dd++) {
+                const float x1 = o[dd] + d[dd];
+                s[dd] = (int)floorf(x1);
+                if (x1 - (float)s[dd] >= 1.f) s[dd] += 1;
+            }
+            const float fac[3] = {sp.cf[0] * w, sp.cf[1] * w, sp.cf[2] * w};
+            SmemAcc<Reg> acc{reg, sF, sJ, qb[q]};
+            deposit_general<ORDER>(acc, o, d, s, fac);
+        }
+        __syncthreads();
+        // one flush of the region's current to global memory (x-rows, coalesced atomics)
+        for (int row = warp; row < 3 * nrows; row += nwarp) {
+            const int comp = row / nrows, r = row - comp * nrows;
+            const int lz = r / t.R[1], ly = r - lz * t.R[1];
+            int py = reg0[1] + ly, pz = reg0[2] + lz;
+            bool ok = true;
+            if (py < 0 || py >= g.n[1]) { if (g.periodic[1]) py = py < 0 ? py + g.n[1] : py - g.n[1]; else ok = false; }
+            if (pz < 0 || pz >= g.n[2]) { if (g.periodic[2]) pz = pz < 0 ? pz + g.n[2] : pz - g.n[2]; else ok = false; }
+            float *Jc = f.J + comp * g.ncell + ((long long)pz * g.n[1] + py) * g.n[0];
+            for (int lx = lane; lx < Rx; lx += 32) {
+                const float v = sJ[comp * R3 + r * Rx + lx];
+                if (v == 0.f) continue;
+                int px = reg0[0] + lx;
+                bool okx = ok;
+                if (px < 0 || px >= g.n[0]) { if (g.periodic[0]) px = px < 0 ? px + g.n[0] : px - g.n[0]; else okx = false; }
+                if (!okx) { atomicOr(err, ERR_INDEX); continue; }
+                atomicAdd(Jc + px, v);
+            }
+        }
+    }
+}
+
+template <int ORDER, bool FROZEN, class Reg>
+cudaError_t launch_t(pic_ctx *c, int si, const ExtDev &ext, Reg reg, int R3)
+{
+    const Species &s = c->sp[si];
+    TileDev t = tile_dev(c, s);
+    const size_t smem = (size_t)(FROZEN ? 3 : 9) * R3 * sizeof(float) + (size_t)kQueue * 8 * sizeof(float);
+    auto kern = k_push<ORDER, FROZEN, Reg>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPushThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    FieldsDev f{c->E, c->B, c->J};
+    kern<<<c->num_sms * per_sm, kPushThreads, smem, c->stream>>>(species_dev(c, s), grid_dev(c), t, f, ext,
+                                                                   c->work + si, c->err, reg);
+    c->kernels++;
+    return cudaGetLastError();
+}
+
+// Compile-time region for the default tile (8^3 cells, drift margin 1); any other tuning uses
+// the runtime-sized region.
+template <int ORDER>
+cudaError_t launch_order(pic_ctx *c, int si, const ExtDev &ext)
+{
+    constexpr int R = 8 + 2 * 1 + (ORDER == 1 ? 3 : 5);
+    const bool fr = c->sp[si].frozen != 0;
+    const TileDev t = tile_dev(c, c->sp[si]);
+    if (c->T[0] == 8 && c->T[1] == 8 && c->T[2] == 8 && c->M == 1) {
+        RegFix<R, R, R> reg;
+        return fr ? launch_t<ORDER, true>(c, si, ext, reg, R * R * R) : launch_t<ORDER, false>(c, si, ext, reg, R * R * R);
+    }
+    RegDyn reg{t.R[0], t.R[0] * t.R[1], t.R[0] * t.R[1] * t.R[2]};
+    return fr ? launch_t<ORDER, true>(c, si, ext, reg, reg.R3) : launch_t<ORDER, false>(c, si, ext, reg, reg.R3);
+}
+
+}  // namespace push
+}  // namespace gbpic
