@@ -263,7 +263,14 @@ SpeciesDev species_dev(const pic_ctx *c, const Species &s)
     d.count = s.count;
     d.h_qm = (float)(0.5 * s.q / s.m * c->dt);
     const double V = c->d[0] * c->d[1] * c->d[2];
-    for (int k = 0; k < 3; k++) d.cf[k] = (float)(-s.q * c->d[k] / (c->dt * V));
+    for (int k = 0; k < 3; k++) {
+        d.cf[k] = (float)(-s.q * c->d[k] / (c->dt * V));
+        // |contribution| <= |cf| w |prefix DS| |A A + DS DS/12| <= 1.1 |cf| wmax: map it to 2^38
+        const double mx = 1.1 * std::fabs((double)d.cf[k]) * s.wmax;
+        const double sc = mx > 0 ? std::ldexp(1.0, 38) / mx : 1.0;
+        d.jscale[k] = (float)sc;
+        d.jinv[k] = 1.0 / (double)d.jscale[k];
+    }
     d.frozen = s.frozen;
     d.cap = (int)s.cap;
     return d;
@@ -429,7 +436,8 @@ int pic_set_tuning(pic_ctx *c, const pic_tuning *t)
     if (t->margin < 0 || t->margin > 2) return fail(c, PIC_ERR_ARG, "margin must be 0..2");
     int R3 = 1;
     for (int d = 0; d < 3; d++) R3 *= t->tile[d] + 2 * t->margin + margin_lo(c) + margin_hi(c);
-    if ((size_t)R3 * 9 * sizeof(float) > 200 * 1024) return fail(c, PIC_ERR_ARG, "tile region exceeds shared memory");
+    if ((size_t)R3 * 12 * sizeof(float) + 16 * 1024 > 220 * 1024)
+        return fail(c, PIC_ERR_ARG, "tile region exceeds shared memory");
     for (int d = 0; d < 3; d++) c->T[d] = t->tile[d];
     c->sort_every = t->sort_every;
     c->M = t->margin;
@@ -462,6 +470,11 @@ int pic_load_species(pic_ctx *c, const pic_species *sp, int64_t n, const double 
     CK(launch_load(c, sid, n, dx, du, dw, frame, sp->origin, sp->match_undulator, s.next_id));
     s.next_id += n;
     s.bound += n;
+    if (n > 0) {
+        double wm = 0;
+        CK(species_wmax(c, sid, &wm));
+        s.wmax = std::max(s.wmax, wm);
+    }
     if (n > 0) {
         CK(cudaStreamSynchronize(c->stream));
         dfree(c, dx);
@@ -537,6 +550,12 @@ int pic_set_plasma(pic_ctx *c, const pic_plasma *p, int *electron_id, int *ion_i
     c->plasma = 1;
     c->sp_e = se;
     c->sp_i = si;
+    {
+        double nmax = 0;
+        for (int i = 0; i < p->n_nodes; i++) nmax = std::max(nmax, std::fabs(p->density[i]));
+        const double wm = c->gR * nmax * c->d[0] * c->d[1] * c->d[2] / ((double)c->ppc[0] * c->ppc[1] * c->ppc[2]);
+        c->sp[se].wmax = c->sp[si].wmax = wm;
+    }
     const double lo = (double)margin_lo(c) + (double)c->shifts + c->bR * (double)c->step * c->dt / c->d[2];
     const int64_t m0 = (int64_t)std::ceil((double)c->ppc[2] * lo - 0.5);
     const int64_t m1 = plane_max(c, c->step, c->shifts);
@@ -784,5 +803,6 @@ const char *pic_last_error(const pic_ctx *c)
 {
     return c ? c->msg.c_str() : g_create_err.c_str();
 }
+
 
 }  // extern "C"

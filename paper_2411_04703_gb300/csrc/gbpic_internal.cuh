@@ -66,6 +66,8 @@ struct SpeciesDev {
     int *count;           // [0] total slots in use, [1] sorted prefix, [2] tile work items
     float h_qm;           // 0.5 (q/m) dt
     float cf[3];          // -q d_c / (dt V): current of unit weight per unit W
+    float jscale[3];      // fixed-point scale of the shared-memory current (max contribution 2^38)
+    double jinv[3];       // 1 / jscale
     int frozen;
     int cap;
 };
@@ -100,6 +102,7 @@ struct Species {
     int *chunk_start = nullptr; // device [ntiles + 1]
     int64_t bound = 0;        // host upper bound of count[0]
     int64_t next_id = 0;
+    double wmax = 0;          // largest |weight| ever held (sets the fixed-point current scale)
 };
 
 }  // namespace gbpic
@@ -190,5 +193,6 @@ cudaError_t launch_load(pic_ctx *c, int si, int64_t n, const double *dx, const d
 cudaError_t launch_inject(pic_ctx *c, int64_t m0, int64_t m1);
 cudaError_t launch_shift_particles(pic_ctx *c, int si);
 cudaError_t launch_moments(pic_ctx *c, int si, int frame, double k, double *out20);
+cudaError_t species_wmax(pic_ctx *c, int si, double *out);
 
 }  // namespace gbpic

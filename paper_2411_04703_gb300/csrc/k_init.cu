@@ -272,6 +272,22 @@ __global__ void k_moments(SpeciesDev sp, MomP p, double *partial)
     }
 }
 
+__global__ void k_wmax(SpeciesDev sp, double *partial)
+{
+    double m = 0.0;
+    const int n = sp.count[0];
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x)
+        m = fmax(m, fabs((double)sp.mom[p].w));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+    __shared__ double ws[32];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < (int)(blockDim.x >> 5); k++) m = fmax(m, ws[k]);
+        partial[blockIdx.x] = m;
+    }
+}
+
 PlaceP place_params(const pic_ctx *c)
 {
     PlaceP g;
@@ -351,6 +367,23 @@ cudaError_t launch_inject(pic_ctx *c, int64_t m0, int64_t m1)
     se.bound += p.count;
     si.bound += p.count;
     return cudaGetLastError();
+}
+
+cudaError_t species_wmax(pic_ctx *c, int si, double *out)
+{
+    const int blocks = 256;
+    k_wmax<<<blocks, 256, 0, c->stream>>>(species_dev(c, c->sp[si]), c->red);
+    c->kernels++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    std::vector<double> part(blocks);
+    e = cudaMemcpyAsync(part.data(), c->red, blocks * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return e;
+    double m = 0.0;
+    for (double v : part) m = std::max(m, v);
+    *out = m;
+    return cudaSuccess;
 }
 
 cudaError_t launch_shift_particles(pic_ctx *c, int si)

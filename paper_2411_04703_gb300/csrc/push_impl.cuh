@@ -154,16 +154,32 @@ template <> struct Shape<2> {
 // ------------------------------------------------------------------ field / current access
 // Shared-memory region of a tile: node (c + x) of the particle's cell c sits at local linear
 // index base + x + y Rx + z Rx Ry.
+//
+// The region's current is accumulated as exact fixed point with native 32-bit integer shared
+// atomics (a float add on shared memory is not a native atomic): a contribution v becomes
+// V = round(v * jscale) with |V| <= 2^38 for the largest possible contribution of the species,
+// split into 19 low bits (unsigned word) and the rest (signed word).  A work item holds at most
+// kChunk = 4096 particles, each adding at most once per node and component, so neither word
+// overflows; the flush recombines hi * 2^19 + lo exactly in 64-bit integers.
+constexpr int kLoBits = 19;
+constexpr unsigned kLoMask = (1u << kLoBits) - 1u;
+static_assert(kChunk <= 4096, "fixed-point current words sized for 4096 contributions per node");
+
 template <class Reg> struct SmemAcc {
     Reg reg;
     const float *sF;
-    float *sJ;
+    unsigned *sJlo;
+    int *sJhi;
+    float js[3];
     int base;
     __device__ __forceinline__ float f(int comp, int x, int y, int z) const {
         return sF[comp * reg.r3() + base + z * reg.r2() + y * reg.rx() + x];
     }
     __device__ __forceinline__ void j(int comp, int x, int y, int z, float v) const {
-        atomicAdd(&sJ[comp * reg.r3() + base + z * reg.r2() + y * reg.rx() + x], v);
+        const int ix = comp * reg.r3() + base + z * reg.r2() + y * reg.rx() + x;
+        const long long V = __float2ll_rn(v * js[comp]);
+        atomicAdd(&sJlo[ix], (unsigned)(V & kLoMask));
+        atomicAdd(&sJhi[ix], (int)(V >> kLoBits));
     }
 };
 
@@ -424,9 +440,11 @@ k_push(SpeciesDev sp, GridDev g, TileDev t, FieldsDev f, ExtDev ext, int *work, 
     __shared__ int s_item, s_qn;
     const int Rx = reg.rx(), R3 = reg.r3();
     float *sF = smem;
-    float *sJ = FROZEN ? smem : smem + 6 * R3;
-    int *qb = reinterpret_cast<int *>(sJ + 3 * R3);      // queue: local base index
+    unsigned *sJlo = reinterpret_cast<unsigned *>(FROZEN ? smem : smem + 6 * R3);
+    int *sJhi = reinterpret_cast<int *>(sJlo + 3 * R3);
+    int *qb = sJhi + 3 * R3;                              // queue: local base index
     float *qd = reinterpret_cast<float *>(qb + kQueue);  // queue: o[3], d[3], w (SoA)
+    const float js[3] = {sp.jscale[0], sp.jscale[1], sp.jscale[2]};
     const int n_total = sp.count[0], n_sorted = sp.count[1], n_tile_items = sp.count[2];
     const int n_items = n_tile_items + (n_total - n_sorted + kChunk - 1) / kChunk;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
@@ -474,7 +492,10 @@ k_push(SpeciesDev sp, GridDev g, TileDev t, FieldsDev f, ExtDev ext, int *work, 
                 }
             }
         }
-        for (int l = threadIdx.x; l < 3 * R3; l += blockDim.x) sJ[l] = 0.f;
+        for (int l = threadIdx.x; l < 3 * R3; l += blockDim.x) {
+            sJlo[l] = 0u;
+            sJhi[l] = 0;
+        }
         if (threadIdx.x == 0) s_qn = 0;
         __syncthreads();
         // lanes of a warp take particles G apart (one cell apart for a sorted plasma), so a
@@ -508,7 +529,7 @@ k_push(SpeciesDev sp, GridDev g, TileDev t, FieldsDev f, ExtDev ext, int *work, 
             float4 mo = sp.mom[p];
             const float o[3] = {P.x, P.y, P.z};
             const int base = ((rel[2] + t.M + t.hl) * t.R[1] + rel[1] + t.M + t.hl) * Rx + rel[0] + t.M + t.hl;
-            SmemAcc<Reg> acc{reg, sF, sJ, base};
+            SmemAcc<Reg> acc{reg, sF, sJlo, sJhi, {js[0], js[1], js[2]}, base};
             float d[3], o1[3];
             int s[3];
             if (push_move<ORDER, FROZEN>(acc, o, c, mo, sp, g, ext, err, d, s, o1)) {
@@ -552,7 +573,7 @@ k_push(SpeciesDev sp, GridDev g, TileDev t, FieldsDev f, ExtDev ext, int *work, 
                 if (x1 - (float)s[dd] >= 1.f) s[dd] += 1;
             }
             const float fac[3] = {sp.cf[0] * w, sp.cf[1] * w, sp.cf[2] * w};
-            SmemAcc<Reg> acc{reg, sF, sJ, qb[q]};
+            SmemAcc<Reg> acc{reg, sF, sJlo, sJhi, {js[0], js[1], js[2]}, qb[q]};
             deposit_general<ORDER>(acc, o, d, s, fac);
         }
         __syncthreads();
@@ -565,9 +586,12 @@ k_push(SpeciesDev sp, GridDev g, TileDev t, FieldsDev f, ExtDev ext, int *work, 
             if (py < 0 || py >= g.n[1]) { if (g.periodic[1]) py = py < 0 ? py + g.n[1] : py - g.n[1]; else ok = false; }
             if (pz < 0 || pz >= g.n[2]) { if (g.periodic[2]) pz = pz < 0 ? pz + g.n[2] : pz - g.n[2]; else ok = false; }
             float *Jc = f.J + comp * g.ncell + ((long long)pz * g.n[1] + py) * g.n[0];
+            const float jinv = (float)sp.jinv[comp];
             for (int lx = lane; lx < Rx; lx += 32) {
-                const float v = sJ[comp * R3 + r * Rx + lx];
-                if (v == 0.f) continue;
+                const int ix = comp * R3 + r * Rx + lx;
+                const long long V = ((long long)sJhi[ix] << kLoBits) + (long long)sJlo[ix];
+                if (V == 0) continue;
+                const float v = (float)V * jinv;
                 int px = reg0[0] + lx;
                 bool okx = ok;
                 if (px < 0 || px >= g.n[0]) { if (g.periodic[0]) px = px < 0 ? px + g.n[0] : px - g.n[0]; else okx = false; }
@@ -583,7 +607,8 @@ cudaError_t launch_t(pic_ctx *c, int si, const ExtDev &ext, Reg reg, int R3)
 {
     const Species &s = c->sp[si];
     TileDev t = tile_dev(c, s);
-    const size_t smem = (size_t)(FROZEN ? 3 : 9) * R3 * sizeof(float) + (size_t)kQueue * 8 * sizeof(float);
+    const size_t smem = (size_t)(FROZEN ? 0 : 6) * R3 * sizeof(float) + (size_t)3 * R3 * 2 * sizeof(int) +
+                        (size_t)kQueue * 8 * sizeof(float);
     auto kern = k_push<ORDER, FROZEN, Reg>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
