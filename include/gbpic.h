@@ -239,6 +239,29 @@ typedef struct {
 int pic_trace_enable(pic_ctx *ctx, int on);
 int pic_trace_read(pic_ctx *ctx, pic_trace *out);
 
+/* Allocation-free counting sort of caller-owned arrays, for callers that cannot let a library
+ * allocate device memory (an application that reserves its whole device budget in its own
+ * pool at start-up and forbids allocations afterwards, or code running where the CUDA
+ * allocator must not be entered).  The paper has no counterpart: it is a variant of the tile
+ * sort that pic_step runs internally.  cells: device int32[n], packed cell indices
+ * i | j << 10 | k << 20 (-1 or a cell outside the grid = dummy, dropped); grid, tile: host int[3] (grid <= 1024 x 1024 x
+ * 2048, 1 <= tile <= grid); order: device int32[n], receives at sorted position q the index of
+ * the input element placed there (live elements only, ascending tile-major key: tiles x-fastest,
+ * cells in a tile x-fastest; order among equal keys unspecified); key_start: device
+ * int32[n_keys + 1] with n_keys = (tiles per dim product) * tile cells, receives the exclusive
+ * start of each key (key_start[n_keys] = number of live elements); stream: cudaStream_t or NULL.
+ * Limits: n <= PIC_NOALLOC_MAX_N, n_keys <= PIC_NOALLOC_MAX_KEYS; larger sizes return
+ * PIC_ERR_ARG with a message in pic_last_error(NULL).  Scratch comes from a fixed device array
+ * inside the library (about 4 MB per GPU that loads the library, held until the process
+ * exits); the first call on each device looks up its address (with that device current), so
+ * make the first call before any stream capture.  It calls no cudaMalloc/cudaFree.  All calls
+ * share that scratch: calls whose work overlaps on the GPU race and give wrong results.
+ * Asynchronous on `stream`. */
+#define PIC_NOALLOC_MAX_N (1 << 20)
+#define PIC_NOALLOC_MAX_KEYS (1 << 22)
+int pic_tile_sort_noalloc(const int32_t *cells, int64_t n, const int grid[3], const int tile[3],
+                          int32_t *order, int32_t *key_start, void *stream);
+
 /* Release every device allocation of the context.  NULL is accepted. */
 int pic_destroy(pic_ctx *ctx);
 

@@ -804,5 +804,13 @@ const char *pic_last_error(const pic_ctx *c)
     return c ? c->msg.c_str() : g_create_err.c_str();
 }
 
+}  // extern "C"
+
+namespace gbpic {
+// Message of a failed context-free call, reported by pic_last_error(NULL).
+void set_global_error(const std::string &m) { g_create_err = m; }
+}  // namespace gbpic
+
+extern "C" {
 
 }  // extern "C"
