@@ -8,7 +8,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/gbpic.h"
+#include "gbpic.h"
 
 namespace gbpic {
 

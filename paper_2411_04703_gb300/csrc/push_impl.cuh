@@ -30,13 +30,15 @@ constexpr int kQueue = 384;   // queued crossing particles per work item (overfl
 
 // ------------------------------------------------------------------ region geometry
 struct RegDyn {
-    int Rx, R2, R3;
+    int Rx, Ry, R2, R3;
     __device__ __forceinline__ int rx() const { return Rx; }
+    __device__ __forceinline__ int ry() const { return Ry; }
     __device__ __forceinline__ int r2() const { return R2; }
     __device__ __forceinline__ int r3() const { return R3; }
 };
 template <int RX, int RY, int RZ> struct RegFix {
     __device__ __forceinline__ static constexpr int rx() { return RX; }
+    __device__ __forceinline__ static constexpr int ry() { return RY; }
     __device__ __forceinline__ static constexpr int r2() { return RX * RY; }
     __device__ __forceinline__ static constexpr int r3() { return RX * RY * RZ; }
 };
@@ -172,14 +174,18 @@ template <class Reg> struct SmemAcc {
     int *sJhi;
     float js[3];
     int base;
+    __device__ __forceinline__ float scale(int comp) const { return js[comp]; }
     __device__ __forceinline__ float f(int comp, int x, int y, int z) const {
         return sF[comp * reg.r3() + base + z * reg.r2() + y * reg.rx() + x];
     }
+    // v is already in fixed-point units (times scale(comp)); split with 32-bit conversions:
+    // hi = floor(v / 2^19), lo = v - hi 2^19 in [0, 2^19] (the FMA difference is exact)
     __device__ __forceinline__ void j(int comp, int x, int y, int z, float v) const {
         const int ix = comp * reg.r3() + base + z * reg.r2() + y * reg.rx() + x;
-        const long long V = __float2ll_rn(v * js[comp]);
-        atomicAdd(&sJlo[ix], (unsigned)(V & kLoMask));
-        atomicAdd(&sJhi[ix], (int)(V >> kLoBits));
+        const float hf = floorf(v * (1.f / (float)(1u << kLoBits)));
+        const float lf = fmaf(-hf, (float)(1u << kLoBits), v);
+        atomicAdd(&sJlo[ix], __float2uint_rn(lf));
+        atomicAdd(&sJhi[ix], (int)hf);
     }
 };
 
@@ -202,6 +208,7 @@ struct GlobAcc {
         }
         return ((long long)p[2] * g.n[1] + p[1]) * g.n[0] + p[0];
     }
+    __device__ __forceinline__ float scale(int) const { return 1.f; }
     __device__ __forceinline__ float f(int comp, int x, int y, int z) const {
         const long long ix = node(x, y, z);
         if (ix < 0) return 0.f;
@@ -255,11 +262,12 @@ __device__ __forceinline__ void esirkepov(const Acc &acc, const int st[3], const
     float P[3][L - 1];
 #pragma unroll
     for (int d = 0; d < 3; d++) {
+        const float fs = fac[d] * acc.scale(d);
         float run = 0.f;
 #pragma unroll
         for (int a = 0; a < L - 1; a++) {
             run += DS[d][a];
-            P[d][a] = fac[d] * run;
+            P[d][a] = fs * run;
         }
     }
     if (!skip_x) {
@@ -432,6 +440,20 @@ __device__ __forceinline__ void step_global(const SpeciesDev &sp, const GridDev 
     sp.pos[p] = P;
 }
 
+// Linear index of grid node (x, y, z) with periodic wrap, or -1 outside a non-periodic face.
+__device__ __forceinline__ long long wrap_node(const GridDev &g, int x, int y, int z)
+{
+    int p[3] = {x, y, z};
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        if (p[d] < 0 || p[d] >= g.n[d]) {
+            if (!g.periodic[d]) return -1;
+            p[d] = p[d] < 0 ? p[d] + g.n[d] : p[d] - g.n[d];
+        }
+    }
+    return ((long long)p[2] * g.n[1] + p[1]) * g.n[0] + p[0];
+}
+
 template <int ORDER, bool FROZEN, class Reg>
 __global__ void __launch_bounds__(kPushThreads)
 k_push(SpeciesDev sp, GridDev g, TileDev t, FieldsDev f, ExtDev ext, int *work, int *err, Reg reg)
@@ -472,23 +494,27 @@ k_push(SpeciesDev sp, GridDev g, TileDev t, FieldsDev f, ExtDev ext, int *work, 
         const int key0 = tile * t.tile_cells;
         const int p_begin = t.cell_start[key0] + wi.y * kChunk;
         const int p_end = min(p_begin + kChunk, t.cell_start[key0 + t.tile_cells]);
-        const int nrows = t.R[1] * t.R[2];
-        // stage E/B of the region (one warp per x-row, lanes along x), zero the J region
+        // Region of the tile: nodes reg0 + (0..R-1) per dim.  A tile away from every face needs
+        // no wrap or bounds test; the loops run over the region's nodes with compile-time
+        // divisions (fixed region) and each thread moves all components of its node.
+        const int R2 = reg.r2(), Ry = reg.ry(), Rz = R3 / R2;
+        const bool interior = reg0[0] >= 0 && reg0[0] + Rx <= g.n[0] && reg0[1] >= 0 && reg0[1] + Ry <= g.n[1] &&
+                              reg0[2] >= 0 && reg0[2] + Rz <= g.n[2];
+        const long long gnx = g.n[0], gnxy = (long long)g.n[0] * g.n[1];
+        const long long gbase = reg0[2] * gnxy + reg0[1] * gnx + reg0[0];
         if (!FROZEN) {
-            for (int row = warp; row < 6 * nrows; row += nwarp) {
-                const int comp = row / nrows, r = row - comp * nrows;
-                const int lz = r / t.R[1], ly = r - lz * t.R[1];
-                int py = reg0[1] + ly, pz = reg0[2] + lz;
-                bool ok = true;
-                if (py < 0 || py >= g.n[1]) { if (g.periodic[1]) py = py < 0 ? py + g.n[1] : py - g.n[1]; else ok = false; }
-                if (pz < 0 || pz >= g.n[2]) { if (g.periodic[2]) pz = pz < 0 ? pz + g.n[2] : pz - g.n[2]; else ok = false; }
-                const float *F = comp < 3 ? f.E + comp * g.ncell : f.B + (comp - 3) * g.ncell;
-                const long long rowbase = ((long long)pz * g.n[1] + py) * g.n[0];
-                for (int lx = lane; lx < Rx; lx += 32) {
-                    int px = reg0[0] + lx;
-                    bool okx = ok;
-                    if (px < 0 || px >= g.n[0]) { if (g.periodic[0]) px = px < 0 ? px + g.n[0] : px - g.n[0]; else okx = false; }
-                    sF[comp * R3 + r * Rx + lx] = okx ? __ldg(F + rowbase + px) : 0.f;
+            for (int l = threadIdx.x; l < R3; l += blockDim.x) {
+                const int lz = l / R2, rem = l - lz * R2, ly = rem / Rx, lx = rem - ly * Rx;
+                long long gi;
+                if (interior) {
+                    gi = gbase + lz * gnxy + ly * gnx + lx;
+                } else {
+                    gi = wrap_node(g, reg0[0] + lx, reg0[1] + ly, reg0[2] + lz);
+                }
+#pragma unroll
+                for (int comp = 0; comp < 3; comp++) {
+                    sF[comp * R3 + l] = gi >= 0 ? __ldg(f.E + comp * g.ncell + gi) : 0.f;
+                    sF[(comp + 3) * R3 + l] = gi >= 0 ? __ldg(f.B + comp * g.ncell + gi) : 0.f;
                 }
             }
         }
@@ -577,26 +603,24 @@ k_push(SpeciesDev sp, GridDev g, TileDev t, FieldsDev f, ExtDev ext, int *work, 
             deposit_general<ORDER>(acc, o, d, s, fac);
         }
         __syncthreads();
-        // one flush of the region's current to global memory (x-rows, coalesced atomics)
-        for (int row = warp; row < 3 * nrows; row += nwarp) {
-            const int comp = row / nrows, r = row - comp * nrows;
-            const int lz = r / t.R[1], ly = r - lz * t.R[1];
-            int py = reg0[1] + ly, pz = reg0[2] + lz;
-            bool ok = true;
-            if (py < 0 || py >= g.n[1]) { if (g.periodic[1]) py = py < 0 ? py + g.n[1] : py - g.n[1]; else ok = false; }
-            if (pz < 0 || pz >= g.n[2]) { if (g.periodic[2]) pz = pz < 0 ? pz + g.n[2] : pz - g.n[2]; else ok = false; }
-            float *Jc = f.J + comp * g.ncell + ((long long)pz * g.n[1] + py) * g.n[0];
-            const float jinv = (float)sp.jinv[comp];
-            for (int lx = lane; lx < Rx; lx += 32) {
-                const int ix = comp * R3 + r * Rx + lx;
-                const long long V = ((long long)sJhi[ix] << kLoBits) + (long long)sJlo[ix];
-                if (V == 0) continue;
-                const float v = (float)V * jinv;
-                int px = reg0[0] + lx;
-                bool okx = ok;
-                if (px < 0 || px >= g.n[0]) { if (g.periodic[0]) px = px < 0 ? px + g.n[0] : px - g.n[0]; else okx = false; }
-                if (!okx) { atomicOr(err, ERR_INDEX); continue; }
-                atomicAdd(Jc + px, v);
+        // one flush of the region's current to global memory: hi 2^19 + lo back to float
+        const float jinv[3] = {(float)sp.jinv[0], (float)sp.jinv[1], (float)sp.jinv[2]};
+        for (int l = threadIdx.x; l < R3; l += blockDim.x) {
+            const int lz = l / R2, rem = l - lz * R2, ly = rem / Rx, lx = rem - ly * Rx;
+            long long gi = -1;
+            bool have = false;
+#pragma unroll
+            for (int comp = 0; comp < 3; comp++) have = have || sJlo[comp * R3 + l] != 0u || sJhi[comp * R3 + l] != 0;
+            if (!have) continue;
+            gi = interior ? gbase + lz * gnxy + ly * gnx + lx : wrap_node(g, reg0[0] + lx, reg0[1] + ly, reg0[2] + lz);
+            if (gi < 0) { atomicOr(err, ERR_INDEX); continue; }
+#pragma unroll
+            for (int comp = 0; comp < 3; comp++) {
+                const unsigned lo = sJlo[comp * R3 + l];
+                const int hi = sJhi[comp * R3 + l];
+                if (lo == 0u && hi == 0) continue;
+                const float v = fmaf((float)hi, (float)(1u << kLoBits), __uint2float_rn(lo)) * jinv[comp];
+                atomicAdd(f.J + comp * g.ncell + gi, v);
             }
         }
     }
@@ -635,7 +659,7 @@ cudaError_t launch_order(pic_ctx *c, int si, const ExtDev &ext)
         RegFix<R, R, R> reg;
         return fr ? launch_t<ORDER, true>(c, si, ext, reg, R * R * R) : launch_t<ORDER, false>(c, si, ext, reg, R * R * R);
     }
-    RegDyn reg{t.R[0], t.R[0] * t.R[1], t.R[0] * t.R[1] * t.R[2]};
+    RegDyn reg{t.R[0], t.R[1], t.R[0] * t.R[1], t.R[0] * t.R[1] * t.R[2]};
     return fr ? launch_t<ORDER, true>(c, si, ext, reg, reg.R3) : launch_t<ORDER, false>(c, si, ext, reg, reg.R3);
 }
 
