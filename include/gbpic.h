@@ -26,8 +26,8 @@
  *    rho at the nodes (i, j, k).
  *  - Every call that launches work enqueues it on the context's stream and returns without
  *    waiting, except the getters, which synchronise that stream.
- *  - Limits: nx, ny <= 1024, nz <= 2048 (cell index packed into 32 bits); fewer than
- *    2^31 particles per species.
+ *  - Limits: nx, ny <= 1024, nz <= 2048 (cell index packed into 32 bits), 8 nx ny nz < 2^31
+ *    (sort keys); fewer than 2^31 particles per species.
  */
 #ifndef GBPIC_H
 #define GBPIC_H
@@ -179,7 +179,9 @@ int pic_step(pic_ctx *ctx, int64_t n);
 /* Wait for the context stream; returns PIC_ERR_DEVICE if a kernel raised the error word. */
 int pic_sync(pic_ctx *ctx);
 
-/* Force a per-tile sort of every species now (the sort also compacts dummy particles). */
+/* Force a per-tile sort of every species now (the sort also compacts dummy particles).  Order:
+ * tiles x-fastest; inside a tile the cells x fastest, then z, then y; inside a cell the octant
+ * of the offset (bit d set when offset_d >= 1/2); order among equal keys unspecified. */
 int pic_sort(pic_ctx *ctx);
 
 /* Copy one grid component (PIC_EX..PIC_JZ; J is the current of the last step) or the charge

@@ -90,7 +90,7 @@ def lib():
                 "oracle_field_transform": (None, [pd, pd, d, pd, pd]),
                 "oracle_lab_to_boosted": (None, [d, pd, pd, pd, pd]),
                 "oracle_boosted_to_lab": (None, [d, pd, d, pd, pd, pd, pd]),
-                "oracle_tile_sort": (None, [l, pl, pi, pi, pl, pl]),
+                "oracle_tile_sort": (None, [l, pd, pi, pi, pl, pl]),
                 "oracle_resonant_wavelength": (d, [d, d, d]),
                 "oracle_doppler_rrf": (d, [d, d]),
                 "oracle_beam_elongation": (d, [d, d]),
@@ -157,15 +157,16 @@ def beam_elongation(gamma_B: float, gamma_R: float) -> float:
     return lib().oracle_beam_elongation(gamma_B, gamma_R)
 
 
-def tile_sort(cells_ijk: np.ndarray, grid, tile):
-    """Stable sort of particles by tile-major cell key; returns (order, keys)."""
-    cells = np.ascontiguousarray(cells_ijk, dtype=np.int64).reshape(-1, 3)
-    n = cells.shape[0]
+def tile_sort(X: np.ndarray, grid, tile):
+    """Stable sort of particles (grid coordinates X, shape (n, 3)) by the tile-major cell +
+    octant key; returns (order, keys)."""
+    Xc = _f64(X).reshape(-1, 3)
+    n = Xc.shape[0]
     order = np.zeros(n, np.int64)
     keys = np.zeros(n, np.int64)
     g = np.ascontiguousarray(grid, dtype=np.int32)
     t = np.ascontiguousarray(tile, dtype=np.int32)
-    lib().oracle_tile_sort(n, _pl(cells), _pi(g), _pi(t), _pl(order), _pl(keys))
+    lib().oracle_tile_sort(n, _pd(Xc), _pi(g), _pi(t), _pl(order), _pl(keys))
     return order, keys
 
 

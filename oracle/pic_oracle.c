@@ -906,15 +906,24 @@ void osim_gather_at(void *h, const double *X, double *EB)
 
 /* ------------------------------------------------------------------ sort */
 
-/* Tile-major key of a cell: tiles of tx*ty*tz cells in x-fastest order, cells inside a
- * tile in x-fastest order.  The sort reorders particles by ascending key; among equal keys
- * the original order is kept (stable), so the result is a plain definition to compare. */
-static long o_tile_key(const int n[3], const int T[3], long i, long j, long k)
+/* Sort key of a particle at grid coordinate X: tiles of tx*ty*tz cells in x-fastest order;
+ * inside a tile the cells in (x fastest, then z, then y) order; inside a cell the octant of
+ * the in-cell offset (bit 0: frac(x) >= 1/2, bit 1: frac(y) >= 1/2, bit 2: frac(z) >= 1/2).
+ * The sort reorders particles by ascending key; among equal keys the original order is kept
+ * (stable), so the result is a plain definition to compare against. */
+static long o_tile_key(const int n[3], const int T[3], const double X[3])
 {
+    long c[3];
+    int oct = 0;
+    for (int d = 0; d < 3; d++) {
+        double fl = floor(X[d]);
+        c[d] = (long)fl;
+        if (X[d] - fl >= 0.5) oct |= 1 << d;
+    }
     long ntx = (n[0] + T[0] - 1) / T[0], nty = (n[1] + T[1] - 1) / T[1];
-    long tile = ((k / T[2]) * nty + (j / T[1])) * ntx + (i / T[0]);
-    long local = ((k % T[2]) * T[1] + (j % T[1])) * T[0] + (i % T[0]);
-    return tile * (long)T[0] * T[1] * T[2] + local;
+    long tile = ((c[2] / T[2]) * nty + (c[1] / T[1])) * ntx + (c[0] / T[0]);
+    long local = ((c[1] % T[1]) * T[2] + (c[2] % T[2])) * T[0] + (c[0] % T[0]);
+    return (tile * (long)T[0] * T[1] * T[2] + local) * 8 + oct;
 }
 
 typedef struct { long key, idx; } o_kv;
@@ -925,12 +934,12 @@ static int o_kv_cmp(const void *a, const void *b)
     return x->idx < y->idx ? -1 : (x->idx > y->idx);
 }
 
-void oracle_tile_sort(long n, const long *cells /*[3n] i,j,k*/, const int *grid3, const int *tile3,
+void oracle_tile_sort(long n, const double *X /*[3n] grid coordinates*/, const int *grid3, const int *tile3,
                       long *order_out, long *keys_out)
 {
     o_kv *kv = (o_kv *)malloc((n > 0 ? n : 1) * sizeof(o_kv));
     for (long p = 0; p < n; p++) {
-        kv[p].key = o_tile_key(grid3, tile3, cells[3 * p], cells[3 * p + 1], cells[3 * p + 2]);
+        kv[p].key = o_tile_key(grid3, tile3, &X[3 * p]);
         kv[p].idx = p;
     }
     qsort(kv, n, sizeof(o_kv), o_kv_cmp);

@@ -121,7 +121,7 @@ void set_tiles(pic_ctx *c)
         c->nt[d] = (c->n[d] + c->T[d] - 1) / c->T[d];
         c->ntiles *= c->nt[d];
     }
-    c->n_keys = (int64_t)c->ntiles * c->T[0] * c->T[1] * c->T[2];
+    c->n_keys = (int64_t)c->ntiles * c->T[0] * c->T[1] * c->T[2] * 8;   // cells x offset octants
 }
 
 int alloc_tile_scratch(pic_ctx *c)
@@ -272,6 +272,7 @@ SpeciesDev species_dev(const pic_ctx *c, const Species &s)
         d.jinv[k] = 1.0 / (double)d.jscale[k];
     }
     d.frozen = s.frozen;
+    d.jz_only = s.frozen && s.jz_only;
     d.cap = (int)s.cap;
     return d;
 }
@@ -311,6 +312,8 @@ int pic_create(pic_ctx **out, pic_grid grid, const double dx[3], double dt, doub
     }
     if (!(dt > 0) || !(dt < 1.0 / std::sqrt(inv2))) return fail(nullptr, PIC_ERR_ARG, "dt must satisfy 0 < dt < Courant limit");
     if (!(gamma_boost >= 1.0)) return fail(nullptr, PIC_ERR_ARG, "gamma_boost must be >= 1");
+    if ((int64_t)n[0] * n[1] * n[2] * 8 >= ((int64_t)1 << 31) - 4096)
+        return fail(nullptr, PIC_ERR_ARG, "grid too large: 8 sort keys per cell must fit in int32");
     bool any_pml = false;
     for (int d = 0; d < 3; d++) {
         for (int f = 0; f < 2; f++) {
@@ -555,6 +558,7 @@ int pic_set_plasma(pic_ctx *c, const pic_plasma *p, int *electron_id, int *ion_i
         for (int i = 0; i < p->n_nodes; i++) nmax = std::max(nmax, std::fabs(p->density[i]));
         const double wm = c->gR * nmax * c->d[0] * c->d[1] * c->d[2] / ((double)c->ppc[0] * c->ppc[1] * c->ppc[2]);
         c->sp[se].wmax = c->sp[si].wmax = wm;
+        c->sp[si].jz_only = 1;   // lab-static ions: u' = (0, 0, -gamma_R beta_R), never pushed
     }
     const double lo = (double)margin_lo(c) + (double)c->shifts + c->bR * (double)c->step * c->dt / c->d[2];
     const int64_t m0 = (int64_t)std::ceil((double)c->ppc[2] * lo - 0.5);
@@ -746,8 +750,11 @@ int pic_get_time(pic_ctx *c, int64_t out[3])
 
 int pic_get_count(pic_ctx *c, int sid, int64_t *n_out)
 {
-    return pic_get_particles(c, sid, std::numeric_limits<int64_t>::max(), n_out, nullptr, nullptr, nullptr,
-                             nullptr, nullptr);
+    int r = check_ctx(c);
+    if (r) return r;
+    if (sid < 0 || sid >= c->nsp || !n_out) return fail(c, PIC_ERR_ARG, "bad species id");
+    CK(species_count_live(c, sid, n_out));
+    return PIC_OK;
 }
 
 int pic_trace_enable(pic_ctx *c, int on)

@@ -15,6 +15,7 @@ namespace gbpic {
 constexpr int kMaxSpecies = 8;
 constexpr int kChunk = 4096;         // particles per work item of the particle kernel
 constexpr int kPushThreads = 512;
+constexpr int kGroup = kChunk / kPushThreads;   // consecutive particles of one lane per work item
 
 // Error bits of the device error word.
 enum : int {
@@ -67,6 +68,7 @@ struct SpeciesDev {
     float h_qm;           // 0.5 (q/m) dt
     float cf[3];          // -q d_c / (dt V): current of unit weight per unit W
     float jscale[3];      // fixed-point scale of the shared-memory current (max contribution 2^38)
+    int jz_only;          // every particle moves along z only: J_x = J_y = 0 (frozen drifting ions)
     double jinv[3];       // 1 / jscale
     int frozen;
     int cap;
@@ -79,7 +81,7 @@ struct TileDev {
     int M;                // allowed drift outside the tile between sorts (cells)
     int hl;               // stencil reach below the particle cell (1 CIC, 2 TSC)
     int R[3];             // shared-memory region size per dim
-    const int *cell_start;   // [n_keys + 1]: first sorted slot of each key
+    const int *cell_start;   // [n_keys + 1]: first sorted slot of each key (8 keys per cell)
     const int2 *items;       // (tile, chunk) work items
 };
 
@@ -103,6 +105,7 @@ struct Species {
     int64_t bound = 0;        // host upper bound of count[0]
     int64_t next_id = 0;
     double wmax = 0;          // largest |weight| ever held (sets the fixed-point current scale)
+    int jz_only = 0;          // frozen with u_x = u_y = 0 for every particle (plasma ions)
 };
 
 }  // namespace gbpic
@@ -194,5 +197,6 @@ cudaError_t launch_inject(pic_ctx *c, int64_t m0, int64_t m1);
 cudaError_t launch_shift_particles(pic_ctx *c, int si);
 cudaError_t launch_moments(pic_ctx *c, int si, int frame, double k, double *out20);
 cudaError_t species_wmax(pic_ctx *c, int si, double *out);
+cudaError_t species_count_live(pic_ctx *c, int si, int64_t *out);
 
 }  // namespace gbpic

@@ -288,6 +288,16 @@ __global__ void k_wmax(SpeciesDev sp, double *partial)
     }
 }
 
+__global__ void k_count_live(SpeciesDev sp, unsigned long long *out)
+{
+    unsigned long long cnt = 0;
+    const int n = sp.count[0];
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x)
+        cnt += __float_as_int(sp.pos[p].w) >= 0;
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(out, cnt);
+}
+
 PlaceP place_params(const pic_ctx *c)
 {
     PlaceP g;
@@ -383,6 +393,21 @@ cudaError_t species_wmax(pic_ctx *c, int si, double *out)
     double m = 0.0;
     for (double v : part) m = std::max(m, v);
     *out = m;
+    return cudaSuccess;
+}
+
+cudaError_t species_count_live(pic_ctx *c, int si, int64_t *out)
+{
+    unsigned long long *d = reinterpret_cast<unsigned long long *>(c->red);
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(unsigned long long), c->stream);
+    if (e != cudaSuccess) return e;
+    k_count_live<<<c->num_sms * 4, 256, 0, c->stream>>>(species_dev(c, c->sp[si]), d);
+    c->kernels++;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    unsigned long long h = 0;
+    if ((e = cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return e;
+    *out = (int64_t)h;
     return cudaSuccess;
 }
 

@@ -1,7 +1,6 @@
 // Counting sort of a species by tile-major cell key (locality for the particle kernel) and
-// construction of its (tile, chunk) work items.  Key of a cell: tiles of Tx*Ty*Tz cells in
-// x-fastest order, cells inside a tile x-fastest; dummy particles get the extra key n_keys
-// and are dropped (compaction).  Histogram with global atomics -> exclusive scan ->
+// construction of its (tile, chunk) work items.  Dummy particles get the extra key n_keys and
+// are dropped (compaction).  Histogram with global atomics -> exclusive scan ->
 // scatter.  The order among particles of one cell is not fixed (atomic ranks).
 #include "gbpic_internal.cuh"
 
@@ -11,20 +10,26 @@ namespace {
 constexpr int kScanThreads = 1024;
 constexpr int kScanSeg = 2 * kScanThreads;
 
-__device__ __forceinline__ int tile_key(int cell, const TileDev &t)
+// Sort key of a particle: tiles in x-fastest order; inside a tile the cells in (x fastest, z,
+// y) order; inside a cell the octant of the offset (bit d set when offset_d >= 1/2).  A warp's
+// 32 consecutive cells then form an 8 x 4 (x, z) block at one y, and the particles of a cold
+// lattice come in the same octant order in every cell.
+__device__ __forceinline__ int tile_key(const float4 &P, const TileDev &t)
 {
+    const int cell = __float_as_int(P.w);
     const int i = cell_i(cell), j = cell_j(cell), k = cell_k(cell);
     const int tile = ((k / t.T[2]) * t.nt[1] + j / t.T[1]) * t.nt[0] + i / t.T[0];
-    const int local = ((k % t.T[2]) * t.T[1] + j % t.T[1]) * t.T[0] + i % t.T[0];
-    return tile * t.tile_cells + local;
+    const int local = ((j % t.T[1]) * t.T[2] + k % t.T[2]) * t.T[0] + i % t.T[0];
+    const int oct = (P.x >= 0.5f) | ((P.y >= 0.5f) << 1) | ((P.z >= 0.5f) << 2);
+    return (tile * t.tile_cells + local) * 8 + oct;
 }
 
 __global__ void k_sort_count(SpeciesDev sp, TileDev t, int n_keys, int *hist, int *rank)
 {
     const int n = sp.count[0];
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-        const int cell = __float_as_int(sp.pos[p].w);
-        const int key = cell < 0 ? n_keys : tile_key(cell, t);
+        const float4 P = sp.pos[p];
+        const int key = __float_as_int(P.w) < 0 ? n_keys : tile_key(P, t);
         rank[p] = atomicAdd(hist + key, 1);
     }
 }
@@ -37,19 +42,19 @@ __global__ void k_sort_scatter(SpeciesDev sp, TileDev t, int n_keys, const int *
         const float4 P = sp.pos[p];
         const int cell = __float_as_int(P.w);
         if (cell < 0) continue;
-        const int dst = start[tile_key(cell, t)] + rank[p];
+        const int dst = start[tile_key(P, t)] + rank[p];
         pos2[dst] = P;
         mom2[dst] = sp.mom[p];
         id2[dst] = sp.id[p];
     }
 }
 
-__global__ void k_tile_chunks(const int *start, int tile_cells, int ntiles, int *chunk_count)
+__global__ void k_tile_chunks(const int *start, int keys_per_tile, int ntiles, int *chunk_count)
 {
     const int tl = blockIdx.x * blockDim.x + threadIdx.x;
     if (tl > ntiles) return;
     if (tl == ntiles) { chunk_count[tl] = 0; return; }
-    const int cnt = start[(tl + 1) * tile_cells] - start[tl * tile_cells];
+    const int cnt = start[(tl + 1) * keys_per_tile] - start[tl * keys_per_tile];
     chunk_count[tl] = (cnt + kChunk - 1) / kChunk;
 }
 
@@ -161,7 +166,7 @@ cudaError_t launch_sort(pic_ctx *c, int si)
     if ((e = exclusive_scan(c, s.cell_start, c->n_keys + 1)) != cudaSuccess) return e;
     k_sort_scatter<<<grid, 256, 0, c->stream>>>(sd, t, n_keys, s.cell_start, s.rank, s.pos2, s.mom2, s.id2);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_tile_chunks<<<(c->ntiles + 1 + 255) / 256, 256, 0, c->stream>>>(s.cell_start, t.tile_cells, c->ntiles,
+    k_tile_chunks<<<(c->ntiles + 1 + 255) / 256, 256, 0, c->stream>>>(s.cell_start, t.tile_cells * 8, c->ntiles,
                                                                        s.chunk_start);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = exclusive_scan(c, s.chunk_start, c->ntiles + 1)) != cudaSuccess) return e;

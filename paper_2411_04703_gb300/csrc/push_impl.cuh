@@ -29,8 +29,12 @@ namespace push {
 constexpr int kQueue = 384;   // queued crossing particles per work item (overflow: inline)
 
 // ------------------------------------------------------------------ region geometry
+// The z-plane pitch is padded to 8 (mod 32) words: the 8 x 4 (x, z) cells a warp works on then
+// start in 32 different shared-memory banks.
+__host__ __device__ constexpr int plane_pitch(int rx, int ry) { return rx * ry + (((8 - (rx * ry) % 32) % 32) + 32) % 32; }
+
 struct RegDyn {
-    int Rx, Ry, R2, R3;
+    int Rx, Ry, R2, R3;   // R2: padded plane pitch; R3 = R2 * Rz
     __device__ __forceinline__ int rx() const { return Rx; }
     __device__ __forceinline__ int ry() const { return Ry; }
     __device__ __forceinline__ int r2() const { return R2; }
@@ -39,8 +43,8 @@ struct RegDyn {
 template <int RX, int RY, int RZ> struct RegFix {
     __device__ __forceinline__ static constexpr int rx() { return RX; }
     __device__ __forceinline__ static constexpr int ry() { return RY; }
-    __device__ __forceinline__ static constexpr int r2() { return RX * RY; }
-    __device__ __forceinline__ static constexpr int r3() { return RX * RY * RZ; }
+    __device__ __forceinline__ static constexpr int r2() { return plane_pitch(RX, RY); }
+    __device__ __forceinline__ static constexpr int r3() { return plane_pitch(RX, RY) * RZ; }
 };
 
 // ------------------------------------------------------------------ shape weights
@@ -491,13 +495,13 @@ k_push(SpeciesDev sp, GridDev g, TileDev t, FieldsDev f, ExtDev ext, int *work, 
         const int tx = tile % t.nt[0], ty = (tile / t.nt[0]) % t.nt[1], tz = tile / (t.nt[0] * t.nt[1]);
         const int t0[3] = {tx * t.T[0], ty * t.T[1], tz * t.T[2]};
         const int reg0[3] = {t0[0] - t.M - t.hl, t0[1] - t.M - t.hl, t0[2] - t.M - t.hl};
-        const int key0 = tile * t.tile_cells;
+        const int key0 = tile * t.tile_cells * 8;
         const int p_begin = t.cell_start[key0] + wi.y * kChunk;
-        const int p_end = min(p_begin + kChunk, t.cell_start[key0 + t.tile_cells]);
+        const int p_end = min(p_begin + kChunk, t.cell_start[key0 + t.tile_cells * 8]);
         // Region of the tile: nodes reg0 + (0..R-1) per dim.  A tile away from every face needs
         // no wrap or bounds test; the loops run over the region's nodes with compile-time
         // divisions (fixed region) and each thread moves all components of its node.
-        const int R2 = reg.r2(), Ry = reg.ry(), Rz = R3 / R2;
+        const int R2 = reg.r2(), Ry = reg.ry(), Rz = R3 / R2;   // R2 padded
         const bool interior = reg0[0] >= 0 && reg0[0] + Rx <= g.n[0] && reg0[1] >= 0 && reg0[1] + Ry <= g.n[1] &&
                               reg0[2] >= 0 && reg0[2] + Rz <= g.n[2];
         const long long gnx = g.n[0], gnxy = (long long)g.n[0] * g.n[1];
@@ -505,6 +509,7 @@ k_push(SpeciesDev sp, GridDev g, TileDev t, FieldsDev f, ExtDev ext, int *work, 
         if (!FROZEN) {
             for (int l = threadIdx.x; l < R3; l += blockDim.x) {
                 const int lz = l / R2, rem = l - lz * R2, ly = rem / Rx, lx = rem - ly * Rx;
+                if (ly >= Ry) continue;   // plane padding
                 long long gi;
                 if (interior) {
                     gi = gbase + lz * gnxy + ly * gnx + lx;
@@ -518,16 +523,18 @@ k_push(SpeciesDev sp, GridDev g, TileDev t, FieldsDev f, ExtDev ext, int *work, 
                 }
             }
         }
-        for (int l = threadIdx.x; l < 3 * R3; l += blockDim.x) {
+        const int c0 = sp.jz_only ? 2 : 0;   // first current component the species can touch
+        for (int l = threadIdx.x + c0 * R3; l < 3 * R3; l += blockDim.x) {
             sJlo[l] = 0u;
             sJhi[l] = 0;
         }
         if (threadIdx.x == 0) s_qn = 0;
         __syncthreads();
-        // lanes of a warp take particles G apart (one cell apart for a sorted plasma), so a
-        // warp's shared atomics rarely hit the same address
+        // each lane takes kGroup = 8 consecutive particles: one cell of an 8-per-cell lattice,
+        // visited in octant order, so at every iteration the warp's 32 lanes sit on 32
+        // different cells with the same stencil shift (bank-conflict-free shared accesses)
         const int len = p_end - p_begin;
-        const int G = (len + nwarp * 32 - 1) / (nwarp * 32);
+        constexpr int G = kGroup;
         for (int k_it = 0; k_it < G; k_it++) {
             const int q = (warp * 32 + lane) * G + k_it;
             if (q >= len) continue;
@@ -554,7 +561,7 @@ k_push(SpeciesDev sp, GridDev g, TileDev t, FieldsDev f, ExtDev ext, int *work, 
             }
             float4 mo = sp.mom[p];
             const float o[3] = {P.x, P.y, P.z};
-            const int base = ((rel[2] + t.M + t.hl) * t.R[1] + rel[1] + t.M + t.hl) * Rx + rel[0] + t.M + t.hl;
+            const int base = (rel[2] + t.M + t.hl) * reg.r2() + (rel[1] + t.M + t.hl) * Rx + rel[0] + t.M + t.hl;
             SmemAcc<Reg> acc{reg, sF, sJlo, sJhi, {js[0], js[1], js[2]}, base};
             float d[3], o1[3];
             int s[3];
@@ -607,15 +614,14 @@ k_push(SpeciesDev sp, GridDev g, TileDev t, FieldsDev f, ExtDev ext, int *work, 
         const float jinv[3] = {(float)sp.jinv[0], (float)sp.jinv[1], (float)sp.jinv[2]};
         for (int l = threadIdx.x; l < R3; l += blockDim.x) {
             const int lz = l / R2, rem = l - lz * R2, ly = rem / Rx, lx = rem - ly * Rx;
+            if (ly >= Ry) continue;   // plane padding (never written by a particle)
             long long gi = -1;
             bool have = false;
-#pragma unroll
-            for (int comp = 0; comp < 3; comp++) have = have || sJlo[comp * R3 + l] != 0u || sJhi[comp * R3 + l] != 0;
+            for (int comp = c0; comp < 3; comp++) have = have || sJlo[comp * R3 + l] != 0u || sJhi[comp * R3 + l] != 0;
             if (!have) continue;
             gi = interior ? gbase + lz * gnxy + ly * gnx + lx : wrap_node(g, reg0[0] + lx, reg0[1] + ly, reg0[2] + lz);
             if (gi < 0) { atomicOr(err, ERR_INDEX); continue; }
-#pragma unroll
-            for (int comp = 0; comp < 3; comp++) {
+            for (int comp = c0; comp < 3; comp++) {
                 const unsigned lo = sJlo[comp * R3 + l];
                 const int hi = sJhi[comp * R3 + l];
                 if (lo == 0u && hi == 0) continue;
@@ -657,9 +663,11 @@ cudaError_t launch_order(pic_ctx *c, int si, const ExtDev &ext)
     const TileDev t = tile_dev(c, c->sp[si]);
     if (c->T[0] == 8 && c->T[1] == 8 && c->T[2] == 8 && c->M == 1) {
         RegFix<R, R, R> reg;
-        return fr ? launch_t<ORDER, true>(c, si, ext, reg, R * R * R) : launch_t<ORDER, false>(c, si, ext, reg, R * R * R);
+        constexpr int R3 = plane_pitch(R, R) * R;
+        return fr ? launch_t<ORDER, true>(c, si, ext, reg, R3) : launch_t<ORDER, false>(c, si, ext, reg, R3);
     }
-    RegDyn reg{t.R[0], t.R[1], t.R[0] * t.R[1], t.R[0] * t.R[1] * t.R[2]};
+    const int P2 = plane_pitch(t.R[0], t.R[1]);
+    RegDyn reg{t.R[0], t.R[1], P2, P2 * t.R[2]};
     return fr ? launch_t<ORDER, true>(c, si, ext, reg, reg.R3) : launch_t<ORDER, false>(c, si, ext, reg, reg.R3);
 }
 

@@ -147,8 +147,8 @@ def test_tile_sort_is_bit_exact():
     sim.sort()
     for name, sid in ids.items():
         P = sim.get_particles(sid)
-        cells = P["cell"].astype(np.int64)
-        order, keys = oracle.tile_sort(cells, w.grid, w.tile)
+        X = P["cell"].astype(np.float64) + P["off"].astype(np.float64)
+        order, keys = oracle.tile_sort(X, w.grid, w.tile)
         # storage order after the sort is by ascending tile-major key
         gk = keys[np.argsort(order)]
         assert np.all(np.diff(gk) >= 0), name

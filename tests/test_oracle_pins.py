@@ -450,16 +450,25 @@ def test_moments_definitions():
     assert m["count"] == n
 
 
-def test_tile_sort_groups_tiles_and_cells():
+def test_tile_sort_groups_tiles_cells_and_octants():
     rng = np.random.default_rng(8)
     grid, tile = (20, 18, 44), (8, 8, 8)
-    cells = np.stack([rng.integers(0, g, 5000) for g in grid], 1)
-    order, keys = oracle.tile_sort(cells, grid, tile)
+    X = np.stack([rng.uniform(0, g, 5000) for g in grid], 1)
+    order, keys = oracle.tile_sort(X, grid, tile)
     assert sorted(order.tolist()) == list(range(5000))
     assert np.all(np.diff(keys) >= 0)
-    c = cells[order]
+    c = np.floor(X[order]).astype(int)
     t = (c[:, 2] // 8 * 3 + c[:, 1] // 8) * 3 + c[:, 0] // 8
-    assert np.all(np.diff(t) >= 0)
+    assert np.all(np.diff(t) >= 0)                       # tiles contiguous, in order
+    # inside a tile: x fastest, then z, then y
+    loc = ((c[:, 1] % 8) * 8 + c[:, 2] % 8) * 8 + c[:, 0] % 8
+    same_tile = np.diff(t) == 0
+    assert np.all(np.diff(loc)[same_tile] >= 0)
+    # inside a cell: ascending octant of the offset
+    frac = X[order] - np.floor(X[order])
+    octant = (frac[:, 0] >= 0.5) + 2 * (frac[:, 1] >= 0.5) + 4 * (frac[:, 2] >= 0.5)
+    same_cell = same_tile & (np.diff(loc) == 0)
+    assert np.all(np.diff(octant)[same_cell] >= 0)
     same = np.diff(keys) == 0
     assert np.all(np.diff(order)[same] > 0)           # stable among equal keys
-    assert np.all((np.diff(c, axis=0) == 0).all(1) == same)
+    assert np.all(same == (same_cell & (np.diff(octant) == 0)))
