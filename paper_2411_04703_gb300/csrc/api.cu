@@ -265,9 +265,11 @@ SpeciesDev species_dev(const pic_ctx *c, const Species &s)
     const double V = c->d[0] * c->d[1] * c->d[2];
     for (int k = 0; k < 3; k++) {
         d.cf[k] = (float)(-s.q * c->d[k] / (c->dt * V));
-        // |contribution| <= |cf| w |prefix DS| |A A + DS DS/12| <= 1.1 |cf| wmax: map it to 2^38
-        const double mx = 1.1 * std::fabs((double)d.cf[k]) * s.wmax;
-        const double sc = mx > 0 ? std::ldexp(1.0, 38) / mx : 1.0;
+        // |contribution| <= |cf| w |prefix DS| |A A + DS DS/12|; |prefix DS| <= the displacement
+        // bound min(1, dt/d_k) (speed of light) and |A A + DS DS/12| <= 1.1: map it to 2^30
+        const double pmax = std::min(1.0, c->dt / c->d[k]);
+        const double mx = 1.1 * std::fabs((double)d.cf[k]) * s.wmax * pmax;
+        const double sc = mx > 0 ? std::ldexp(1.0, 30) / mx : 1.0;
         d.jscale[k] = (float)sc;
         d.jinv[k] = 1.0 / (double)d.jscale[k];
     }

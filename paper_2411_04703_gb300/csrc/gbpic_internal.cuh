@@ -67,7 +67,7 @@ struct SpeciesDev {
     int *count;           // [0] total slots in use, [1] sorted prefix, [2] tile work items
     float h_qm;           // 0.5 (q/m) dt
     float cf[3];          // -q d_c / (dt V): current of unit weight per unit W
-    float jscale[3];      // fixed-point scale of the shared-memory current (max contribution 2^38)
+    float jscale[3];      // fixed-point scale of the shared-memory current (max contribution 2^30)
     int jz_only;          // every particle moves along z only: J_x = J_y = 0 (frozen drifting ions)
     double jinv[3];       // 1 / jscale
     int frozen;

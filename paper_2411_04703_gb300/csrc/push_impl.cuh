@@ -163,10 +163,11 @@ template <> struct Shape<2> {
 //
 // The region's current is accumulated as exact fixed point with native 32-bit integer shared
 // atomics (a float add on shared memory is not a native atomic): a contribution v becomes
-// V = round(v * jscale) with |V| <= 2^38 for the largest possible contribution of the species,
-// split into 19 low bits (unsigned word) and the rest (signed word).  A work item holds at most
+// V = round(v * jscale), an int32 with |V| <= 2^30 for the largest possible contribution of the
+// species (weight, charge and the speed-of-light bound of the displacement per step), split into
+// its 19 low bits (unsigned word) and the rest (signed word).  A work item holds at most
 // kChunk = 4096 particles, each adding at most once per node and component, so neither word
-// overflows; the flush recombines hi * 2^19 + lo exactly in 64-bit integers.
+// overflows; the flush recombines hi * 2^19 + lo.
 constexpr int kLoBits = 19;
 constexpr unsigned kLoMask = (1u << kLoBits) - 1u;
 static_assert(kChunk <= 4096, "fixed-point current words sized for 4096 contributions per node");
@@ -182,14 +183,12 @@ template <class Reg> struct SmemAcc {
     __device__ __forceinline__ float f(int comp, int x, int y, int z) const {
         return sF[comp * reg.r3() + base + z * reg.r2() + y * reg.rx() + x];
     }
-    // v is already in fixed-point units (times scale(comp)); split with 32-bit conversions:
-    // hi = floor(v / 2^19), lo = v - hi 2^19 in [0, 2^19] (the FMA difference is exact)
+    // v is already in fixed-point units (times scale(comp)), |v| <= 2^30
     __device__ __forceinline__ void j(int comp, int x, int y, int z, float v) const {
         const int ix = comp * reg.r3() + base + z * reg.r2() + y * reg.rx() + x;
-        const float hf = floorf(v * (1.f / (float)(1u << kLoBits)));
-        const float lf = fmaf(-hf, (float)(1u << kLoBits), v);
-        atomicAdd(&sJlo[ix], __float2uint_rn(lf));
-        atomicAdd(&sJhi[ix], (int)hf);
+        const int V = __float2int_rn(v);
+        atomicAdd(&sJlo[ix], (unsigned)V & kLoMask);
+        atomicAdd(&sJhi[ix], V >> kLoBits);
     }
 };
 
@@ -251,7 +250,7 @@ __device__ __forceinline__ float gather(const Acc &a, int comp, int sx, int sy, 
 // written as DS_c [A_a A_b + DS_a DS_b / 12] with A = S0 + DS/2, and J_c(node + 1/2) =
 // -q w (d_c/dt) (sum of W_c over the nodes up to this one) / V; the prefix over the last window
 // node vanishes (sum DS = 0) and is not stored.  fac = -q w d_c/(dt V).
-template <int L, class Acc>
+template <int L, bool TEST_ZERO, class Acc>
 __device__ __forceinline__ void esirkepov(const Acc &acc, const int st[3], const float S0[3][L],
                                           const float DS[3][L], const float fac[3], bool skip_x, bool skip_y)
 {
@@ -280,10 +279,10 @@ __device__ __forceinline__ void esirkepov(const Acc &acc, const int st[3], const
 #pragma unroll
             for (int j = 0; j < L; j++) {
                 const float Y = fmaf(A[1][j], A[2][k], Q[1][j] * DS[2][k]);
-                if (Y == 0.f) continue;
+                if (TEST_ZERO && Y == 0.f) continue;
 #pragma unroll
                 for (int i = 0; i < L - 1; i++)
-                    if (P[0][i] != 0.f) acc.j(0, st[0] + i, st[1] + j, st[2] + k, P[0][i] * Y);
+                    if (!TEST_ZERO || P[0][i] != 0.f) acc.j(0, st[0] + i, st[1] + j, st[2] + k, P[0][i] * Y);
             }
     }
     if (!skip_y) {
@@ -292,10 +291,10 @@ __device__ __forceinline__ void esirkepov(const Acc &acc, const int st[3], const
 #pragma unroll
             for (int i = 0; i < L; i++) {
                 const float Y = fmaf(A[2][k], A[0][i], Q[2][k] * DS[0][i]);
-                if (Y == 0.f) continue;
+                if (TEST_ZERO && Y == 0.f) continue;
 #pragma unroll
                 for (int j = 0; j < L - 1; j++)
-                    if (P[1][j] != 0.f) acc.j(1, st[0] + i, st[1] + j, st[2] + k, P[1][j] * Y);
+                    if (!TEST_ZERO || P[1][j] != 0.f) acc.j(1, st[0] + i, st[1] + j, st[2] + k, P[1][j] * Y);
             }
     }
 #pragma unroll
@@ -303,10 +302,10 @@ __device__ __forceinline__ void esirkepov(const Acc &acc, const int st[3], const
 #pragma unroll
         for (int i = 0; i < L; i++) {
             const float Y = fmaf(A[0][i], A[1][j], Q[0][i] * DS[1][j]);
-            if (Y == 0.f) continue;
+            if (TEST_ZERO && Y == 0.f) continue;
 #pragma unroll
             for (int k = 0; k < L - 1; k++)
-                if (P[2][k] != 0.f) acc.j(2, st[0] + i, st[1] + j, st[2] + k, P[2][k] * Y);
+                if (!TEST_ZERO || P[2][k] != 0.f) acc.j(2, st[0] + i, st[1] + j, st[2] + k, P[2][k] * Y);
         }
 }
 
@@ -321,7 +320,7 @@ __device__ __forceinline__ void deposit_general(const Acc &acc, const float o[3]
     float S0[3][L], DS[3][L];
 #pragma unroll
     for (int dd = 0; dd < 3; dd++) S::general(o[dd], d[dd], s[dd], st[dd], S0[dd], DS[dd]);
-    esirkepov<L>(acc, st, S0, DS, fac, d[0] == 0.f, d[1] == 0.f);
+    esirkepov<L, true>(acc, st, S0, DS, fac, d[0] == 0.f, d[1] == 0.f);
 }
 
 // Nearest node / cell unchanged in every dimension: window of order+1 nodes.
@@ -335,7 +334,7 @@ __device__ __forceinline__ void deposit_simple(const Acc &acc, const float o[3],
     float S0[3][L], DS[3][L];
 #pragma unroll
     for (int dd = 0; dd < 3; dd++) S::simple(o[dd], d[dd], st[dd], S0[dd], DS[dd]);
-    esirkepov<L>(acc, st, S0, DS, fac, d[0] == 0.f, d[1] == 0.f);
+    esirkepov<L, false>(acc, st, S0, DS, fac, d[0] == 0.f, d[1] == 0.f);
 }
 
 // Gather, external field, Boris push and move of one particle.  On return d holds the push
