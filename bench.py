@@ -264,13 +264,15 @@ def run_gbpic(args):
         sim2.sync()
         barrier()
         torch.cuda.synchronize()
+        ne_plasma0 = sim2.get_count(ids2["plasma_e"])
         t0 = time.perf_counter()
         b = w.beam
         sb = sim2.load_species(b.q, b.m, xh, uh, wh, frame=api.PIC_FRAME_LAB, origin=b.origin)
-        ne0 = sim2.get_count(sb) + sim2.get_count(ids2["plasma_e"])
         sim2.step(args.steps)
         mom = sim2.get_moments(sb, api.PIC_FRAME_LAB, k_bunch=0.0)
         t_e2e = time.perf_counter() - t0
+        # particle counts for the metric, read outside the timed region
+        ne0 = sim2.get_count(sb) + ne_plasma0
         ne1 = int(mom["count"]) + sim2.get_count(ids2["plasma_e"])
         barrier()
         h2d = (xh.numel() + uh.numel() + wh.numel()) * 8

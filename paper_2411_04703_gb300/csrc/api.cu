@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <limits>
 
@@ -380,7 +381,7 @@ int pic_create(pic_ctx **out, pic_grid grid, const double dx[3], double dt, doub
     int r;
     if ((r = alloc_zero(c, &c->E, 3 * c->ncell)) || (r = alloc_zero(c, &c->B, 3 * c->ncell)) ||
         (r = alloc_zero(c, &c->J, 3 * c->ncell)) || (r = alloc_zero(c, &c->err, 4)) ||
-        (r = alloc_zero(c, &c->work, kMaxSpecies)) || (r = alloc_zero(c, &c->red, 512 * 16 + 1024)) ||
+        (r = alloc_zero(c, &c->work, 2 * kMaxSpecies)) || (r = alloc_zero(c, &c->red, 512 * 16 + 1024)) ||
         (r = alloc_zero(c, &c->shift_tab, 24)) || (r = alloc_tile_scratch(c)))
         return bail(r);
     if (any_pml) {
@@ -585,7 +586,7 @@ int pic_step(pic_ctx *c, int64_t nsteps)
             for (int si = 0; si < c->nsp; si++) CK(launch_sort(c, si));
         }
         CK(cudaMemsetAsync(c->J, 0, sizeof(float) * 3 * c->ncell, c->stream));
-        CK(cudaMemsetAsync(c->work, 0, sizeof(int) * kMaxSpecies, c->stream));
+        CK(cudaMemsetAsync(c->work, 0, sizeof(int) * 2 * kMaxSpecies, c->stream));
         const ExtDev ext = ext_step(c);
         for (int si = 0; si < c->nsp; si++) {
             TraceScope ts(c, c->sp[si].frozen ? TR_PUSH_FROZEN : TR_PUSH);

@@ -152,7 +152,7 @@ struct pic_ctx {
     int64_t step = 0, shifts = 0, m_last = -1;
     // bookkeeping
     int *err = nullptr;           // device error word
-    int *work = nullptr;          // device work counters [kMaxSpecies]
+    int *work = nullptr;          // device work counters [2 * kMaxSpecies]
     double *red = nullptr;        // reduction partials
     double *red_out = nullptr;
     int nsp = 0;

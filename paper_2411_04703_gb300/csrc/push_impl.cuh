@@ -29,9 +29,11 @@ namespace push {
 constexpr int kQueue = 384;   // queued crossing particles per work item (overflow: inline)
 
 // ------------------------------------------------------------------ region geometry
-// The z-plane pitch is padded to 8 (mod 32) words: the 8 x 4 (x, z) cells a warp works on then
-// start in 32 different shared-memory banks.
-__host__ __device__ constexpr int plane_pitch(int rx, int ry) { return rx * ry + (((8 - (rx * ry) % 32) % 32) + 32) % 32; }
+// The z-plane pitch is padded to 4 (mod 16) words.  The 32 lanes of a warp work on cells 16
+// apart in the tile's (x, z, y) order, i.e. the same x, z = z0 + 2b (b < 4) and y = y0 + a
+// (a < 8); their words then sit at Rx a + 2 pitch b = Rx a + 8 b (mod 32), which with an odd
+// region width Rx are 32 different banks.
+__host__ __device__ constexpr int plane_pitch(int rx, int ry) { return rx * ry + (((4 - (rx * ry) % 16) % 16) + 16) % 16; }
 
 struct RegDyn {
     int Rx, Ry, R2, R3;   // R2: padded plane pitch; R3 = R2 * Rz
@@ -337,58 +339,62 @@ __device__ __forceinline__ void deposit_simple(const Acc &acc, const float o[3],
     esirkepov<L, false>(acc, st, S0, DS, fac, d[0] == 0.f, d[1] == 0.f);
 }
 
-// Gather, external field, Boris push and move of one particle.  On return d holds the push
-// displacement (cells), s the cell shift, o1 the new offsets and c the new cell.  Returns false
-// when the particle left through a non-periodic face (it becomes a dummy particle).
+// Gather, external field and Boris rotation of one particle: u^{n-1/2} -> u^{n+1/2} in mo.
+template <int ORDER, class Acc>
+__device__ __forceinline__ void push_u(const Acc &acc, const float o[3], const int c[3], float4 &mo,
+                                       const SpeciesDev &sp, const ExtDev &ext)
+{
+    using S = Shape<ORDER>;
+    constexpr int N = S::N;
+    int su[3], ss[3];
+    float wu[3][N], ws[3][N];
+#pragma unroll
+    for (int dd = 0; dd < 3; dd++) { S::unst(o[dd], su[dd], wu[dd]); S::stag(o[dd], ss[dd], ws[dd]); }
+    float E[3], B[3];
+    E[0] = gather<N>(acc, 0, ss[0], su[1], su[2], ws[0], wu[1], wu[2]);
+    E[1] = gather<N>(acc, 1, su[0], ss[1], su[2], wu[0], ws[1], wu[2]);
+    E[2] = gather<N>(acc, 2, su[0], su[1], ss[2], wu[0], wu[1], ws[2]);
+    B[0] = gather<N>(acc, 3, su[0], ss[1], ss[2], wu[0], ws[1], ws[2]);
+    B[1] = gather<N>(acc, 4, ss[0], su[1], ss[2], ws[0], wu[1], ws[2]);
+    B[2] = gather<N>(acc, 5, ss[0], ss[1], su[2], ws[0], ws[1], wu[2]);
+    if (ext.type == PIC_EXT_PLANAR_UNDULATOR) {
+        float f = 1.f;
+        if (ext.ramp_mode) {
+            const float r = fmaf(ext.ramp_a, (float)c[2] + o[2], ext.ramp_b);
+            f = ext.ramp_mode == 1 ? fminf(fmaxf(r, 0.f), 1.f) : (r >= 0.f ? 1.f : 0.f);
+        }
+        const float ph = ext.phase_tab[c[2]] + fmaf(ext.kdz, o[2], ext.theta);
+        const float By = ext.B0g * f * cosf(ph);
+        B[1] += By;
+        E[0] -= ext.beta_R * By;
+    }
+    const float h = sp.h_qm;
+    float um[3];
+#pragma unroll
+    for (int dd = 0; dd < 3; dd++) um[dd] = fmaf(h, E[dd], dd == 0 ? mo.x : (dd == 1 ? mo.y : mo.z));
+    const float ig = rsqrtf(1.f + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
+    float t[3];
+#pragma unroll
+    for (int dd = 0; dd < 3; dd++) t[dd] = h * B[dd] * ig;
+    const float s2 = 2.f / (1.f + t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+    const float up[3] = {um[0] + um[1] * t[2] - um[2] * t[1], um[1] + um[2] * t[0] - um[0] * t[2],
+                         um[2] + um[0] * t[1] - um[1] * t[0]};
+    const float sv[3] = {s2 * t[0], s2 * t[1], s2 * t[2]};
+    mo.x = um[0] + up[1] * sv[2] - up[2] * sv[1] + h * E[0];
+    mo.y = um[1] + up[2] * sv[0] - up[0] * sv[2] + h * E[1];
+    mo.z = um[2] + up[0] * sv[1] - up[1] * sv[0] + h * E[2];
+}
+
+// Gather, external field, Boris push (unless FROZEN) and move of one particle.  On return d
+// holds the push displacement (cells), s the cell shift, o1 the new offsets and c the new cell.
+// Returns false when the particle left through a non-periodic face (it becomes a dummy).
 template <int ORDER, bool FROZEN, class Acc>
 __device__ __forceinline__ bool push_move(const Acc &acc, const float o[3], int c[3], float4 &mo,
                                           const SpeciesDev &sp, const GridDev &g, const ExtDev &ext,
                                           int *err, float d[3], int s[3], float o1[3])
 {
-    using S = Shape<ORDER>;
-    constexpr int N = S::N;
-    float u[3] = {mo.x, mo.y, mo.z};
-    if (!FROZEN) {
-        int su[3], ss[3];
-        float wu[3][N], ws[3][N];
-#pragma unroll
-        for (int dd = 0; dd < 3; dd++) { S::unst(o[dd], su[dd], wu[dd]); S::stag(o[dd], ss[dd], ws[dd]); }
-        float E[3], B[3];
-        E[0] = gather<N>(acc, 0, ss[0], su[1], su[2], ws[0], wu[1], wu[2]);
-        E[1] = gather<N>(acc, 1, su[0], ss[1], su[2], wu[0], ws[1], wu[2]);
-        E[2] = gather<N>(acc, 2, su[0], su[1], ss[2], wu[0], wu[1], ws[2]);
-        B[0] = gather<N>(acc, 3, su[0], ss[1], ss[2], wu[0], ws[1], ws[2]);
-        B[1] = gather<N>(acc, 4, ss[0], su[1], ss[2], ws[0], wu[1], ws[2]);
-        B[2] = gather<N>(acc, 5, ss[0], ss[1], su[2], ws[0], ws[1], wu[2]);
-        if (ext.type == PIC_EXT_PLANAR_UNDULATOR) {
-            float f = 1.f;
-            if (ext.ramp_mode) {
-                const float r = fmaf(ext.ramp_a, (float)c[2] + o[2], ext.ramp_b);
-                f = ext.ramp_mode == 1 ? fminf(fmaxf(r, 0.f), 1.f) : (r >= 0.f ? 1.f : 0.f);
-            }
-            const float ph = ext.phase_tab[c[2]] + fmaf(ext.kdz, o[2], ext.theta);
-            const float By = ext.B0g * f * cosf(ph);
-            B[1] += By;
-            E[0] -= ext.beta_R * By;
-        }
-        // Boris rotation
-        const float h = sp.h_qm;
-        float um[3];
-#pragma unroll
-        for (int dd = 0; dd < 3; dd++) um[dd] = fmaf(h, E[dd], u[dd]);
-        const float ig = rsqrtf(1.f + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
-        float t[3];
-#pragma unroll
-        for (int dd = 0; dd < 3; dd++) t[dd] = h * B[dd] * ig;
-        const float s2 = 2.f / (1.f + t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
-        const float up[3] = {um[0] + um[1] * t[2] - um[2] * t[1], um[1] + um[2] * t[0] - um[0] * t[2],
-                             um[2] + um[0] * t[1] - um[1] * t[0]};
-        const float sv[3] = {s2 * t[0], s2 * t[1], s2 * t[2]};
-        u[0] = um[0] + up[1] * sv[2] - up[2] * sv[1] + h * E[0];
-        u[1] = um[1] + up[2] * sv[0] - up[0] * sv[2] + h * E[1];
-        u[2] = um[2] + up[0] * sv[1] - up[1] * sv[0] + h * E[2];
-        mo.x = u[0]; mo.y = u[1]; mo.z = u[2];
-    }
+    if (!FROZEN) push_u<ORDER>(acc, o, c, mo, sp, ext);
+    const float u[3] = {mo.x, mo.y, mo.z};
     const float ig = rsqrtf(1.f + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
     if (!(ig > 0.f)) { atomicOr(err, ERR_NAN); return false; }
     bool alive = true;
@@ -444,6 +450,31 @@ __device__ __forceinline__ void step_global(const SpeciesDev &sp, const GridDev 
 }
 
 // Linear index of grid node (x, y, z) with periodic wrap, or -1 outside a non-periodic face.
+__device__ __forceinline__ long long wrap_node(const GridDev &g, int x, int y, int z);
+
+// Stage the six field components of a tile's region in shared memory.  A tile away from every
+// face needs no wrap or bounds test; the loop runs over the region's nodes with compile-time
+// divisions (fixed region) and each thread moves all components of its node.
+template <class Reg>
+__device__ __forceinline__ void stage_fields(const Reg &reg, const GridDev &g, const FieldsDev &f, float *sF,
+                                             const int reg0[3], bool interior, long long gbase)
+{
+    const int Rx = reg.rx(), Ry = reg.ry(), R2 = reg.r2(), R3 = reg.r3();
+    const long long gnx = g.n[0], gnxy = (long long)g.n[0] * g.n[1];
+    for (int l = threadIdx.x; l < R3; l += blockDim.x) {
+        const int lz = l / R2, rem = l - lz * R2, ly = rem / Rx, lx = rem - ly * Rx;
+        if (ly >= Ry) continue;   // plane padding
+        const long long gi = interior ? gbase + lz * gnxy + ly * gnx + lx
+                                      : wrap_node(g, reg0[0] + lx, reg0[1] + ly, reg0[2] + lz);
+#pragma unroll
+        for (int comp = 0; comp < 3; comp++) {
+            sF[comp * R3 + l] = gi >= 0 ? __ldg(f.E + comp * g.ncell + gi) : 0.f;
+            sF[(comp + 3) * R3 + l] = gi >= 0 ? __ldg(f.B + comp * g.ncell + gi) : 0.f;
+        }
+    }
+}
+
+
 __device__ __forceinline__ long long wrap_node(const GridDev &g, int x, int y, int z)
 {
     int p[3] = {x, y, z};
@@ -457,8 +488,10 @@ __device__ __forceinline__ long long wrap_node(const GridDev &g, int x, int y, i
     return ((long long)p[2] * g.n[1] + p[1]) * g.n[0] + p[0];
 }
 
+// The deposit-only instantiation (frozen species) is held to two CTAs per SM (its smaller
+// shared region allows it; measured faster for the drifting ions despite a few spills).
 template <int ORDER, bool FROZEN, class Reg>
-__global__ void __launch_bounds__(kPushThreads)
+__global__ void __launch_bounds__(kPushThreads, FROZEN ? 2 : 1)
 k_push(SpeciesDev sp, GridDev g, TileDev t, FieldsDev f, ExtDev ext, int *work, int *err, Reg reg)
 {
     extern __shared__ float smem[];
@@ -497,31 +530,13 @@ k_push(SpeciesDev sp, GridDev g, TileDev t, FieldsDev f, ExtDev ext, int *work, 
         const int key0 = tile * t.tile_cells * 8;
         const int p_begin = t.cell_start[key0] + wi.y * kChunk;
         const int p_end = min(p_begin + kChunk, t.cell_start[key0 + t.tile_cells * 8]);
-        // Region of the tile: nodes reg0 + (0..R-1) per dim.  A tile away from every face needs
-        // no wrap or bounds test; the loops run over the region's nodes with compile-time
-        // divisions (fixed region) and each thread moves all components of its node.
-        const int R2 = reg.r2(), Ry = reg.ry(), Rz = R3 / R2;   // R2 padded
+        // Region of the tile: nodes reg0 + (0..R-1) per dim (plane pitch padded).
+        const int R2 = reg.r2(), Ry = reg.ry(), Rz = R3 / R2;
         const bool interior = reg0[0] >= 0 && reg0[0] + Rx <= g.n[0] && reg0[1] >= 0 && reg0[1] + Ry <= g.n[1] &&
                               reg0[2] >= 0 && reg0[2] + Rz <= g.n[2];
         const long long gnx = g.n[0], gnxy = (long long)g.n[0] * g.n[1];
         const long long gbase = reg0[2] * gnxy + reg0[1] * gnx + reg0[0];
-        if (!FROZEN) {
-            for (int l = threadIdx.x; l < R3; l += blockDim.x) {
-                const int lz = l / R2, rem = l - lz * R2, ly = rem / Rx, lx = rem - ly * Rx;
-                if (ly >= Ry) continue;   // plane padding
-                long long gi;
-                if (interior) {
-                    gi = gbase + lz * gnxy + ly * gnx + lx;
-                } else {
-                    gi = wrap_node(g, reg0[0] + lx, reg0[1] + ly, reg0[2] + lz);
-                }
-#pragma unroll
-                for (int comp = 0; comp < 3; comp++) {
-                    sF[comp * R3 + l] = gi >= 0 ? __ldg(f.E + comp * g.ncell + gi) : 0.f;
-                    sF[(comp + 3) * R3 + l] = gi >= 0 ? __ldg(f.B + comp * g.ncell + gi) : 0.f;
-                }
-            }
-        }
+        if (!FROZEN) stage_fields(reg, g, f, sF, reg0, interior, gbase);
         const int c0 = sp.jz_only ? 2 : 0;   // first current component the species can touch
         for (int l = threadIdx.x + c0 * R3; l < 3 * R3; l += blockDim.x) {
             sJlo[l] = 0u;
@@ -531,11 +546,16 @@ k_push(SpeciesDev sp, GridDev g, TileDev t, FieldsDev f, ExtDev ext, int *work, 
         __syncthreads();
         // each lane takes kGroup = 8 consecutive particles: one cell of an 8-per-cell lattice,
         // visited in octant order, so at every iteration the warp's 32 lanes sit on 32
-        // different cells with the same stencil shift (bank-conflict-free shared accesses)
+        // different cells with the same stencil shift (bank-conflict-free shared accesses, see
+        // plane_pitch)
         const int len = p_end - p_begin;
         constexpr int G = kGroup;
         for (int k_it = 0; k_it < G; k_it++) {
-            const int q = (warp * 32 + lane) * G + k_it;
+            // lane-major: a warp's lanes sit kChunk/32 particles apart in the cell-sorted item, so
+            // in a dense bunch (hundreds of particles per cell and octant) they still deposit into
+            // different windows instead of queueing on the same shared-memory words; each lane's
+            // G consecutive particles share cache lines across the warps
+            const int q = lane * (kChunk / 32) + warp * G + k_it;
             if (q >= len) continue;
             const int p = p_begin + q;
             float4 P = sp.pos[p];
