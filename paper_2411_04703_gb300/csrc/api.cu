@@ -91,7 +91,7 @@ int check_ctx(pic_ctx *c)
     return PIC_OK;
 }
 
-int make_species(pic_ctx *c, double q, double m, int frozen, int64_t cap, int *sid)
+int make_species(pic_ctx *c, double q, double m, int frozen, int64_t cap, int *sid, bool lattice = false)
 {
     if (c->nsp >= kMaxSpecies) return fail(c, PIC_ERR_ARG, "too many species (max 8)");
     if (cap < 1 || cap >= (int64_t)std::numeric_limits<int>::max() - kChunk)
@@ -105,6 +105,20 @@ int make_species(pic_ctx *c, double q, double m, int frozen, int64_t cap, int *s
     s.cap = cap;
     s.max_items = c->ntiles + cap / kChunk + 2;
     int r;
+    if (lattice) {
+        // a ring of lattice planes replaces the particle records: live planes span the active z
+        // range, so plane m - plane_cap is always below the grid when plane m is injected
+        s.lattice = 1;
+        s.cap = 0;
+        s.plane_cap = (int64_t)c->ppc[2] * (c->n[2] + 4) + 2;
+        if ((r = alloc_zero(c, &s.planes, s.plane_cap)) || (r = alloc_zero(c, &s.tx, c->n[0])) ||
+            (r = alloc_zero(c, &s.ty, c->n[1])) || (r = alloc_zero(c, &s.zacc, c->n[2])) ||
+            (r = alloc_zero(c, &s.count, 4)))
+            return r;
+        CK(cudaMemsetAsync(s.planes, 0xff, sizeof(PlaneRec) * s.plane_cap, c->stream));   // kz = -1: empty
+        *sid = c->nsp++;
+        return PIC_OK;
+    }
     if ((r = alloc_zero(c, &s.pos, cap)) || (r = alloc_zero(c, &s.mom, cap)) || (r = alloc_zero(c, &s.pos2, cap)) ||
         (r = alloc_zero(c, &s.mom2, cap)) || (r = alloc_zero(c, &s.id, cap)) || (r = alloc_zero(c, &s.id2, cap)) ||
         (r = alloc_zero(c, &s.count, 4)) || (r = alloc_zero(c, &s.rank, cap)) ||
@@ -165,6 +179,42 @@ struct TraceScope {
 
 enum { TR_SORT = 0, TR_PUSH = 1, TR_PUSH_FROZEN = 2, TR_FIELDS = 3, TR_WINDOW = 4, TR_INJECT = 5, TR_OTHER = 6 };
 
+// Particle records of a species for the diagnostics: the species' own, or for a lattice species
+// temporary records materialised from its planes, released (after the stream drains) with the view.
+struct RecordView {
+    pic_ctx *c = nullptr;
+    Species s;
+    bool tmp = false;
+    ~RecordView()
+    {
+        if (!tmp) return;
+        cudaStreamSynchronize(c->stream);
+        dfree(c, s.pos);
+        dfree(c, s.mom);
+        dfree(c, s.id);
+        dfree(c, s.count);
+    }
+};
+
+int record_view(pic_ctx *c, int si, RecordView &v)
+{
+    v.c = c;
+    v.s = c->sp[si];
+    if (!v.s.lattice) return PIC_OK;
+    v.tmp = true;
+    v.s.pos = v.s.mom = nullptr;
+    v.s.id = v.s.count = nullptr;
+    const int64_t per_plane = (int64_t)(c->xr[1] - c->xr[0]) * (c->xr[3] - c->xr[2]) * c->ppc[0] * c->ppc[1];
+    const int64_t n = v.s.plane_cap * per_plane;
+    int r;
+    if ((r = alloc_zero(c, &v.s.pos, n)) || (r = alloc_zero(c, &v.s.mom, n)) || (r = alloc_zero(c, &v.s.id, n)) ||
+        (r = alloc_zero(c, &v.s.count, 4)))
+        return r;
+    v.s.cap = n;
+    CK(launch_lattice_records(c, si, v.s));
+    return PIC_OK;
+}
+
 int inject_due(pic_ctx *c)
 {
     const int64_t m1 = plane_max(c, c->step, c->shifts);
@@ -173,6 +223,7 @@ int inject_due(pic_ctx *c)
     const int64_t add = (m1 - c->m_last) * per_plane;
     for (int si : {c->sp_e, c->sp_i}) {
         Species &s = c->sp[si];
+        if (s.lattice) continue;
         if (s.bound + add > s.cap) {
             CK(cudaStreamSynchronize(c->stream));
             int cnt = 0;
@@ -275,7 +326,6 @@ SpeciesDev species_dev(const pic_ctx *c, const Species &s)
         d.jinv[k] = 1.0 / (double)d.jscale[k];
     }
     d.frozen = s.frozen;
-    d.jz_only = s.frozen && s.jz_only;
     d.cap = (int)s.cap;
     return d;
 }
@@ -542,7 +592,7 @@ int pic_set_plasma(pic_ctx *c, const pic_plasma *p, int *electron_id, int *ion_i
     }
     int se, si;
     if ((r = make_species(c, -1.0, 1.0, 0, cap, &se))) return r;
-    if ((r = make_species(c, 1.0, 1836.15267343, 1, cap, &si))) return r;
+    if ((r = make_species(c, 1.0, 1836.15267343, 1, cap, &si, true))) return r;
     c->nprof = p->n_nodes;
     c->prof_z.assign(p->z_nodes, p->z_nodes + p->n_nodes);
     c->prof_n.assign(p->density, p->density + p->n_nodes);
@@ -561,12 +611,15 @@ int pic_set_plasma(pic_ctx *c, const pic_plasma *p, int *electron_id, int *ion_i
         for (int i = 0; i < p->n_nodes; i++) nmax = std::max(nmax, std::fabs(p->density[i]));
         const double wm = c->gR * nmax * c->d[0] * c->d[1] * c->d[2] / ((double)c->ppc[0] * c->ppc[1] * c->ppc[2]);
         c->sp[se].wmax = c->sp[si].wmax = wm;
-        c->sp[si].jz_only = 1;   // lab-static ions: u' = (0, 0, -gamma_R beta_R), never pushed
     }
+    CK(launch_lattice_profiles(c, si));
     const double lo = (double)margin_lo(c) + (double)c->shifts + c->bR * (double)c->step * c->dt / c->d[2];
     const int64_t m0 = (int64_t)std::ceil((double)c->ppc[2] * lo - 0.5);
     const int64_t m1 = plane_max(c, c->step, c->shifts);
     if ((m1 - m0 + 1) * per_plane > cap) return fail(c, PIC_ERR_CAPACITY, "plasma capacity below the window fill");
+    if (m1 - m0 + 1 > c->sp[si].plane_cap) return fail(c, PIC_ERR_CAPACITY, "plasma lattice ring below the window fill");
+    if (c->sp[si].plane_cap * per_plane >= (int64_t)std::numeric_limits<int>::max())
+        return fail(c, PIC_ERR_ARG, "plasma lattice too large for 32-bit particle slots");
     CK(launch_inject(c, m0, m1));
     c->m_last = m1;
     CK(cudaStreamSynchronize(c->stream));
@@ -583,12 +636,20 @@ int pic_step(pic_ctx *c, int64_t nsteps)
     for (int64_t it = 0; it < nsteps; it++) {
         if (c->step % c->sort_every == 0) {
             TraceScope ts(c, TR_SORT);
-            for (int si = 0; si < c->nsp; si++) CK(launch_sort(c, si));
+            for (int si = 0; si < c->nsp; si++)
+                if (!c->sp[si].lattice) CK(launch_sort(c, si));
         }
-        CK(cudaMemsetAsync(c->J, 0, sizeof(float) * 3 * c->ncell, c->stream));
+        // the lattice species writes J_z whole, before the other species add to it
+        const bool lat = c->plasma && c->sp[c->sp_i].lattice;
+        CK(cudaMemsetAsync(c->J, 0, sizeof(float) * (lat ? 2 : 3) * c->ncell, c->stream));
         CK(cudaMemsetAsync(c->work, 0, sizeof(int) * 2 * kMaxSpecies, c->stream));
+        if (lat) {
+            TraceScope ts(c, TR_PUSH_FROZEN);
+            CK(launch_lattice_step(c, c->sp_i));
+        }
         const ExtDev ext = ext_step(c);
         for (int si = 0; si < c->nsp; si++) {
+            if (c->sp[si].lattice) continue;
             TraceScope ts(c, c->sp[si].frozen ? TR_PUSH_FROZEN : TR_PUSH);
             CK(launch_push(c, si, ext));
         }
@@ -604,7 +665,8 @@ int pic_step(pic_ctx *c, int64_t nsteps)
             while (c->shifts < due) {
                 TraceScope ts(c, TR_WINDOW);
                 CK(launch_shift_fields(c));
-                for (int si = 0; si < c->nsp; si++) CK(launch_shift_particles(c, si));
+                for (int si = 0; si < c->nsp; si++)
+                    CK(c->sp[si].lattice ? launch_lattice_shift(c, si) : launch_shift_particles(c, si));
                 c->shifts++;
             }
         }
@@ -636,7 +698,8 @@ int pic_sort(pic_ctx *c)
     int r = check_ctx(c);
     if (r) return r;
     TraceScope ts(c, TR_SORT);
-    for (int si = 0; si < c->nsp; si++) CK(launch_sort(c, si));
+    for (int si = 0; si < c->nsp; si++)
+        if (!c->sp[si].lattice) CK(launch_sort(c, si));
     return PIC_OK;
 }
 
@@ -651,7 +714,12 @@ int pic_get_fields(pic_ctx *c, int which, float *dst, size_t n)
     else if (which >= PIC_JX && which <= PIC_JZ) src = c->J + (which - PIC_JX) * c->ncell;
     else if (which == PIC_RHO) {
         if (!c->rho && (r = alloc_zero(c, &c->rho, c->ncell))) return r;
-        CK(launch_rho(c, c->rho));
+        CK(cudaMemsetAsync(c->rho, 0, sizeof(float) * c->ncell, c->stream));
+        for (int si = 0; si < c->nsp; si++) {
+            RecordView v;
+            if ((r = record_view(c, si, v))) return r;
+            CK(launch_rho(c, v.s, c->rho));
+        }
         src = c->rho;
     } else {
         return fail(c, PIC_ERR_ARG, "unknown field");
@@ -682,7 +750,9 @@ int pic_get_particles(pic_ctx *c, int sid, int64_t cap, int64_t *n_out, int32_t 
     int r = check_ctx(c);
     if (r) return r;
     if (sid < 0 || sid >= c->nsp || !n_out) return fail(c, PIC_ERR_ARG, "bad species id");
-    Species &s = c->sp[sid];
+    RecordView v;
+    if ((r = record_view(c, sid, v))) return r;
+    const Species &s = v.s;
     CK(cudaStreamSynchronize(c->stream));
     int cnt = 0;
     CK(cudaMemcpy(&cnt, s.count, sizeof(int), cudaMemcpyDeviceToHost));
@@ -734,8 +804,10 @@ int pic_get_moments(pic_ctx *c, int sid, int frame, double k_bunch, pic_moments 
     if (r) return r;
     if (sid < 0 || sid >= c->nsp || !out) return fail(c, PIC_ERR_ARG, "bad species id");
     if (frame != PIC_FRAME_LAB && frame != PIC_FRAME_BOOSTED) return fail(c, PIC_ERR_ARG, "unknown frame");
+    RecordView view;
+    if ((r = record_view(c, sid, view))) return r;
     double v[20];
-    CK(launch_moments(c, sid, frame == PIC_FRAME_LAB ? PIC_FRAME_LAB : PIC_FRAME_BOOSTED, k_bunch, v));
+    CK(launch_moments(c, view.s, frame == PIC_FRAME_LAB ? PIC_FRAME_LAB : PIC_FRAME_BOOSTED, k_bunch, v));
     CK(launch_field_energy(c, &v[19]));
     static_assert(sizeof(pic_moments) == 20 * sizeof(double), "pic_moments layout");
     std::memcpy(out, v, sizeof(v));
@@ -756,7 +828,9 @@ int pic_get_count(pic_ctx *c, int sid, int64_t *n_out)
     int r = check_ctx(c);
     if (r) return r;
     if (sid < 0 || sid >= c->nsp || !n_out) return fail(c, PIC_ERR_ARG, "bad species id");
-    CK(species_count_live(c, sid, n_out));
+    RecordView v;
+    if ((r = record_view(c, sid, v))) return r;
+    CK(species_count_live(c, v.s, n_out));
     return PIC_OK;
 }
 

@@ -68,7 +68,6 @@ struct SpeciesDev {
     float h_qm;           // 0.5 (q/m) dt
     float cf[3];          // -q d_c / (dt V): current of unit weight per unit W
     float jscale[3];      // fixed-point scale of the shared-memory current (max contribution 2^30)
-    int jz_only;          // every particle moves along z only: J_x = J_y = 0 (frozen drifting ions)
     double jinv[3];       // 1 / jscale
     int frozen;
     int cap;
@@ -89,6 +88,27 @@ struct FieldsDev {
     float *E, *B, *J;     // [3][ncell] each
 };
 
+// One plane of the lab-static plasma lattice, held by a lattice species (the frozen plasma
+// ions): every ion of plane m shares the z offset, the cell row and the weight, and ion r of
+// the plane (r over the transverse lattice, as injected) has id id0 + r.
+struct PlaneRec {
+    float oz;             // z offset in the cell
+    int kz;               // cell row; -1: the plane was dropped (or never placed)
+    float w;              // macroparticle weight
+    int id0;
+};
+
+// Particle shape of order 1 (CIC) or 2 (TSC) at distance x from a node, FP64 (the lattice
+// species' current and transverse profiles; the particle kernel uses its own FP32 forms).
+__device__ __forceinline__ double shape_weight(int order, double x)
+{
+    const double a = fabs(x);
+    if (order == 1) return a < 1.0 ? 1.0 - a : 0.0;
+    if (a <= 0.5) return 0.75 - a * a;
+    if (a < 1.5) return 0.5 * (1.5 - a) * (1.5 - a);
+    return 0.0;
+}
+
 // ------------------------------------------------------------------------- host context
 struct Species {
     double q = -1, m = 1;
@@ -105,7 +125,12 @@ struct Species {
     int64_t bound = 0;        // host upper bound of count[0]
     int64_t next_id = 0;
     double wmax = 0;          // largest |weight| ever held (sets the fixed-point current scale)
-    int jz_only = 0;          // frozen with u_x = u_y = 0 for every particle (plasma ions)
+    // lattice species (plasma ions): no particle records, a ring of lattice planes instead
+    int lattice = 0;
+    PlaneRec *planes = nullptr;  // device [plane_cap]; plane m in slot m mod plane_cap
+    int64_t plane_cap = 0;
+    float *tx = nullptr, *ty = nullptr;   // device [n0], [n1]: node weights summed over the transverse lattice
+    double *zacc = nullptr;      // device [n2]: J_z per unit transverse weight, one step
 };
 
 }  // namespace gbpic
@@ -179,7 +204,12 @@ PmlDev pml_dev(const pic_ctx *c);
 
 // k_push.cu
 cudaError_t launch_push(pic_ctx *c, int si, const ExtDev &ext);
-cudaError_t launch_rho(pic_ctx *c, float *rho);
+cudaError_t launch_rho(pic_ctx *c, const Species &s, float *rho);
+// k_lattice.cu
+cudaError_t launch_lattice_profiles(pic_ctx *c, int si);
+cudaError_t launch_lattice_step(pic_ctx *c, int si);
+cudaError_t launch_lattice_shift(pic_ctx *c, int si);
+cudaError_t launch_lattice_records(pic_ctx *c, int si, Species &out);
 // k_fields.cu
 cudaError_t launch_fdtd_b(pic_ctx *c, float dtt);
 cudaError_t launch_fdtd_e(pic_ctx *c);
@@ -195,8 +225,8 @@ cudaError_t launch_load(pic_ctx *c, int si, int64_t n, const double *dx, const d
                         int64_t id_base);
 cudaError_t launch_inject(pic_ctx *c, int64_t m0, int64_t m1);
 cudaError_t launch_shift_particles(pic_ctx *c, int si);
-cudaError_t launch_moments(pic_ctx *c, int si, int frame, double k, double *out20);
+cudaError_t launch_moments(pic_ctx *c, const Species &s, int frame, double k, double *out20);
 cudaError_t species_wmax(pic_ctx *c, int si, double *out);
-cudaError_t species_count_live(pic_ctx *c, int si, int64_t *out);
+cudaError_t species_count_live(pic_ctx *c, const Species &s, int64_t *out);
 
 }  // namespace gbpic

@@ -17,27 +17,32 @@ struct PlaceP {
     int mlo, mhi;
 };
 
-// Grid coordinate -> (cell, float offset); returns false outside the active region.
+// Grid coordinate X of dimension d -> (cell, float offset); false outside the active region.
+__device__ __forceinline__ bool place1(const PlaceP &g, int d, double X, float &o, int &c)
+{
+    double fl = floor(X);
+    float of = (float)(X - fl);
+    if (of >= 1.f) { of = 0.f; fl += 1.0; }
+    long long ci = (long long)fl;
+    bool ok = true;
+    if (g.periodic[d]) {
+        ci %= g.n[d];
+        if (ci < 0) ci += g.n[d];
+    } else if (ci < g.mlo || ci > g.n[d] - 1 - g.mhi) {
+        ok = false;
+        ci = 0;
+    }
+    c = (int)ci;
+    o = of;
+    return ok;
+}
+
 __device__ __forceinline__ bool place(const PlaceP &g, const double X[3], float o[3], int c[3])
 {
-    bool ok = true;
-#pragma unroll
-    for (int d = 0; d < 3; d++) {
-        double fl = floor(X[d]);
-        float of = (float)(X[d] - fl);
-        if (of >= 1.f) { of = 0.f; fl += 1.0; }
-        long long ci = (long long)fl;
-        if (g.periodic[d]) {
-            ci %= g.n[d];
-            if (ci < 0) ci += g.n[d];
-        } else if (ci < g.mlo || ci > g.n[d] - 1 - g.mhi) {
-            ok = false;
-            ci = 0;
-        }
-        c[d] = (int)ci;
-        o[d] = of;
-    }
-    return ok;
+    const bool a = place1(g, 0, X[0], o[0], c[0]);
+    const bool b = place1(g, 1, X[1], o[1], c[1]);
+    const bool z = place1(g, 2, X[2], o[2], c[2]);
+    return a && b && z;
 }
 
 struct LoadP {
@@ -119,6 +124,8 @@ struct InjP {
     const double *prof;  // [2][nprof]: z nodes then densities
     int nprof;
     int id_e, id_i;
+    PlaneRec *planes;    // ions as a lattice species: plane m goes to slot m mod plane_cap
+    long long plane_cap;
 };
 
 __device__ double profile(const double *prof, int np, double z)
@@ -134,33 +141,105 @@ __device__ double profile(const double *prof, int np, double z)
     return prof[2 * np - 1];
 }
 
+// Lattice point t of planes m0.. (transverse index r = t mod per_plane, ppc_x fastest, then
+// ppc_y, then the cells of the x range, then y): grid coordinates of the point.
+__device__ __forceinline__ void lattice_point(const InjP &p, long long t, long long &m, int &r, double X[3])
+{
+    m = p.m0 + t / p.per_plane;
+    r = (int)(t % p.per_plane);
+    int q = r;
+    const int a = q % p.ppc[0];
+    q /= p.ppc[0];
+    const int b = q % p.ppc[1];
+    q /= p.ppc[1];
+    const int ii = q % p.nxr, jj = q / p.nxr;
+    X[0] = p.x0 + ii + (a + 0.5) / p.ppc[0];
+    X[1] = p.y0 + jj + (b + 0.5) / p.ppc[1];
+    X[2] = ((double)m + 0.5) / p.ppc[2] - p.zshift;
+}
+
 __global__ void k_inject(SpeciesDev se, SpeciesDev si, InjP p, int *err)
 {
-    const int base_e = se.count[0], base_i = si.count[0];
+    const int base_e = se.count[0], base_i = p.planes ? 0 : si.count[0];
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < p.count; t += (long long)gridDim.x * blockDim.x) {
-        const long long m = p.m0 + t / p.per_plane;
-        int r = (int)(t % p.per_plane);
-        const int a = r % p.ppc[0];
-        r /= p.ppc[0];
-        const int b = r % p.ppc[1];
-        r /= p.ppc[1];
-        const int ii = r % p.nxr, jj = r / p.nxr;
+        long long m;
+        int r;
+        double X[3];
+        lattice_point(p, t, m, r, X);
         const double zc = ((double)m + 0.5) / p.ppc[2];
-        double X[3] = {p.x0 + ii + (a + 0.5) / p.ppc[0], p.y0 + jj + (b + 0.5) / p.ppc[1], zc - p.zshift};
         const double dens = p.gR * profile(p.prof, p.nprof, p.gR * zc * p.dz);
         float o[3];
         int c[3];
         const bool ok = place(p.g, X, o, c) && dens > 0.0;
         const float4 P = make_float4(o[0], o[1], o[2], __int_as_float(ok ? pack_cell(c[0], c[1], c[2]) : -1));
         const float4 Mo = make_float4(0.f, 0.f, p.uz, (float)(dens * p.wfac));
-        const long long se_slot = base_e + t, si_slot = base_i + t;
-        if (se_slot >= se.cap || si_slot >= si.cap) { atomicOr(err, ERR_CAPACITY); continue; }
+        const long long se_slot = base_e + t;
+        if (se_slot >= se.cap) { atomicOr(err, ERR_CAPACITY); continue; }
         se.pos[se_slot] = P;
         se.mom[se_slot] = Mo;
         se.id[se_slot] = p.id_e + (int)t;
+        if (p.planes) {
+            if (r != 0) continue;
+            // one plane record: the z placement, the weight and the plane's first id
+            PlaneRec &slot = p.planes[m % p.plane_cap];
+            if (slot.kz >= 0) { atomicOr(err, ERR_CAPACITY); continue; }
+            float oz;
+            int kz;
+            const bool okz = place1(p.g, 2, X[2], oz, kz) && dens > 0.0;
+            slot = PlaneRec{oz, okz ? kz : -1, Mo.w, p.id_i + (int)t};
+            continue;
+        }
+        const long long si_slot = base_i + t;
+        if (si_slot >= si.cap) { atomicOr(err, ERR_CAPACITY); continue; }
         si.pos[si_slot] = P;
         si.mom[si_slot] = Mo;
         si.id[si_slot] = p.id_i + (int)t;
+    }
+}
+
+// Transverse profile of the lattice species: T(i) = sum over the lattice's points x along dim
+// d (cells lo .. hi-1, ppc points each, placed as at injection) of S(i - x); periodic dims wrap.
+__global__ void k_lattice_profile(PlaceP g, int d, int lo, int hi, int ppc, int order, float *out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n[d]) return;
+    double acc = 0.0;
+    for (int cell = lo; cell < hi; cell++)
+        for (int a = 0; a < ppc; a++) {
+            float o;
+            int ci;
+            if (!place1(g, d, cell + (a + 0.5) / ppc, o, ci)) continue;
+            double x = (double)i - ((double)ci + (double)o);
+            if (g.periodic[d]) x -= g.n[d] * rint(x / g.n[d]);
+            acc += shape_weight(order, x);
+        }
+    out[i] = (float)acc;
+}
+
+// Particle records of the lattice species, materialised from its planes: slot s of the plane
+// ring and transverse index r give record s * per_plane + r (dropped planes give dummies).
+__global__ void k_lattice_records(SpeciesDev out, const PlaneRec *planes, long long cap, InjP p)
+{
+    const long long n = cap * p.per_plane;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        out.count[0] = (int)n;
+        out.count[1] = 0;
+        out.count[2] = 0;
+    }
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        const PlaneRec pl = planes[t / p.per_plane];
+        long long m;
+        int r;
+        double X[3];
+        lattice_point(p, t, m, r, X);
+        float ox, oy;
+        int cx, cy;
+        const bool okx = place1(p.g, 0, X[0], ox, cx);
+        const bool oky = place1(p.g, 1, X[1], oy, cy);
+        const bool ok = pl.kz >= 0 && okx && oky;
+        out.pos[t] = make_float4(ox, oy, pl.oz, __int_as_float(ok ? pack_cell(cx, cy, pl.kz) : -1));
+        out.mom[t] = make_float4(0.f, 0.f, p.uz, pl.w);
+        out.id[t] = pl.id0 + r;
     }
 }
 
@@ -364,18 +443,60 @@ cudaError_t launch_inject(pic_ctx *c, int64_t m0, int64_t m1)
     p.nprof = c->nprof;
     p.id_e = (int)se.next_id;
     p.id_i = (int)si.next_id;
+    p.planes = si.lattice ? si.planes : nullptr;
+    p.plane_cap = si.plane_cap;
     if (p.count <= 0) return cudaSuccess;
     const long long blocks = std::min<long long>((p.count + 255) / 256, (long long)c->num_sms * 16);
     k_inject<<<(unsigned)blocks, 256, 0, c->stream>>>(species_dev(c, se), species_dev(c, si), p, c->err);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_bump<<<1, 1, 0, c->stream>>>(se.count, p.count, (int)se.cap, c->err);
-    k_bump<<<1, 1, 0, c->stream>>>(si.count, p.count, (int)si.cap, c->err);
-    c->kernels += 3;
+    c->kernels += 2;
+    if (!si.lattice) {
+        k_bump<<<1, 1, 0, c->stream>>>(si.count, p.count, (int)si.cap, c->err);
+        c->kernels++;
+        si.bound += p.count;
+    }
     se.next_id += p.count;
     si.next_id += p.count;
     se.bound += p.count;
-    si.bound += p.count;
+    return cudaGetLastError();
+}
+
+namespace {
+InjP lattice_params(pic_ctx *c)
+{
+    InjP p{};
+    p.g = place_params(c);
+    p.nxr = c->xr[1] - c->xr[0];
+    p.x0 = c->xr[0];
+    p.y0 = c->xr[2];
+    for (int d = 0; d < 3; d++) p.ppc[d] = c->ppc[d];
+    p.per_plane = p.nxr * (c->xr[3] - c->xr[2]) * c->ppc[0] * c->ppc[1];
+    p.uz = (float)(-sqrt(c->gR * c->gR - 1.0));
+    return p;
+}
+}  // namespace
+
+cudaError_t launch_lattice_profiles(pic_ctx *c, int si)
+{
+    const Species &s = c->sp[si];
+    const PlaceP g = place_params(c);
+    k_lattice_profile<<<(c->n[0] + 127) / 128, 128, 0, c->stream>>>(g, 0, c->xr[0], c->xr[1], c->ppc[0], c->order, s.tx);
+    k_lattice_profile<<<(c->n[1] + 127) / 128, 128, 0, c->stream>>>(g, 1, c->xr[2], c->xr[3], c->ppc[1], c->order, s.ty);
+    c->kernels += 2;
+    return cudaGetLastError();
+}
+
+// out: pos, mom, id of plane_cap * per_plane slots and count[4], allocated by the caller.
+cudaError_t launch_lattice_records(pic_ctx *c, int si, Species &out)
+{
+    const Species &s = c->sp[si];
+    const InjP p = lattice_params(c);
+    const long long n = s.plane_cap * p.per_plane;
+    const long long blocks = std::max<long long>(1, std::min<long long>((n + 255) / 256, (long long)c->num_sms * 16));
+    k_lattice_records<<<(unsigned)blocks, 256, 0, c->stream>>>(species_dev(c, out), s.planes, s.plane_cap, p);
+    c->kernels++;
     return cudaGetLastError();
 }
 
@@ -396,12 +517,12 @@ cudaError_t species_wmax(pic_ctx *c, int si, double *out)
     return cudaSuccess;
 }
 
-cudaError_t species_count_live(pic_ctx *c, int si, int64_t *out)
+cudaError_t species_count_live(pic_ctx *c, const Species &s, int64_t *out)
 {
     unsigned long long *d = reinterpret_cast<unsigned long long *>(c->red);
     cudaError_t e = cudaMemsetAsync(d, 0, sizeof(unsigned long long), c->stream);
     if (e != cudaSuccess) return e;
-    k_count_live<<<c->num_sms * 4, 256, 0, c->stream>>>(species_dev(c, c->sp[si]), d);
+    k_count_live<<<c->num_sms * 4, 256, 0, c->stream>>>(species_dev(c, s), d);
     c->kernels++;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     unsigned long long h = 0;
@@ -418,9 +539,8 @@ cudaError_t launch_shift_particles(pic_ctx *c, int si)
     return cudaGetLastError();
 }
 
-cudaError_t launch_moments(pic_ctx *c, int si, int frame, double k, double *out)
+cudaError_t launch_moments(pic_ctx *c, const Species &s, int frame, double k, double *out)
 {
-    const Species &s = c->sp[si];
     MomP p{};
     for (int d = 0; d < 3; d++) p.d[d] = c->d[d];
     p.shifts = (double)c->shifts;

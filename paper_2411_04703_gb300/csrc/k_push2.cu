@@ -50,21 +50,15 @@ cudaError_t launch_push(pic_ctx *c, int si, const ExtDev &ext)
     return c->order == 1 ? launch_push_order1(c, si, ext) : push::launch_order<2>(c, si, ext);
 }
 
-cudaError_t launch_rho(pic_ctx *c, float *rho)
+// Adds the charge density of species s to rho.
+cudaError_t launch_rho(pic_ctx *c, const Species &s, float *rho)
 {
-    cudaError_t e = cudaMemsetAsync(rho, 0, sizeof(float) * c->ncell, c->stream);
-    if (e != cudaSuccess) return e;
     const float V = (float)(c->d[0] * c->d[1] * c->d[2]);
-    for (int si = 0; si < c->nsp; si++) {
-        const Species &s = c->sp[si];
-        const float qv = (float)(s.q / V);
-        if (c->order == 1) k_rho<1><<<c->num_sms * 8, 256, 0, c->stream>>>(species_dev(c, s), grid_dev(c), qv, rho);
-        else k_rho<2><<<c->num_sms * 8, 256, 0, c->stream>>>(species_dev(c, s), grid_dev(c), qv, rho);
-        c->kernels++;
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
+    const float qv = (float)(s.q / V);
+    if (c->order == 1) k_rho<1><<<c->num_sms * 8, 256, 0, c->stream>>>(species_dev(c, s), grid_dev(c), qv, rho);
+    else k_rho<2><<<c->num_sms * 8, 256, 0, c->stream>>>(species_dev(c, s), grid_dev(c), qv, rho);
+    c->kernels++;
+    return cudaGetLastError();
 }
 
 }  // namespace gbpic

@@ -537,8 +537,7 @@ k_push(SpeciesDev sp, GridDev g, TileDev t, FieldsDev f, ExtDev ext, int *work, 
         const long long gnx = g.n[0], gnxy = (long long)g.n[0] * g.n[1];
         const long long gbase = reg0[2] * gnxy + reg0[1] * gnx + reg0[0];
         if (!FROZEN) stage_fields(reg, g, f, sF, reg0, interior, gbase);
-        const int c0 = sp.jz_only ? 2 : 0;   // first current component the species can touch
-        for (int l = threadIdx.x + c0 * R3; l < 3 * R3; l += blockDim.x) {
+        for (int l = threadIdx.x; l < 3 * R3; l += blockDim.x) {
             sJlo[l] = 0u;
             sJhi[l] = 0;
         }
@@ -636,11 +635,11 @@ k_push(SpeciesDev sp, GridDev g, TileDev t, FieldsDev f, ExtDev ext, int *work, 
             if (ly >= Ry) continue;   // plane padding (never written by a particle)
             long long gi = -1;
             bool have = false;
-            for (int comp = c0; comp < 3; comp++) have = have || sJlo[comp * R3 + l] != 0u || sJhi[comp * R3 + l] != 0;
+            for (int comp = 0; comp < 3; comp++) have = have || sJlo[comp * R3 + l] != 0u || sJhi[comp * R3 + l] != 0;
             if (!have) continue;
             gi = interior ? gbase + lz * gnxy + ly * gnx + lx : wrap_node(g, reg0[0] + lx, reg0[1] + ly, reg0[2] + lz);
             if (gi < 0) { atomicOr(err, ERR_INDEX); continue; }
-            for (int comp = c0; comp < 3; comp++) {
+            for (int comp = 0; comp < 3; comp++) {
                 const unsigned lo = sJlo[comp * R3 + l];
                 const int hi = sJhi[comp * R3 + l];
                 if (lo == 0u && hi == 0) continue;

@@ -146,6 +146,8 @@ def test_tile_sort_is_bit_exact():
     sim.step(3)
     sim.sort()
     for name, sid in ids.items():
+        if name == "plasma_i":
+            continue   # the frozen ions are held as lattice planes, not sorted records
         P = sim.get_particles(sid)
         X = P["cell"].astype(np.float64) + P["off"].astype(np.float64)
         order, keys = oracle.tile_sort(X, w.grid, w.tile)
