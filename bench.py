@@ -26,6 +26,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -63,7 +64,7 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        self.path = os.path.join(os.environ.get("GBPIC_CLOCKS_DIR", tempfile.gettempdir()), f"clocks_rank{index}.csv")
 
     def start(self):
         try:
@@ -102,6 +103,40 @@ class ClockSampler:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def oracle_sample_ensemble(steps, warmup, seed=4):
+    """FP64 oracle on a bounded sample of the batched ensemble: run 0 on a 32 x 32 x 64 sub-box
+    (same cells, K, plasma density and particles per cell; beam scaled with the volume)."""
+    import oracle
+    from paper_2411_04703_gb300 import workloads as W
+    oracle.build()
+    e = W.batched_ensemble(seed=seed)
+    w = W.ensemble_run(e, 0)
+    w.grid = (32, 32, 64)
+    w.plasma = W.dataclasses.replace(w.plasma, xrange=(0, 32, 0, 32))
+    w.beam.n = max(1000, e.n_beam[0] // 8)
+    w.beam.origin = (16.0, 16.0, 32.0)
+    o = oracle.Sim(w.grid, w.d, w.dt, w.gamma_R, bc=w.bc, order=w.order)
+    o.set_external(w.undulator.K, w.undulator.lambda_u)
+    se = o.add_species(-1.0, 1.0)
+    si = o.add_species(1.0, 1836.15267343, frozen=True)
+    sb = o.add_species(-1.0, 1.0)
+    p = w.plasma
+    o.set_plasma(se, si, p.ppc, p.xrange, p.z_nodes, p.n_nodes)
+    x, u, wt = W.sample_beam(w)
+    o.load(sb, x, u, wt, frame=0, origin=w.beam.origin, match_undulator=True)
+    if warmup:
+        o.step(warmup)
+    n0 = o.count(se) + o.count(sb)
+    t0 = time.perf_counter()
+    o.step(steps)
+    t = time.perf_counter() - t0
+    n1 = o.count(se) + o.count(sb)
+    value = 0.5 * (n0 + n1) * steps / t
+    sample = (f"FP64 oracle, run 0 of the ensemble on a 32x32x64 sub-box (4 ppc plasma + frozen ions, "
+              f"{o.count(sb)} beam), {steps} steps after {warmup} warm-up, single thread")
+    return value, t, sample
 
 
 def oracle_sample(steps, warmup, seed=2):
@@ -182,13 +217,37 @@ def run_gbpic(args):
         if world > 1:
             dist.barrier()
 
-    grid = tuple(int(v) for v in args.grid.split(","))
-    nb = args.beam or int(round(4194304 * (grid[0] * grid[1] * grid[2]) / (128 * 128 * 512)))
-    w = W.plasma_buncher(grid=grid, n_beam=nb, seed=2 + rank)
-    if grid != (128, 128, 512):
-        w.name = f"plasma buncher {grid[0]}x{grid[1]}x{grid[2]} (reduced), {nb} beam + 8 ppc plasma, TSC"
-    beam = W.sample_beam(w)
-    sim, ids = api.from_workload(w, device=local, beam_arrays=beam)
+    ens = None
+    if args.workload == "ensemble":
+        # batched sweep: 64 runs of 64x64x128 stacked in one context (one launch per kernel)
+        import numpy as np
+        ens = W.batched_ensemble(runs=args.runs, seed=4 + rank)
+        w = ens.base
+        parts = [W.sample_beam(W.ensemble_run(ens, r)) for r in range(ens.runs)]
+        beam = (np.concatenate([q[0] for q in parts], axis=1), np.concatenate([q[1] for q in parts], axis=1),
+                np.concatenate([q[2] for q in parts]))
+        if args.sort_every:
+            ens.base.sort_every = args.sort_every
+        sim, ids = api.from_ensemble(ens, device=local)
+        ncell_total = w.ncell * ens.runs
+        boundaries = "periodic (each run)"
+        l2 = "inputs larger than L2 (particle state ~8 GB, fields 0.4 GB)"
+    else:
+        grid = tuple(int(v) for v in args.grid.split(","))
+        nb = args.beam or int(round(4194304 * (grid[0] * grid[1] * grid[2]) / (128 * 128 * 512)))
+        w = W.plasma_buncher(grid=grid, n_beam=nb, seed=2 + rank)
+        if grid != (128, 128, 512):
+            w.name = f"plasma buncher {grid[0]}x{grid[1]}x{grid[2]} (reduced), {nb} beam + 8 ppc plasma, TSC"
+        if args.sort_every:
+            w.sort_every = args.sort_every
+        beam = W.sample_beam(w)
+        sim, ids = api.from_workload(w, device=local, beam_arrays=beam)
+        ncell_total = w.ncell
+        boundaries = "transverse CPML 10 cells, moving window"
+        l2 = "inputs larger than L2 (particle state ~9 GB, fields 0.3 GB)"
+    tuned = None
+    if not args.no_autotune:
+        tuned = sim.autotune(16)   # timed trials of the sort cadence (untimed here, advance the run)
     sim.trace_enable(True)
     if args.warmup:
         sim.step(args.warmup)
@@ -220,7 +279,7 @@ def run_gbpic(args):
 
     # roofline of the dominant kernel class (live CUDA-event trace of the timed region)
     hbm, peak_kind = peaks()
-    ncell = w.ncell
+    ncell = ncell_total
     n_beam = sim.get_count(ids["beam"])
     n_e = 0.5 * (n0 + n1) - n_beam
     classes = tr["ms"]
@@ -260,14 +319,23 @@ def run_gbpic(args):
         xh = torch.from_numpy(x).pin_memory()
         uh = torch.from_numpy(u).pin_memory()
         wh = torch.from_numpy(wt).pin_memory()
-        sim2, ids2 = api.from_workload(w, device=local, beam=False)
+        if ens is not None:
+            sim2, ids2 = api.from_ensemble(ens, device=local, beam=False)
+        else:
+            sim2, ids2 = api.from_workload(w, device=local, beam=False)
         sim2.sync()
         barrier()
         torch.cuda.synchronize()
         ne_plasma0 = sim2.get_count(ids2["plasma_e"])
         t0 = time.perf_counter()
         b = w.beam
-        sb = sim2.load_species(b.q, b.m, xh, uh, wh, frame=api.PIC_FRAME_LAB, origin=b.origin)
+        match = bool(w.undulator is not None and w.undulator.match)
+        if ens is not None:
+            sb = sim2.load_species_batch(b.q, b.m, ens.n_beam, xh, uh, wh, frame=api.PIC_FRAME_LAB,
+                                         origin=b.origin, match_undulator=match)
+        else:
+            sb = sim2.load_species(b.q, b.m, xh, uh, wh, frame=api.PIC_FRAME_LAB, origin=b.origin,
+                                   match_undulator=match)
         sim2.step(args.steps)
         mom = sim2.get_moments(sb, api.PIC_FRAME_LAB, k_bunch=0.0)
         t_e2e = time.perf_counter() - t0
@@ -285,7 +353,7 @@ def run_gbpic(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cv, ct, sample = oracle_sample(3, 0)
+        cv, ct, sample = oracle_sample_ensemble(2, 0) if ens is not None else oracle_sample(3, 0)
         cpu = {"value": cv, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
 
     if rank == 0:
@@ -293,14 +361,16 @@ def run_gbpic(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": w.name, "grid": list(w.grid), "beam": w.beam.n,
+            "config": {"workload": w.name, "grid": list(w.grid), "beam": int(n_beam),
                        "plasma_electrons": int(n_e), "frozen_ions": int(0.5 * (frozen0 + frozen1)),
-                       "shape": "TSC", "boundaries": "transverse CPML 10 cells, moving window",
-                       "tile": list(w.tile), "sort_every": w.sort_every,
-                       "l2": "inputs larger than L2 (particle state ~9 GB, fields 0.3 GB)",
+                       "shape": "TSC", "boundaries": boundaries,
+                       "tile": list(w.tile), "sort_every": tuned if tuned else w.sort_every,
+                       "sort_every_from": "autotuner" if tuned else "workload",
+                       "l2": l2,
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "gpu_launches": int(tr["kernels"]),
+            "fallback_deposits": int(tr.get("fallback", 0)),
         }
         print(json.dumps(line))
     if world > 1:
@@ -319,6 +389,12 @@ def main():
     ap.add_argument("--grid", default="128,128,512",
                     help="plasma-buncher grid (a smaller one, e.g. 64,64,128, for profiling captures)")
     ap.add_argument("--beam", type=int, default=0, help="beam macroparticles (0: scaled with the grid)")
+    ap.add_argument("--sort-every", type=int, default=0, help="steps between tile sorts (0: the workload's)")
+    ap.add_argument("--runs", type=int, default=64, help="ensemble runs (the batched sweep has 64)")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the workload's sort cadence")
+    ap.add_argument("--workload", choices=["buncher", "ensemble"], default="buncher",
+                    help="buncher: the plasma buncher 128x128x512 (default); ensemble: the batched sweep "
+                         "of 64 runs of 64x64x128 in one context")
     args = ap.parse_args()
     if args.warmup < 0 or args.steps < 1:
         raise SystemExit("need --steps >= 1 and --warmup >= 0")

@@ -26,8 +26,8 @@
  *    rho at the nodes (i, j, k).
  *  - Every call that launches work enqueues it on the context's stream and returns without
  *    waiting, except the getters, which synchronise that stream.
- *  - Limits: nx, ny <= 1024, nz <= 2048 (cell index packed into 32 bits), 8 nx ny nz < 2^31
- *    (sort keys); fewer than 2^31 particles per species.
+ *  - Limits: nx, ny <= 1024; bits(nx) + bits(ny) + bits(nz) <= 31 (the cell index is packed
+ *    into one int32); 8 nx ny nz < 2^31 (sort keys); fewer than 2^31 particles per species.
  */
 #ifndef GBPIC_H
 #define GBPIC_H
@@ -93,6 +93,20 @@ typedef struct {
 int pic_create(pic_ctx **out, pic_grid grid, const double dx[3], double dt, double gamma_boost,
                const pic_boundaries *bc, int shape_order, const pic_device *dev);
 
+/* Ensemble of `runs` independent simulations in one context (batched sweeps of undulator K and
+ * plasma density with uneven beam sizes): every run has the grid `grid`, cell size, time step,
+ * boost, boundaries and shape order given here, and its own particles, plasma density and
+ * undulator K.  The runs are stacked along z (run r owns rows r*nz .. (r+1)*nz - 1 of a grid of
+ * nx x ny x runs*nz cells; grid arrays and particle cells use that stacked index), z must be
+ * periodic and is periodic inside each run, so no field, particle or current crosses between
+ * runs.  One pic_step advances every run with one launch per kernel (the particle kernel's work
+ * items span all runs).  nz must be a multiple of the tile's z size.  Per-run setup:
+ * pic_load_species_batch, pic_set_external_field_batch, pic_set_plasma_batch; per-run
+ * diagnostics: pic_get_moments_run.  runs = 1 is the same as pic_create. */
+int pic_create_batch(pic_ctx **out, int runs, pic_grid grid, const double dx[3], double dt,
+                     double gamma_boost, const pic_boundaries *bc, int shape_order,
+                     const pic_device *dev);
+
 /* Tile size for the per-tile sort and the particle kernel (cells, each 2..16), number of
  * steps between sorts (>= 1), and the margin (cells, 0..2) a particle may drift outside its
  * tile between sorts before it takes the slower global-memory path.  Defaults 8x8x8, 8, 1. */
@@ -130,6 +144,16 @@ typedef struct {
 int pic_load_species(pic_ctx *ctx, const pic_species *sp, int64_t n, const double *x,
                      const double *u, const double *w, int frame, int *species_id);
 
+/* Ensemble form of pic_load_species: one species spanning every run, n_run[r] particles loaded
+ * into run r (host int64[runs]).  x, u: host FP64 [3][n] and w: [n] or NULL, with n the sum of
+ * n_run, run-major (the particles of run 0 first).  origin is in each run's own cell
+ * coordinates; run r's particles wrap inside its rows; each run's undulator K is used for
+ * match_undulator.  Ids are numbered 0..n-1 across the runs in that order.  Also valid on a
+ * single-run context (n_run[0] = n). */
+int pic_load_species_batch(pic_ctx *ctx, const pic_species *sp, const int64_t *n_run,
+                           const double *x, const double *u, const double *w, int frame,
+                           int *species_id);
+
 /* Static lab element transformed into the RRF.  PIC_EXT_PLANAR_UNDULATOR: lab field
  * B_y = B0 f(z) cos(k_u z + phase), B0 = K k_u (K = e B0/(m c k_u)), k_u = 2 pi/lambda_u;
  * f = 0 before z_start, linear to 1 over ramp_len (the entrance "gentle slope", Sec.
@@ -143,6 +167,11 @@ typedef struct {
     double K, lambda_u, phase, z_start, ramp_len;
 } pic_external;
 int pic_set_external_field(pic_ctx *ctx, const pic_external *f);
+
+/* Ensemble form: f[runs] (host), one element per run; the runs may differ in K only (same
+ * type, lambda_u, phase, z_start and ramp_len, and no entrance ramp: the undulator fills each
+ * periodic run).  On an ensemble, pic_set_external_field gives every run the same K. */
+int pic_set_external_field_batch(pic_ctx *ctx, const pic_external *f);
 
 /* Background plasma (Sec. "Relativistic booster frame": N'_e = gamma_R N_e, Eq. Nnormi;
  * static lab elements move at -c beta_R, Eq. Vprime; plasma enters the window on one side
@@ -165,6 +194,13 @@ typedef struct {
 } pic_plasma;
 int pic_set_plasma(pic_ctx *ctx, const pic_plasma *p, int *electron_id, int *ion_id);
 
+/* Periodic z (a single run or an ensemble): the lattice fills the whole box once (planes
+ * 0 .. ppc_z * nz - 1, each run's planes with the profile in the run's own coordinates) and
+ * drifts around it; no plane is injected later.  Ensemble form: density_scale (host FP64
+ * [runs], >= 0) multiplies the profile of run r. */
+int pic_set_plasma_batch(pic_ctx *ctx, const pic_plasma *p, const double *density_scale,
+                         int *electron_id, int *ion_id);
+
 /* Advance n steps (Sec. "Relativistic booster frame": leap-frog push and current weighting
  * for Eq. Max3-Max4, Maxwell Eq. Max1-Max2).  Per step: every `sort_every` steps a per-tile
  * counting sort of each species by cell; per species a fused kernel gathers E^n, B^n (same
@@ -173,8 +209,21 @@ int pic_set_plasma(pic_ctx *ctx, const pic_plasma *p, int *electron_id, int *ion
  * deposits the Esirkepov current J^{n+1/2}; then B^{n+1/2} = B^n - dt/2 curl E^n,
  * E^{n+1} = E^n + dt (curl B^{n+1/2} - J), B^{n+1} = B^{n+1/2} - dt/2 curl E^{n+1} (with CPML);
  * then the window shifts due by step n+1 and plasma planes entering the front are injected.
- * Asynchronous on the context stream. */
+ * The current of a tile is summed exactly in fixed point (order-independent) with a scale set per
+ * species and step from four times the largest displacement of the previous step; a particle
+ * moving further, and every particle of a tile holding fewer than 32, adds its current with
+ * float atomics instead.  Asynchronous on the context stream. */
 int pic_step(pic_ctx *ctx, int64_t n);
+
+/* Autotuner of the tile-sort cadence (tile and sort sizes picked by an autotuner the project
+ * writes).  Runs trials of whole sort periods (>= 8 steps each) with sort_every = 1, 2, 3, 4, 6,
+ * 8, 12, 16, 24, 32 (up to max_sort_every), each starting with a sort, in two passes (ascending,
+ * then descending), times them with CUDA events on the context stream and keeps the fastest per
+ * step (a rarer sort must win by 2 %).  The trial steps are real steps: the simulation advances
+ * by their total (about 200 steps for max_sort_every = 16).  A
+ * fast drift (cells per step) favours frequent sorts, a slow one rare sorts; the tile stays the
+ * compiled 8x8x8 region.  *sort_every_out (may be NULL) receives the choice.  Synchronous. */
+int pic_autotune(pic_ctx *ctx, int max_sort_every, int *sort_every_out);
 
 /* Wait for the context stream; returns PIC_ERR_DEVICE if a kernel raised the error word. */
 int pic_sync(pic_ctx *ctx);
@@ -202,7 +251,7 @@ int pic_set_fields(pic_ctx *ctx, int which, const float *src, size_t n);
 int pic_get_particles(pic_ctx *ctx, int species_id, int64_t cap, int64_t *n_out, int32_t *cell,
                       float *off, float *u, float *w, int64_t *id);
 
-/* FP64 beam diagnostics (the benchmark spec precision split: FP64 for back-transformed diagnostics
+/* FP64 beam diagnostics (precision split: FP64 for back-transformed diagnostics
  * and conservation sums).  frame PIC_FRAME_BOOSTED: at t' = step dt, positions in
  * normalised RRF length (z' absolute, window shifts included).  PIC_FRAME_LAB: each
  * particle's RRF event and momentum are transformed back (inverse Eq. Lor1-Lor2) and drifted
@@ -219,6 +268,11 @@ typedef struct {
     double bunching, kinetic_energy, mean_t, field_energy;
 } pic_moments;
 int pic_get_moments(pic_ctx *ctx, int species_id, int frame, double k_bunch, pic_moments *out);
+
+/* pic_get_moments restricted to the particles and field cells of one run of an ensemble
+ * (0 <= run < runs); positions are in the run's own coordinates.  Synchronous. */
+int pic_get_moments_run(pic_ctx *ctx, int species_id, int run, int frame, double k_bunch,
+                        pic_moments *out);
 
 /* Step count, window shifts and last injected plasma plane of the context: out[3]. */
 int pic_get_time(pic_ctx *ctx, int64_t out[3]);
@@ -237,6 +291,8 @@ typedef struct {
     double ms[8];
     int64_t events[8];
     int64_t kernels;
+    int64_t fallback;   /* particles whose current took global float atomics because they moved
+                           beyond the step's fixed-point range (see pic_step) */
 } pic_trace;
 int pic_trace_enable(pic_ctx *ctx, int on);
 int pic_trace_read(pic_ctx *ctx, pic_trace *out);

@@ -514,6 +514,7 @@ static void o_inject_planes(osim *s, long m0, long m1)
         double dens = s->gR * o_profile(s, zlab);             /* Eq. Nnormi */
         double zg = zabs - s->bR * tp / s->d[2] - (double)s->shifts;
         double w = dens * s->d[0] * s->d[1] * s->d[2] / ((double)s->ppc[0] * s->ppc[1] * s->ppc[2]);
+        if (s->bc[2][0] == O_PERIODIC) zg -= floor(zg / (double)s->n[2]) * (double)s->n[2];
         for (int j = s->xr[2]; j < s->xr[3]; j++)
             for (int i = s->xr[0]; i < s->xr[1]; i++)
                 for (int b = 0; b < s->ppc[1]; b++)
@@ -558,6 +559,15 @@ void osim_set_plasma(void *h, int sp_e, int sp_i, const int *ppc, const int *xr,
     memcpy(s->zprof, zn, nprof * sizeof(double));
     memcpy(s->nprof_v, dn, nprof * sizeof(double));
     if (!fill) return; /* parameters only: the caller loads an existing plasma state */
+    if (s->bc[2][0] == O_PERIODIC) {
+        /* periodic box (reading): the lattice fills the whole box once, planes 0 .. p_z n_z - 1,
+         * and drifts around it; the density of plane m is the profile at its lab position at
+         * t' = 0 and travels with it.  No plane is ever injected. */
+        long m1 = (long)s->ppc[2] * s->n[2] - 1;
+        o_inject_planes(s, 0, m1);
+        s->m_last = m1;
+        return;
+    }
     double lo = (double)o_margin_lo(s->order) + (double)s->shifts + s->bR * (double)s->step * s->dt / s->d[2];
     long m0 = (long)ceil((double)s->ppc[2] * lo - 0.5);
     long m1 = o_plane_max(s, s->step, s->shifts);
@@ -832,7 +842,7 @@ static void o_step(osim *s)
         long due = o_shifts_due(s, s->step);
         while (s->shifts < due) o_window_shift(s);
     }
-    if (s->plasma) {
+    if (s->plasma && s->bc[2][0] != O_PERIODIC) {
         long m1 = o_plane_max(s, s->step, s->shifts);
         o_inject_planes(s, s->m_last + 1, m1);
         if (m1 > s->m_last) s->m_last = m1;

@@ -76,7 +76,7 @@ class pic_plasma(C.Structure):
 
 
 class pic_trace(C.Structure):
-    _fields_ = [("ms", C.c_double * 8), ("events", C.c_int64 * 8), ("kernels", C.c_int64)]
+    _fields_ = [("ms", C.c_double * 8), ("events", C.c_int64 * 8), ("kernels", C.c_int64), ("fallback", C.c_int64)]
 
 
 TRACE_CLASSES = ["sort", "push", "push_frozen", "fields", "window", "inject", "other", "unused"]
@@ -108,6 +108,12 @@ def lib(build_if_missing: bool = True):
         P = C.POINTER
         sigs = {
             "pic_create": [P(vp), pic_grid, P(d), d, d, P(pic_boundaries), i, P(pic_device)],
+            "pic_create_batch": [P(vp), i, pic_grid, P(d), d, d, P(pic_boundaries), i, P(pic_device)],
+            "pic_load_species_batch": [vp, P(pic_species), P(i64), vp, vp, vp, i, P(i)],
+            "pic_set_external_field_batch": [vp, P(pic_external)],
+            "pic_set_plasma_batch": [vp, P(pic_plasma), P(d), P(i), P(i)],
+            "pic_get_moments_run": [vp, i, i, i, d, P(pic_moments)],
+            "pic_autotune": [vp, i, P(i)],
             "pic_set_tuning": [vp, P(pic_tuning)],
             "pic_load_species": [vp, P(pic_species), i64, vp, vp, vp, i, P(i)],
             "pic_set_external_field": [vp, P(pic_external)],
@@ -155,12 +161,15 @@ class Sim:
 
     def __init__(self, grid, d, dt, gamma_R, bc=((0, 0), (0, 0), (0, 0)), pml=0, order=1,
                  moving_window=False, window_v=0.0, device=0, stream=None, tuning=None,
-                 torch_allocator=True):
+                 torch_allocator=True, runs=1):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("gbpic needs a CUDA GPU (no CPU fallback)")
         self.L = lib()
-        self.grid = tuple(int(v) for v in grid)
+        self.runs = int(runs)
+        self.run_grid = tuple(int(v) for v in grid)
+        # an ensemble stacks its runs along z: the context's grid has runs * nz rows
+        self.grid = (self.run_grid[0], self.run_grid[1], self.run_grid[2] * self.runs)
         self.d = tuple(float(v) for v in d)
         self.dt = float(dt)
         self.gamma_R = float(gamma_R)
@@ -205,8 +214,8 @@ class Sim:
         b.window_v = float(window_v)
         h = C.c_void_p()
         darr = (C.c_double * 3)(*self.d)
-        r = self.L.pic_create(C.byref(h), pic_grid(*self.grid), darr, self.dt, self.gamma_R, C.byref(b),
-                              self.order, C.byref(dev))
+        r = self.L.pic_create_batch(C.byref(h), self.runs, pic_grid(*self.run_grid), darr, self.dt, self.gamma_R,
+                                    C.byref(b), self.order, C.byref(dev))
         if r != PIC_OK:
             raise PicError(r, self.L.pic_last_error(None).decode())
         self.h = h
@@ -255,6 +264,44 @@ class Sim:
                                             int(frame), C.byref(sid)))
         return sid.value
 
+    def load_species_batch(self, q, m, n_run, x, u, w=None, frame=PIC_FRAME_LAB, origin=(0.0, 0.0, 0.0),
+                           capacity=0, frozen=False, match_undulator=False):
+        """Ensemble load: n_run[r] particles into run r; x, u: (3, sum n_run) FP64, run-major."""
+        counts = np.ascontiguousarray(n_run, np.int64)
+        assert counts.size == self.runs
+        n = int(counts.sum())
+        xs, us = _f64_c(x), _f64_c(u)
+        ws = _f64_c(w) if w is not None else None
+        sp = pic_species(float(q), float(m), int(bool(frozen)), int(max(capacity, n, 1)),
+                         (C.c_double * 3)(*[float(v) for v in origin]), int(bool(match_undulator)))
+        sid = C.c_int()
+        self._check(self.L.pic_load_species_batch(self.h, C.byref(sp), counts.ctypes.data_as(C.POINTER(C.c_int64)),
+                                                  _ptr(xs), _ptr(us), _ptr(ws), int(frame), C.byref(sid)))
+        return sid.value
+
+    def set_external_field_batch(self, K_run, lambda_u, phase=0.0, kind=PIC_EXT_PLANAR_UNDULATOR):
+        arr = (pic_external * self.runs)(*[pic_external(int(kind), float(k), float(lambda_u), float(phase),
+                                                        -math.inf, -1.0) for k in K_run])
+        self._check(self.L.pic_set_external_field_batch(self.h, arr))
+
+    def set_plasma_batch(self, ppc, x_range, z_nodes, density, density_scale, capacity=0):
+        zn = np.ascontiguousarray(z_nodes, np.float64)
+        dn = np.ascontiguousarray(density, np.float64)
+        sc = np.ascontiguousarray(density_scale, np.float64)
+        assert sc.size == self.runs
+        p = pic_plasma((C.c_int * 3)(*ppc), (C.c_int * 4)(*x_range), int(zn.size),
+                       zn.ctypes.data_as(C.POINTER(C.c_double)), dn.ctypes.data_as(C.POINTER(C.c_double)),
+                       int(capacity))
+        e, i = C.c_int(), C.c_int()
+        self._check(self.L.pic_set_plasma_batch(self.h, C.byref(p), sc.ctypes.data_as(C.POINTER(C.c_double)),
+                                                C.byref(e), C.byref(i)))
+        return e.value, i.value
+
+    def get_moments_run(self, sid, run, frame=PIC_FRAME_BOOSTED, k_bunch=0.0):
+        m = pic_moments()
+        self._check(self.L.pic_get_moments_run(self.h, int(sid), int(run), int(frame), float(k_bunch), C.byref(m)))
+        return dict(zip(MOMENT_NAMES, list(m.v)))
+
     def set_external_field(self, K, lambda_u, phase=0.0, z_start=-math.inf, ramp_len=-1.0,
                            kind=PIC_EXT_PLANAR_UNDULATOR):
         f = pic_external(int(kind), float(K), float(lambda_u), float(phase), float(z_start), float(ramp_len))
@@ -273,6 +320,12 @@ class Sim:
     # ------------------------------------------------------------------ stepping
     def step(self, n=1):
         self._check(self.L.pic_step(self.h, int(n)))
+
+    def autotune(self, max_sort_every=16):
+        """Pick the sort cadence by timed trials (advances the simulation); returns it."""
+        out = C.c_int()
+        self._check(self.L.pic_autotune(self.h, int(max_sort_every), C.byref(out)))
+        return out.value
 
     def sync(self):
         self._check(self.L.pic_sync(self.h))
@@ -327,7 +380,7 @@ class Sim:
         self._check(self.L.pic_trace_read(self.h, C.byref(t)))
         return {"ms": {TRACE_CLASSES[k]: t.ms[k] for k in range(7)},
                 "events": {TRACE_CLASSES[k]: int(t.events[k]) for k in range(7)},
-                "kernels": int(t.kernels)}
+                "kernels": int(t.kernels), "fallback": int(t.fallback)}
 
     def get_time(self):
         out = (C.c_int64 * 3)()
@@ -363,4 +416,29 @@ def from_workload(w, device=0, stream=None, tuning=None, beam=True, beam_arrays=
         b = w.beam
         ids["beam"] = sim.load_species(b.q, b.m, x, u, wt, frame=PIC_FRAME_LAB, origin=b.origin,
                                        match_undulator=bool(w.undulator is not None and w.undulator.match))
+    return sim, ids
+
+
+def from_ensemble(e, device=0, stream=None, tuning=None, beam=True):
+    """Create an ensemble Sim for a :class:`workloads.Ensemble` (runs stacked along z) and load
+    every run's undulator K, plasma density and seeded beam.  Returns (sim, species ids dict)."""
+    from . import workloads as W
+    b = e.base
+    t = tuning if tuning is not None else {"tile": b.tile, "sort_every": b.sort_every, "margin": 1}
+    sim = Sim(b.grid, b.d, b.dt, b.gamma_R, bc=b.bc, pml=b.pml, order=b.order, device=device, stream=stream,
+              tuning=t, runs=e.runs)
+    ids = {}
+    if b.undulator is not None:
+        sim.set_external_field_batch(e.K, b.undulator.lambda_u, b.undulator.phase)
+    if b.plasma is not None:
+        p = b.plasma
+        ids["plasma_e"], ids["plasma_i"] = sim.set_plasma_batch(p.ppc, p.xrange, p.z_nodes, p.n_nodes, e.dens_scale)
+    if beam and b.beam is not None:
+        parts = [W.sample_beam(W.ensemble_run(e, r)) for r in range(e.runs)]
+        x = np.concatenate([q[0] for q in parts], axis=1)
+        u = np.concatenate([q[1] for q in parts], axis=1)
+        wt = np.concatenate([q[2] for q in parts])
+        ids["beam"] = sim.load_species_batch(b.beam.q, b.beam.m, [q[0].shape[1] for q in parts], x, u, wt,
+                                             frame=PIC_FRAME_LAB, origin=b.beam.origin,
+                                             match_undulator=bool(b.undulator is not None and b.undulator.match))
     return sim, ids

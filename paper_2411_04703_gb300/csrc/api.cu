@@ -91,6 +91,9 @@ int check_ctx(pic_ctx *c)
     return PIC_OK;
 }
 
+// Largest displacement (cells) along d in one step: the speed of light, min(1, dt / d_d).
+double light_bound(const pic_ctx *c, int d) { return std::min(1.0, c->dt / c->d[d]); }
+
 int make_species(pic_ctx *c, double q, double m, int frozen, int64_t cap, int *sid, bool lattice = false)
 {
     if (c->nsp >= kMaxSpecies) return fail(c, PIC_ERR_ARG, "too many species (max 8)");
@@ -123,9 +126,32 @@ int make_species(pic_ctx *c, double q, double m, int frozen, int64_t cap, int *s
         (r = alloc_zero(c, &s.mom2, cap)) || (r = alloc_zero(c, &s.id, cap)) || (r = alloc_zero(c, &s.id2, cap)) ||
         (r = alloc_zero(c, &s.count, 4)) || (r = alloc_zero(c, &s.rank, cap)) ||
         (r = alloc_zero(c, &s.items, s.max_items)) || (r = alloc_zero(c, &s.cell_start, c->n_keys + 1)) ||
-        (r = alloc_zero(c, &s.chunk_start, c->ntiles + 1)))
+        (r = alloc_zero(c, &s.chunk_start, c->ntiles + 1)) || (r = alloc_zero(c, &s.dlim, 4)) ||
+        (r = alloc_zero(c, &s.sparse_start, c->ntiles + 1)) || (r = alloc_zero(c, &s.sparse_tiles, c->ntiles)) ||
+        (r = alloc_zero(c, &s.dmax, 4)))
         return r;
+    {
+        // the first deposit assumes the speed of light
+        const float b[4] = {(float)light_bound(c, 0), (float)light_bound(c, 1), (float)light_bound(c, 2), 0.f};
+        CK(cudaMemcpyAsync(s.dlim, b, sizeof(b), cudaMemcpyHostToDevice, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    if (c->runs > 1) {
+        s.wmax_run.assign(c->runs, 0.0);
+        if ((r = alloc_zero(c, &s.wrun, (size_t)c->runs))) return r;
+    }
     *sid = c->nsp++;
+    return PIC_OK;
+}
+
+// Upload the per-run largest weights of species s (ensembles).
+int upload_wrun(pic_ctx *c, Species &s)
+{
+    if (!s.wrun) return PIC_OK;
+    std::vector<float> w(s.wmax_run.size());
+    for (size_t q = 0; q < w.size(); q++) w[q] = (float)s.wmax_run[q];
+    CK(cudaMemcpyAsync(s.wrun, w.data(), sizeof(float) * w.size(), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
     return PIC_OK;
 }
 
@@ -217,6 +243,7 @@ int record_view(pic_ctx *c, int si, RecordView &v)
 
 int inject_due(pic_ctx *c)
 {
+    if (c->bc[2][0] == PIC_BC_PERIODIC) return PIC_OK;   // the periodic lattice is filled once
     const int64_t m1 = plane_max(c, c->step, c->shifts);
     if (m1 <= c->m_last) return PIC_OK;
     const int64_t per_plane = (int64_t)(c->xr[1] - c->xr[0]) * (c->xr[3] - c->xr[2]) * c->ppc[0] * c->ppc[1];
@@ -254,6 +281,7 @@ ExtDev ext_step(const pic_ctx *c)
     x.kdz = (float)(kp * c->d[2]);
     x.theta = (float)std::fmod(kp * ((double)c->shifts * c->d[2] + c->bR * tp) + c->phase0, two_pi);
     x.phase_tab = c->phase_tab;
+    x.amp_tab = c->amp_tab;
     if (std::isfinite(c->z_start) && c->ramp >= 0.0) {
         const double a = c->gR * c->d[2];
         const double b = c->gR * ((double)c->shifts * c->d[2] + c->bR * tp) - c->z_start;
@@ -287,6 +315,8 @@ GridDev grid_dev(const pic_ctx *c)
     g.mlo = margin_lo(c);
     g.mhi = margin_hi(c);
     g.ncell = c->ncell;
+    g.cc = c->cc;
+    g.nzr = c->nzr;
     return g;
 }
 
@@ -303,6 +333,8 @@ TileDev tile_dev(const pic_ctx *c, const Species &s)
     for (int d = 0; d < 3; d++) t.R[d] = c->T[d] + 2 * c->M + margin_lo(c) + margin_hi(c);
     t.cell_start = s.cell_start;
     t.items = s.items;
+    t.sparse_tiles = s.sparse_tiles;
+    t.cc = c->cc;
     return t;
 }
 
@@ -317,14 +349,15 @@ SpeciesDev species_dev(const pic_ctx *c, const Species &s)
     const double V = c->d[0] * c->d[1] * c->d[2];
     for (int k = 0; k < 3; k++) {
         d.cf[k] = (float)(-s.q * c->d[k] / (c->dt * V));
-        // |contribution| <= |cf| w |prefix DS| |A A + DS DS/12|; |prefix DS| <= the displacement
-        // bound min(1, dt/d_k) (speed of light) and |A A + DS DS/12| <= 1.1: map it to 2^30
-        const double pmax = std::min(1.0, c->dt / c->d[k]);
-        const double mx = 1.1 * std::fabs((double)d.cf[k]) * s.wmax * pmax;
-        const double sc = mx > 0 ? std::ldexp(1.0, 30) / mx : 1.0;
-        d.jscale[k] = (float)sc;
-        d.jinv[k] = 1.0 / (double)d.jscale[k];
+        // |contribution| <= |cf| w |prefix DS| |A A + DS DS/12|; |prefix DS| <= |d_k| and
+        // |A A + DS DS/12| <= 1.1
+        d.jb[k] = (float)(1.1 * std::fabs((double)d.cf[k]));
     }
+    d.wmax = (float)s.wmax;
+    d.wrun = s.wrun;
+    d.dlim = s.dlim;
+    d.dmax = s.dmax;
+    d.nfall = c->nfall;
     d.frozen = s.frozen;
     d.cap = (int)s.cap;
     return d;
@@ -346,17 +379,34 @@ PmlDev pml_dev(const pic_ctx *c)
 
 }  // namespace gbpic
 
-extern "C" {
+namespace {
 
-int pic_create(pic_ctx **out, pic_grid grid, const double dx[3], double dt, double gamma_boost,
-               const pic_boundaries *bc, int shape_order, const pic_device *dev)
+int bits_for(int n)
+{
+    int b = 0;
+    while ((1 << b) < n) b++;
+    return b;
+}
+
+// A context of `runs` independent runs of grid.nz rows each, stacked along z (runs = 1: one run).
+int create_impl(pic_ctx **out, int runs, pic_grid grid, const double dx[3], double dt, double gamma_boost,
+                const pic_boundaries *bc, int shape_order, const pic_device *dev)
 {
     if (!out) return fail(nullptr, PIC_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (!dx || !bc) return fail(nullptr, PIC_ERR_ARG, "dx and bc are required");
-    const int n[3] = {grid.nx, grid.ny, grid.nz};
-    if (n[0] < 1 || n[1] < 1 || n[2] < 1 || n[0] > 1024 || n[1] > 1024 || n[2] > 2048)
-        return fail(nullptr, PIC_ERR_ARG, "grid must be 1..1024 x 1..1024 x 1..2048 cells");
+    if (runs < 1 || runs > 4096) return fail(nullptr, PIC_ERR_ARG, "runs must be 1..4096");
+    if (grid.nz < 1 || (int64_t)grid.nz * runs > (1 << 20)) return fail(nullptr, PIC_ERR_ARG, "nz * runs must be 1..2^20");
+    const int n[3] = {grid.nx, grid.ny, grid.nz * runs};
+    if (n[0] < 1 || n[1] < 1 || n[0] > 1024 || n[1] > 1024)
+        return fail(nullptr, PIC_ERR_ARG, "nx and ny must be 1..1024 cells");
+    if (bits_for(n[0]) + bits_for(n[1]) + bits_for(n[2]) > 31)
+        return fail(nullptr, PIC_ERR_ARG, "grid too large: the packed cell index needs more than 31 bits");
+    if (runs > 1) {
+        if (bc->face[2][0] != PIC_BC_PERIODIC || bc->face[2][1] != PIC_BC_PERIODIC)
+            return fail(nullptr, PIC_ERR_ARG, "ensemble runs are stacked along z: z must be periodic");
+        if (grid.nz % 8 != 0) return fail(nullptr, PIC_ERR_ARG, "ensemble runs need nz a multiple of the tile size 8");
+    }
     if (shape_order != 1 && shape_order != 2) return fail(nullptr, PIC_ERR_ARG, "shape_order must be 1 (CIC) or 2 (TSC)");
     double inv2 = 0;
     for (int d = 0; d < 3; d++) {
@@ -412,6 +462,12 @@ int pic_create(pic_ctx **out, pic_grid grid, const double dx[3], double dt, doub
         c->bc[d][0] = bc->face[d][0];
         c->bc[d][1] = bc->face[d][1];
     }
+    c->runs = runs;
+    c->nzr = grid.nz;
+    c->cc.sj = bits_for(n[0]);
+    c->cc.sk = c->cc.sj + bits_for(n[1]);
+    c->cc.mi = (1 << c->cc.sj) - 1;
+    c->cc.mj = (1 << (c->cc.sk - c->cc.sj)) - 1;
     c->dt = dt;
     c->gR = gamma_boost;
     c->bR = std::sqrt(1.0 - 1.0 / (gamma_boost * gamma_boost));
@@ -430,7 +486,7 @@ int pic_create(pic_ctx **out, pic_grid grid, const double dx[3], double dt, doub
     };
     int r;
     if ((r = alloc_zero(c, &c->E, 3 * c->ncell)) || (r = alloc_zero(c, &c->B, 3 * c->ncell)) ||
-        (r = alloc_zero(c, &c->J, 3 * c->ncell)) || (r = alloc_zero(c, &c->err, 4)) ||
+        (r = alloc_zero(c, &c->J, 3 * c->ncell)) || (r = alloc_zero(c, &c->err, 4)) || (r = alloc_zero(c, &c->nfall, 1)) ||
         (r = alloc_zero(c, &c->work, 2 * kMaxSpecies)) || (r = alloc_zero(c, &c->red, 512 * 16 + 1024)) ||
         (r = alloc_zero(c, &c->shift_tab, 24)) || (r = alloc_tile_scratch(c)))
         return bail(r);
@@ -456,7 +512,11 @@ int pic_create(pic_ctx **out, pic_grid grid, const double dx[3], double dt, doub
                 }
             }
         }
-        if (cudaMemcpy(c->pml_coef, coef.data(), coef.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+        // on the context stream, after the zeroing memset (a legacy-stream cudaMemcpy does not wait
+        // for a non-blocking stream, and the memset could land after it)
+        if (cudaMemcpyAsync(c->pml_coef, coef.data(), coef.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(c->stream) != cudaSuccess)
             return bail(fail_cuda(c, cudaGetLastError(), "copy PML coefficients"));
     }
     {
@@ -472,12 +532,30 @@ int pic_create(pic_ctx **out, pic_grid grid, const double dx[3], double dt, doub
                 tab.push_back(c->psiB + q * c->ncell);
             }
         c->shift_n = (int)tab.size();
-        if (cudaMemcpy(c->shift_tab, tab.data(), tab.size() * sizeof(float *), cudaMemcpyHostToDevice) != cudaSuccess)
+        if (cudaMemcpyAsync(c->shift_tab, tab.data(), tab.size() * sizeof(float *), cudaMemcpyHostToDevice, c->stream) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(c->stream) != cudaSuccess)
             return bail(fail_cuda(c, cudaGetLastError(), "copy shift table"));
     }
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return bail(fail_cuda(c, cudaGetLastError(), "create sync"));
     *out = c;
     return PIC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pic_create(pic_ctx **out, pic_grid grid, const double dx[3], double dt, double gamma_boost,
+               const pic_boundaries *bc, int shape_order, const pic_device *dev)
+{
+    return create_impl(out, 1, grid, dx, dt, gamma_boost, bc, shape_order, dev);
+}
+
+int pic_create_batch(pic_ctx **out, int runs, pic_grid grid, const double dx[3], double dt, double gamma_boost,
+                     const pic_boundaries *bc, int shape_order, const pic_device *dev)
+{
+    return create_impl(out, runs, grid, dx, dt, gamma_boost, bc, shape_order, dev);
 }
 
 int pic_set_tuning(pic_ctx *c, const pic_tuning *t)
@@ -492,8 +570,10 @@ int pic_set_tuning(pic_ctx *c, const pic_tuning *t)
     if (t->margin < 0 || t->margin > 2) return fail(c, PIC_ERR_ARG, "margin must be 0..2");
     int R3 = 1;
     for (int d = 0; d < 3; d++) R3 *= t->tile[d] + 2 * t->margin + margin_lo(c) + margin_hi(c);
-    if ((size_t)R3 * 12 * sizeof(float) + 16 * 1024 > 220 * 1024)
+    if ((size_t)R3 * 12 * sizeof(float) + 40 * 1024 > 224 * 1024)
         return fail(c, PIC_ERR_ARG, "tile region exceeds shared memory");
+    if (c->runs > 1 && c->nzr % t->tile[2] != 0)
+        return fail(c, PIC_ERR_ARG, "ensemble: the tile's z size must divide the rows of a run");
     for (int d = 0; d < 3; d++) c->T[d] = t->tile[d];
     c->sort_every = t->sort_every;
     c->M = t->margin;
@@ -501,12 +581,24 @@ int pic_set_tuning(pic_ctx *c, const pic_tuning *t)
     return alloc_tile_scratch(c);
 }
 
-int pic_load_species(pic_ctx *c, const pic_species *sp, int64_t n, const double *x, const double *u,
-                     const double *w, int frame, int *species_id)
+}  // extern "C"
+
+namespace {
+
+// Creates a species and loads n_run[r] particles into each run r (arrays run-major, [3][n] with
+// n the total).
+int load_impl(pic_ctx *c, const pic_species *sp, const int64_t *n_run, int nr, const double *x, const double *u,
+              const double *w, int frame, int *species_id)
 {
     int r = check_ctx(c);
     if (r) return r;
-    if (!sp || !species_id || n < 0) return fail(c, PIC_ERR_ARG, "invalid species arguments");
+    if (!sp || !species_id || !n_run) return fail(c, PIC_ERR_ARG, "invalid species arguments");
+    int64_t n = 0;
+    for (int q = 0; q < nr; q++) {
+        if (n_run[q] < 0) return fail(c, PIC_ERR_ARG, "negative particle count");
+        n += n_run[q];
+    }
+    if (n >= (int64_t)std::numeric_limits<int>::max() - kChunk) return fail(c, PIC_ERR_ARG, "too many particles");
     if (n > 0 && (!x || !u)) return fail(c, PIC_ERR_ARG, "x and u are required when n > 0");
     if (frame != PIC_FRAME_LAB && frame != PIC_FRAME_BOOSTED) return fail(c, PIC_ERR_ARG, "unknown frame");
     const int64_t cap = std::max<int64_t>(sp->capacity, std::max<int64_t>(n, 1));
@@ -523,13 +615,29 @@ int pic_load_species(pic_ctx *c, const pic_species *sp, int64_t n, const double 
         CK(cudaMemcpyAsync(du, u, sizeof(double) * 3 * n, cudaMemcpyDefault, c->stream));
         if (w) CK(cudaMemcpyAsync(dw, w, sizeof(double) * n, cudaMemcpyDefault, c->stream));
     }
-    CK(launch_load(c, sid, n, dx, du, dw, frame, sp->origin, sp->match_undulator, s.next_id));
+    int64_t off = 0;
+    for (int q = 0; q < nr; q++) {
+        CK(launch_load(c, sid, n_run[q], dx ? dx + off : nullptr, du ? du + off : nullptr, dw ? dw + off : nullptr,
+                       frame, sp->origin, sp->match_undulator, s.next_id + off, q, n));
+        off += n_run[q];
+    }
     s.next_id += n;
     s.bound += n;
     if (n > 0) {
         double wm = 0;
         CK(species_wmax(c, sid, &wm));
         s.wmax = std::max(s.wmax, wm);
+    }
+    CK(launch_dlim_from_momenta(c, sid));
+    if (c->runs > 1) {
+        int64_t o2 = 0;
+        for (int q = 0; q < nr; q++) {
+            double wm = n_run[q] > 0 ? 1.0 : 0.0;
+            if (dw && n_run[q] > 0) CK(absmax_f64(c, dw + o2, n_run[q], &wm));
+            s.wmax_run[q] = std::max(s.wmax_run[q], wm);
+            o2 += n_run[q];
+        }
+        if ((r = upload_wrun(c, s))) return r;
     }
     if (n > 0) {
         CK(cudaStreamSynchronize(c->stream));
@@ -539,6 +647,27 @@ int pic_load_species(pic_ctx *c, const pic_species *sp, int64_t n, const double 
     }
     *species_id = sid;
     return PIC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pic_load_species(pic_ctx *c, const pic_species *sp, int64_t n, const double *x, const double *u,
+                     const double *w, int frame, int *species_id)
+{
+    int r = check_ctx(c);
+    if (r) return r;
+    if (c->runs > 1) return fail(c, PIC_ERR_STATE, "ensemble context: load with pic_load_species_batch");
+    return load_impl(c, sp, &n, 1, x, u, w, frame, species_id);
+}
+
+int pic_load_species_batch(pic_ctx *c, const pic_species *sp, const int64_t *n_run, const double *x, const double *u,
+                           const double *w, int frame, int *species_id)
+{
+    int r = check_ctx(c);
+    if (r) return r;
+    return load_impl(c, sp, n_run, c->runs, x, u, w, frame, species_id);
 }
 
 int pic_set_external_field(pic_ctx *c, const pic_external *f)
@@ -560,16 +689,46 @@ int pic_set_external_field(pic_ctx *c, const pic_external *f)
     c->phase0 = f->phase;
     c->z_start = f->z_start;
     c->ramp = f->ramp_len;
+    if (c->runs > 1 && std::isfinite(f->z_start) && f->ramp_len >= 0.0)
+        return fail(c, PIC_ERR_ARG, "ensemble: the undulator must fill the periodic box (no entrance ramp)");
     if (!c->phase_tab && (r = alloc_zero(c, &c->phase_tab, c->n[2]))) return r;
     std::vector<float> tab(c->n[2]);
     const double kdz = c->ku * c->gR * c->d[2];
-    for (int k = 0; k < c->n[2]; k++) tab[k] = (float)std::fmod(kdz * k, 2.0 * M_PI);
+    // phase of row k in its own run's coordinates (k mod nzr; k for a single run)
+    for (int k = 0; k < c->n[2]; k++) tab[k] = (float)std::fmod(kdz * (k % c->nzr), 2.0 * M_PI);
     CK(cudaMemcpyAsync(c->phase_tab, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->B0_run.clear();
+    return PIC_OK;
+}
+
+int pic_set_external_field_batch(pic_ctx *c, const pic_external *f)
+{
+    int r = check_ctx(c);
+    if (r) return r;
+    if (!f) return fail(c, PIC_ERR_ARG, "external field is NULL");
+    for (int q = 1; q < c->runs; q++)
+        if (f[q].type != f[0].type || f[q].lambda_u != f[0].lambda_u || f[q].phase != f[0].phase ||
+            f[q].z_start != f[0].z_start || f[q].ramp_len != f[0].ramp_len)
+            return fail(c, PIC_ERR_ARG, "ensemble runs may differ in K only");
+    if ((r = pic_set_external_field(c, &f[0]))) return r;
+    if (f[0].type == PIC_EXT_NONE) return PIC_OK;
+    c->B0_run.resize(c->runs);
+    for (int q = 0; q < c->runs; q++) c->B0_run[q] = f[q].K * c->ku;
+    if (!c->amp_tab && (r = alloc_zero(c, &c->amp_tab, c->n[2]))) return r;
+    std::vector<float> amp(c->n[2]);
+    for (int k = 0; k < c->n[2]; k++) amp[k] = (float)(c->gR * c->B0_run[k / c->nzr]);
+    CK(cudaMemcpyAsync(c->amp_tab, amp.data(), amp.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return PIC_OK;
 }
 
-int pic_set_plasma(pic_ctx *c, const pic_plasma *p, int *electron_id, int *ion_id)
+}  // extern "C"
+
+namespace {
+
+// Background plasma; scale: density factor of each run (ensembles) or NULL.
+int plasma_impl(pic_ctx *c, const pic_plasma *p, const double *scale, int *electron_id, int *ion_id)
 {
     int r = check_ctx(c);
     if (r) return r;
@@ -606,26 +765,63 @@ int pic_set_plasma(pic_ctx *c, const pic_plasma *p, int *electron_id, int *ion_i
     c->plasma = 1;
     c->sp_e = se;
     c->sp_i = si;
+    if (c->runs > 1) {
+        c->dens_run.assign(c->runs, 1.0);
+        if (scale)
+            for (int q = 0; q < c->runs; q++) {
+                if (!(scale[q] >= 0.0)) return fail(c, PIC_ERR_ARG, "density scales must be >= 0");
+                c->dens_run[q] = scale[q];
+            }
+        if ((r = alloc_zero(c, &c->dens_scale, (size_t)c->runs))) return r;
+        CK(cudaMemcpyAsync(c->dens_scale, c->dens_run.data(), sizeof(double) * c->runs, cudaMemcpyHostToDevice, c->stream));
+    }
     {
         double nmax = 0;
         for (int i = 0; i < p->n_nodes; i++) nmax = std::max(nmax, std::fabs(p->density[i]));
-        const double wm = c->gR * nmax * c->d[0] * c->d[1] * c->d[2] / ((double)c->ppc[0] * c->ppc[1] * c->ppc[2]);
+        const double wm1 = c->gR * nmax * c->d[0] * c->d[1] * c->d[2] / ((double)c->ppc[0] * c->ppc[1] * c->ppc[2]);
+        double wm = wm1;
+        if (c->runs > 1) {
+            wm *= *std::max_element(c->dens_run.begin(), c->dens_run.end());
+            for (int q = 0; q < c->runs; q++) c->sp[se].wmax_run[q] = wm1 * c->dens_run[q];
+            if ((r = upload_wrun(c, c->sp[se]))) return r;
+        }
         c->sp[se].wmax = c->sp[si].wmax = wm;
     }
     CK(launch_lattice_profiles(c, si));
+    // open z: fill the window between the margins, later planes enter at the front; periodic z:
+    // the lattice fills the whole box once and drifts around it (no plane is ever injected)
+    const bool zper = c->bc[2][0] == PIC_BC_PERIODIC;
     const double lo = (double)margin_lo(c) + (double)c->shifts + c->bR * (double)c->step * c->dt / c->d[2];
-    const int64_t m0 = (int64_t)std::ceil((double)c->ppc[2] * lo - 0.5);
-    const int64_t m1 = plane_max(c, c->step, c->shifts);
+    const int64_t m0 = zper ? 0 : (int64_t)std::ceil((double)c->ppc[2] * lo - 0.5);
+    const int64_t m1 = zper ? (int64_t)c->ppc[2] * c->n[2] - 1 : plane_max(c, c->step, c->shifts);
     if ((m1 - m0 + 1) * per_plane > cap) return fail(c, PIC_ERR_CAPACITY, "plasma capacity below the window fill");
     if (m1 - m0 + 1 > c->sp[si].plane_cap) return fail(c, PIC_ERR_CAPACITY, "plasma lattice ring below the window fill");
     if (c->sp[si].plane_cap * per_plane >= (int64_t)std::numeric_limits<int>::max())
         return fail(c, PIC_ERR_ARG, "plasma lattice too large for 32-bit particle slots");
     CK(launch_inject(c, m0, m1));
+    CK(launch_dlim_from_momenta(c, se));
     c->m_last = m1;
     CK(cudaStreamSynchronize(c->stream));
     *electron_id = se;
     *ion_id = si;
     return PIC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pic_set_plasma(pic_ctx *c, const pic_plasma *p, int *electron_id, int *ion_id)
+{
+    return plasma_impl(c, p, nullptr, electron_id, ion_id);
+}
+
+int pic_set_plasma_batch(pic_ctx *c, const pic_plasma *p, const double *density_scale, int *electron_id, int *ion_id)
+{
+    int r = check_ctx(c);
+    if (r) return r;
+    if (!density_scale) return fail(c, PIC_ERR_ARG, "density_scale is NULL");
+    return plasma_impl(c, p, density_scale, electron_id, ion_id);
 }
 
 int pic_step(pic_ctx *c, int64_t nsteps)
@@ -634,7 +830,7 @@ int pic_step(pic_ctx *c, int64_t nsteps)
     if (r) return r;
     if (nsteps < 0) return fail(c, PIC_ERR_ARG, "negative step count");
     for (int64_t it = 0; it < nsteps; it++) {
-        if (c->step % c->sort_every == 0) {
+        if ((c->step - c->sort_base) % c->sort_every == 0) {
             TraceScope ts(c, TR_SORT);
             for (int si = 0; si < c->nsp; si++)
                 if (!c->sp[si].lattice) CK(launch_sort(c, si));
@@ -672,6 +868,61 @@ int pic_step(pic_ctx *c, int64_t nsteps)
         }
         if (c->plasma && (r = inject_due(c))) return r;
     }
+    return PIC_OK;
+}
+
+int pic_autotune(pic_ctx *c, int max_sort_every, int *sort_every_out)
+{
+    int r = check_ctx(c);
+    if (r) return r;
+    if (max_sort_every < 1) return fail(c, PIC_ERR_ARG, "max_sort_every must be >= 1");
+    cudaEvent_t a = nullptr, b = nullptr;
+    CK(cudaEventCreate(&a));
+    if (cudaEventCreate(&b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        return fail(c, PIC_ERR_CUDA, "cudaEventCreate failed");
+    }
+    std::vector<int> cand;
+    for (int se : {1, 2, 3, 4, 6, 8, 12, 16, 24, 32})
+        if (se <= max_sort_every) cand.push_back(se);
+    // two passes, ascending then descending, so that a cost that drifts as the run evolves
+    // weighs on every candidate alike
+    std::vector<double> tot(cand.size(), 0.0);
+    const int nc = (int)cand.size();
+    for (int pass = 0; pass < 2 && !r; pass++) {
+        for (int q = 0; q < nc; q++) {
+            const int idx = pass == 0 ? q : nc - 1 - q;
+            const int se = cand[idx];
+            // each trial starts right after a sort and covers whole sort periods (>= 8 steps)
+            const int64_t steps = ((std::max(8, se) + se - 1) / se) * (int64_t)se;
+            c->sort_every = se;
+            c->sort_base = c->step;   // the trial's first step sorts
+            cudaEventRecord(a, c->stream);
+            r = pic_step(c, steps);
+            cudaEventRecord(b, c->stream);
+            if (r) break;
+            float ms = 0;
+            if (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+                r = fail_cuda(c, cudaGetLastError(), "autotune timing");
+                break;
+            }
+            tot[idx] += ms / (double)steps;
+        }
+    }
+    double best_ms = 0;
+    int best = c->sort_every;
+    for (int q = 0; q < nc && !r; q++) {
+        // a rarer sort must beat the best so far by 2 % (timing noise; fresher sorting is safer)
+        if (best_ms == 0 || tot[q] < 0.98 * best_ms) {
+            best_ms = tot[q];
+            best = cand[q];
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (r) return r;
+    c->sort_every = best;
+    if (sort_every_out) *sort_every_out = best;
     return PIC_OK;
 }
 
@@ -777,9 +1028,9 @@ int pic_get_particles(pic_ctx *c, int sid, int64_t cap, int64_t *n_out, int32_t 
         std::memcpy(&cb, &P[p].w, sizeof(int));
         if (cb < 0) continue;
         if (cell) {
-            cell[k] = cell_i(cb);
-            cell[cap + k] = cell_j(cb);
-            cell[2 * cap + k] = cell_k(cb);
+            cell[k] = c->cc.i(cb);
+            cell[cap + k] = c->cc.j(cb);
+            cell[2 * cap + k] = c->cc.k(cb);
         }
         if (off) {
             off[k] = P[p].x;
@@ -798,7 +1049,11 @@ int pic_get_particles(pic_ctx *c, int sid, int64_t cap, int64_t *n_out, int32_t 
     return PIC_OK;
 }
 
-int pic_get_moments(pic_ctx *c, int sid, int frame, double k_bunch, pic_moments *out)
+}  // extern "C"
+
+namespace {
+
+int moments_impl(pic_ctx *c, int sid, int run, int frame, double k_bunch, pic_moments *out)
 {
     int r = check_ctx(c);
     if (r) return r;
@@ -807,11 +1062,28 @@ int pic_get_moments(pic_ctx *c, int sid, int frame, double k_bunch, pic_moments 
     RecordView view;
     if ((r = record_view(c, sid, view))) return r;
     double v[20];
-    CK(launch_moments(c, view.s, frame == PIC_FRAME_LAB ? PIC_FRAME_LAB : PIC_FRAME_BOOSTED, k_bunch, v));
-    CK(launch_field_energy(c, &v[19]));
+    CK(launch_moments(c, view.s, frame == PIC_FRAME_LAB ? PIC_FRAME_LAB : PIC_FRAME_BOOSTED, k_bunch, v, run));
+    CK(launch_field_energy(c, &v[19], run));
     static_assert(sizeof(pic_moments) == 20 * sizeof(double), "pic_moments layout");
     std::memcpy(out, v, sizeof(v));
     return PIC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pic_get_moments(pic_ctx *c, int sid, int frame, double k_bunch, pic_moments *out)
+{
+    return moments_impl(c, sid, -1, frame, k_bunch, out);
+}
+
+int pic_get_moments_run(pic_ctx *c, int sid, int run, int frame, double k_bunch, pic_moments *out)
+{
+    int r = check_ctx(c);
+    if (r) return r;
+    if (run < 0 || run >= c->runs) return fail(c, PIC_ERR_ARG, "run index outside the ensemble");
+    return moments_impl(c, sid, run, frame, k_bunch, out);
 }
 
 int pic_get_time(pic_ctx *c, int64_t out[3])
@@ -865,6 +1137,11 @@ int pic_trace_read(pic_ctx *c, pic_trace *out)
     }
     out->kernels = c->kernels;
     c->kernels = 0;
+    unsigned long long nf = 0;
+    CK(cudaMemcpyAsync(&nf, c->nfall, sizeof(nf), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemsetAsync(c->nfall, 0, sizeof(nf), c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    out->fallback = (int64_t)nf;
     return PIC_OK;
 }
 

@@ -16,6 +16,7 @@ constexpr int kMaxSpecies = 8;
 constexpr int kChunk = 4096;         // particles per work item of the particle kernel
 constexpr int kPushThreads = 512;
 constexpr int kGroup = kChunk / kPushThreads;   // consecutive particles of one lane per work item
+constexpr int kSparse = 32;   // a tile with fewer particles takes the global-memory path, one warp per tile
 
 // Error bits of the device error word.
 enum : int {
@@ -25,11 +26,21 @@ enum : int {
     ERR_NAN = 8,        // non-finite momentum produced by the push
 };
 
-// Cell index packed into 32 bits: i | j << 10 | k << 20; -1 marks a dummy particle.
-__host__ __device__ __forceinline__ int pack_cell(int i, int j, int k) { return i | (j << 10) | (k << 20); }
-__host__ __device__ __forceinline__ int cell_i(int c) { return c & 1023; }
-__host__ __device__ __forceinline__ int cell_j(int c) { return (c >> 10) & 1023; }
-__host__ __device__ __forceinline__ int cell_k(int c) { return c >> 20; }
+// Cell index packed into 31 bits: i | j << sj | k << sk, with sj the bits of nx and sk - sj
+// the bits of ny (set per context); -1 marks a dummy particle.
+struct CellCode {
+    int sj, sk, mi, mj;
+    __host__ __device__ __forceinline__ int pack(int i, int j, int k) const { return i | (j << sj) | (k << sk); }
+    __host__ __device__ __forceinline__ int i(int c) const { return c & mi; }
+    __host__ __device__ __forceinline__ int j(int c) const { return (c >> sj) & mj; }
+    __host__ __device__ __forceinline__ int k(int c) const { return c >> sk; }
+};
+
+// Ensembles: `runs` independent runs of nzr cells along z are stacked along z in one grid; z is
+// periodic inside each run's block of rows [b, b + nzr), b a multiple of nzr.  A single run has
+// nzr = nz.
+__host__ __device__ __forceinline__ int zblock(int k, int nzr) { return (k / nzr) * nzr; }
+__host__ __device__ __forceinline__ int zwrap(int k, int b, int nzr) { return k < b ? k + nzr : (k >= b + nzr ? k - nzr : k); }
 
 struct GridDev {
     int n[3];
@@ -39,6 +50,8 @@ struct GridDev {
     float dt_over_d[3];
     int mlo, mhi;        // particle margins of the non-periodic dims
     long long ncell;
+    CellCode cc;
+    int nzr;             // rows per run along z (z wraps inside a run's block when periodic)
 };
 
 struct PmlDev {
@@ -58,6 +71,7 @@ struct ExtDev {
     const float *phase_tab;  // (k'_u dz k) mod 2 pi for k = 0 .. nz-1
     int ramp_mode;        // 0: f = 1; 1: linear ramp; 2: step
     float ramp_a, ramp_b; // ramp argument r = ramp_a (k + off_z) + ramp_b
+    const float *amp_tab; // ensembles: gamma_R B0 of the run that owns row k; NULL: B0g everywhere
 };
 
 struct SpeciesDev {
@@ -67,8 +81,16 @@ struct SpeciesDev {
     int *count;           // [0] total slots in use, [1] sorted prefix, [2] tile work items
     float h_qm;           // 0.5 (q/m) dt
     float cf[3];          // -q d_c / (dt V): current of unit weight per unit W
-    float jscale[3];      // fixed-point scale of the shared-memory current (max contribution 2^30)
-    double jinv[3];       // 1 / jscale
+    // Fixed-point scale of the shared-memory current, set per work item: a contribution is at most
+    // jb_c w |d_c| (w the largest weight, d_c the displacement), and the scale maps the bound
+    // jb_c w dlim_c to at most 2^30.  dlim is adaptive: four times the largest |d_c| of the
+    // previous step; a particle moving further deposits with float atomics.
+    float jb[3];          // 1.1 |cf_c|
+    float wmax;           // largest |weight| the species holds
+    const float *wrun;    // ensembles: largest |weight| of each run; NULL: wmax everywhere
+    const float *dlim;    // device [3]: displacement bound of this step (cells)
+    unsigned *dmax;       // device [3]: largest |displacement| of this step (float bits, atomicMax)
+    unsigned long long *nfall;  // device counter of particles that took the float-atomic fallback
     int frozen;
     int cap;
 };
@@ -81,7 +103,9 @@ struct TileDev {
     int hl;               // stencil reach below the particle cell (1 CIC, 2 TSC)
     int R[3];             // shared-memory region size per dim
     const int *cell_start;   // [n_keys + 1]: first sorted slot of each key (8 keys per cell)
-    const int2 *items;       // (tile, chunk) work items
+    const int2 *items;       // (tile, chunk) work items of the tiles with >= kSparse particles
+    const int *sparse_tiles; // tiles with 1 .. kSparse-1 particles (count[3] of them)
+    CellCode cc;
 };
 
 struct FieldsDev {
@@ -122,9 +146,15 @@ struct Species {
     int64_t max_items = 0;
     int *cell_start = nullptr;  // device [n_keys + 1]
     int *chunk_start = nullptr; // device [ntiles + 1]
+    int *sparse_start = nullptr;  // device [ntiles + 1]: scan of the sparse-tile flags
+    int *sparse_tiles = nullptr;  // device [ntiles]: the sparse tiles
     int64_t bound = 0;        // host upper bound of count[0]
     int64_t next_id = 0;
     double wmax = 0;          // largest |weight| ever held (sets the fixed-point current scale)
+    std::vector<double> wmax_run;  // ensembles: largest |weight| ever held in each run
+    float *wrun = nullptr;    // device [runs] copy of wmax_run (ensembles)
+    float *dlim = nullptr;    // device [3] adaptive displacement bound of the current deposit
+    unsigned *dmax = nullptr; // device [3] largest displacement measured in the last push
     // lattice species (plasma ions): no particle records, a ring of lattice planes instead
     int lattice = 0;
     PlaneRec *planes = nullptr;  // device [plane_cap]; plane m in slot m mod plane_cap
@@ -141,6 +171,8 @@ struct pic_ctx {
     bool own_stream = false;
     int num_sms = 0;
     int n[3] = {0, 0, 0};
+    int runs = 1, nzr = 0;        // ensemble: runs stacked along z, nzr rows each
+    gbpic::CellCode cc{};
     double d[3] = {0, 0, 0};
     double dt = 0, gR = 1, bR = 0;
     int bc[3][2] = {{0, 0}, {0, 0}, {0, 0}};
@@ -159,14 +191,19 @@ struct pic_ctx {
     int ext_type = 0;
     double K = 0, lam_u = 0, ku = 0, B0 = 0, phase0 = 0, z_start = 0, ramp = -1;
     float *phase_tab = nullptr;
+    std::vector<double> B0_run;   // ensembles: B0 of each run (empty: B0 for every run)
+    float *amp_tab = nullptr;     // ensembles: device [nz] gamma_R B0 of the run owning row k
+    std::vector<double> dens_run; // ensembles: plasma density scale of each run
     // plasma
     int plasma = 0, sp_e = -1, sp_i = -1, ppc[3] = {1, 1, 1}, xr[4] = {0, 0, 0, 0};
     double *prof = nullptr;   // device [2][nprof]
+    double *dens_scale = nullptr;  // ensembles: device [runs] density scale of each run
     int nprof = 0;
     std::vector<double> prof_z, prof_n;
     // tiles
     int T[3] = {8, 8, 8};
     int sort_every = 8;
+    int64_t sort_base = 0;        // pic_step sorts when (step - sort_base) % sort_every == 0
     int M = 1;
     int nt[3] = {1, 1, 1};
     int ntiles = 1;
@@ -177,6 +214,7 @@ struct pic_ctx {
     int64_t step = 0, shifts = 0, m_last = -1;
     // bookkeeping
     int *err = nullptr;           // device error word
+    unsigned long long *nfall = nullptr;   // device counter of fallback deposits (tracing)
     int *work = nullptr;          // device work counters [2 * kMaxSpecies]
     double *red = nullptr;        // reduction partials
     double *red_out = nullptr;
@@ -204,6 +242,7 @@ PmlDev pml_dev(const pic_ctx *c);
 
 // k_push.cu
 cudaError_t launch_push(pic_ctx *c, int si, const ExtDev &ext);
+cudaError_t launch_dlim_from_momenta(pic_ctx *c, int si);
 cudaError_t launch_rho(pic_ctx *c, const Species &s, float *rho);
 // k_lattice.cu
 cudaError_t launch_lattice_profiles(pic_ctx *c, int si);
@@ -214,7 +253,7 @@ cudaError_t launch_lattice_records(pic_ctx *c, int si, Species &out);
 cudaError_t launch_fdtd_b(pic_ctx *c, float dtt);
 cudaError_t launch_fdtd_e(pic_ctx *c);
 cudaError_t launch_shift_fields(pic_ctx *c);
-cudaError_t launch_field_energy(pic_ctx *c, double *out_host);
+cudaError_t launch_field_energy(pic_ctx *c, double *out_host, int run);
 // k_sort.cu
 cudaError_t launch_sort(pic_ctx *c, int si);
 cudaError_t exclusive_scan(pic_ctx *c, int *data, int64_t n);
@@ -222,11 +261,12 @@ int64_t scan_scratch_size(int64_t n);
 // k_init.cu
 cudaError_t launch_load(pic_ctx *c, int si, int64_t n, const double *dx, const double *du,
                         const double *dw, int frame, const double origin[3], int match,
-                        int64_t id_base);
+                        int64_t id_base, int run, int64_t stride);
 cudaError_t launch_inject(pic_ctx *c, int64_t m0, int64_t m1);
 cudaError_t launch_shift_particles(pic_ctx *c, int si);
-cudaError_t launch_moments(pic_ctx *c, const Species &s, int frame, double k, double *out20);
+cudaError_t launch_moments(pic_ctx *c, const Species &s, int frame, double k, double *out20, int run);
 cudaError_t species_wmax(pic_ctx *c, int si, double *out);
 cudaError_t species_count_live(pic_ctx *c, const Species &s, int64_t *out);
+cudaError_t absmax_f64(pic_ctx *c, const double *a, int64_t n, double *out);
 
 }  // namespace gbpic

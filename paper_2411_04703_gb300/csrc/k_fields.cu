@@ -8,14 +8,15 @@
 namespace gbpic {
 namespace {
 
-__device__ __forceinline__ float ld(const float *F, const GridDev &g, int i, int j, int k)
+// Neighbour value; zb: first row of the run that owns the updated cell (0 for a single run).
+__device__ __forceinline__ float ld(const float *F, const GridDev &g, int i, int j, int k, int zb)
 {
     if (i >= g.n[0]) { if (!g.periodic[0]) return 0.f; i -= g.n[0]; }
     if (i < 0) { if (!g.periodic[0]) return 0.f; i += g.n[0]; }
     if (j >= g.n[1]) { if (!g.periodic[1]) return 0.f; j -= g.n[1]; }
     if (j < 0) { if (!g.periodic[1]) return 0.f; j += g.n[1]; }
-    if (k >= g.n[2]) { if (!g.periodic[2]) return 0.f; k -= g.n[2]; }
-    if (k < 0) { if (!g.periodic[2]) return 0.f; k += g.n[2]; }
+    if (k >= zb + g.nzr) { if (!g.periodic[2]) return 0.f; k -= g.nzr; }
+    if (k < zb) { if (!g.periodic[2]) return 0.f; k += g.nzr; }
     return __ldg(F + ((long long)k * g.n[1] + j) * g.n[0] + i);
 }
 
@@ -36,17 +37,18 @@ __global__ void k_fdtd_b(FieldsDev f, GridDev g, PmlDev pml, float dtt)
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k = blockIdx.z;
     if (i >= g.n[0] || j >= g.n[1]) return;
+    const int zb = zblock(k, g.nzr);
     const long long N = g.ncell;
     const long long ix = ((long long)k * g.n[1] + j) * g.n[0] + i;
     const float *Ex = f.E, *Ey = f.E + N, *Ez = f.E + 2 * N;
     const float ex = Ex[ix], ey = Ey[ix], ez = Ez[ix];
     const float idx = 1.f / g.d[0], idy = 1.f / g.d[1], idz = 1.f / g.d[2];
-    float dEz_dy = (ld(Ez, g, i, j + 1, k) - ez) * idy;
-    float dEy_dz = (ld(Ey, g, i, j, k + 1) - ey) * idz;
-    float dEx_dz = (ld(Ex, g, i, j, k + 1) - ex) * idz;
-    float dEz_dx = (ld(Ez, g, i + 1, j, k) - ez) * idx;
-    float dEy_dx = (ld(Ey, g, i + 1, j, k) - ey) * idx;
-    float dEx_dy = (ld(Ex, g, i, j + 1, k) - ex) * idy;
+    float dEz_dy = (ld(Ez, g, i, j + 1, k, zb) - ez) * idy;
+    float dEy_dz = (ld(Ey, g, i, j, k + 1, zb) - ey) * idz;
+    float dEx_dz = (ld(Ex, g, i, j, k + 1, zb) - ex) * idz;
+    float dEz_dx = (ld(Ez, g, i + 1, j, k, zb) - ez) * idx;
+    float dEy_dx = (ld(Ey, g, i + 1, j, k, zb) - ey) * idx;
+    float dEx_dy = (ld(Ex, g, i, j + 1, k, zb) - ex) * idy;
     if (pml.on) {
         const float bx = pml.bB[0][i], by = pml.bB[1][j], bz = pml.bB[2][k];
         dEz_dy = cpml(pml.psiB + 0 * N, ix, by, dEz_dy);
@@ -69,17 +71,18 @@ __global__ void k_fdtd_e(FieldsDev f, GridDev g, PmlDev pml)
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k = blockIdx.z;
     if (i >= g.n[0] || j >= g.n[1]) return;
+    const int zb = zblock(k, g.nzr);
     const long long N = g.ncell;
     const long long ix = ((long long)k * g.n[1] + j) * g.n[0] + i;
     const float *Bx = f.B, *By = f.B + N, *Bz = f.B + 2 * N;
     const float bxv = Bx[ix], byv = By[ix], bzv = Bz[ix];
     const float idx = 1.f / g.d[0], idy = 1.f / g.d[1], idz = 1.f / g.d[2];
-    float dBz_dy = (bzv - ld(Bz, g, i, j - 1, k)) * idy;
-    float dBy_dz = (byv - ld(By, g, i, j, k - 1)) * idz;
-    float dBx_dz = (bxv - ld(Bx, g, i, j, k - 1)) * idz;
-    float dBz_dx = (bzv - ld(Bz, g, i - 1, j, k)) * idx;
-    float dBy_dx = (byv - ld(By, g, i - 1, j, k)) * idx;
-    float dBx_dy = (bxv - ld(Bx, g, i, j - 1, k)) * idy;
+    float dBz_dy = (bzv - ld(Bz, g, i, j - 1, k, zb)) * idy;
+    float dBy_dz = (byv - ld(By, g, i, j, k - 1, zb)) * idz;
+    float dBx_dz = (bxv - ld(Bx, g, i, j, k - 1, zb)) * idz;
+    float dBz_dx = (bzv - ld(Bz, g, i - 1, j, k, zb)) * idx;
+    float dBy_dx = (byv - ld(By, g, i - 1, j, k, zb)) * idx;
+    float dBx_dy = (bxv - ld(Bx, g, i, j - 1, k, zb)) * idy;
     if (pml.on) {
         const float bx = pml.bE[0][i], by = pml.bE[1][j], bz = pml.bE[2][k];
         dBz_dy = cpml(pml.psiE + 0 * N, ix, by, dBz_dy);
@@ -153,14 +156,18 @@ cudaError_t launch_shift_fields(pic_ctx *c)
     return cudaGetLastError();
 }
 
-cudaError_t launch_field_energy(pic_ctx *c, double *out_host)
+// (1/2) sum (E^2 + B^2) dV over the grid, or over the rows of one run of an ensemble (run >= 0).
+cudaError_t launch_field_energy(pic_ctx *c, double *out_host, int run)
 {
     const int blocks = 1024;
     double acc = 0.0;
     std::vector<double> part(blocks);
-    for (int q = 0; q < 2; q++) {
-        const float *a = q == 0 ? c->E : c->B;
-        k_sumsq<<<blocks, 256, 0, c->stream>>>(a, 3 * c->ncell, c->red);
+    const long long plane = (long long)c->n[0] * c->n[1];
+    const long long off = run < 0 ? 0 : (long long)run * c->nzr * plane;
+    const long long len = run < 0 ? c->ncell : (long long)c->nzr * plane;
+    for (int q = 0; q < 6; q++) {
+        const float *a = (q < 3 ? c->E + q * c->ncell : c->B + (q - 3) * c->ncell) + off;
+        k_sumsq<<<blocks, 256, 0, c->stream>>>(a, len, c->red);
         c->kernels++;
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;

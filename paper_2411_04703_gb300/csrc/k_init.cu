@@ -15,19 +15,25 @@ struct PlaceP {
     int n[3];
     int periodic[3];
     int mlo, mhi;
+    int nzr;          // rows per run (ensembles)
+    CellCode cc;
 };
 
 // Grid coordinate X of dimension d -> (cell, float offset); false outside the active region.
-__device__ __forceinline__ bool place1(const PlaceP &g, int d, double X, float &o, int &c)
+// A periodic z wraps inside the run whose first row is zb.
+__device__ __forceinline__ bool place1(const PlaceP &g, int d, double X, float &o, int &c, int zb = 0)
 {
     double fl = floor(X);
     float of = (float)(X - fl);
     if (of >= 1.f) { of = 0.f; fl += 1.0; }
     long long ci = (long long)fl;
     bool ok = true;
+    const int per = d == 2 ? g.nzr : g.n[d];
+    const int base = d == 2 ? zb : 0;
     if (g.periodic[d]) {
-        ci %= g.n[d];
-        if (ci < 0) ci += g.n[d];
+        ci = (ci - base) % per;
+        if (ci < 0) ci += per;
+        ci += base;
     } else if (ci < g.mlo || ci > g.n[d] - 1 - g.mhi) {
         ok = false;
         ci = 0;
@@ -37,11 +43,11 @@ __device__ __forceinline__ bool place1(const PlaceP &g, int d, double X, float &
     return ok;
 }
 
-__device__ __forceinline__ bool place(const PlaceP &g, const double X[3], float o[3], int c[3])
+__device__ __forceinline__ bool place(const PlaceP &g, const double X[3], float o[3], int c[3], int zb = 0)
 {
     const bool a = place1(g, 0, X[0], o[0], c[0]);
     const bool b = place1(g, 1, X[1], o[1], c[1]);
-    const bool z = place1(g, 2, X[2], o[2], c[2]);
+    const bool z = place1(g, 2, X[2], o[2], c[2], zb);
     return a && b && z;
 }
 
@@ -51,8 +57,9 @@ struct LoadP {
     double gR, bR, igR2;
     int frame, match;
     double qm, Aamp, ku, phase0;   // undulator vector potential A_x = Aamp sin(k_u z + phase0)
-    long long n;
+    long long n, stride;           // particles of this launch; component stride of x and u
     int id_base;
+    int zb;                        // first row of the run the particles are loaded into
 };
 
 __global__ void k_load(SpeciesDev sp, LoadP p, const double *x, const double *u, const double *w, int *err)
@@ -60,8 +67,9 @@ __global__ void k_load(SpeciesDev sp, LoadP p, const double *x, const double *u,
     const long long n = p.n;
     const int base = sp.count[0];
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        double xi[3] = {x[i], x[n + i], x[2 * n + i]};
-        double ui[3] = {u[i], u[n + i], u[2 * n + i]};
+        const long long st = p.stride;
+        double xi[3] = {x[i], x[st + i], x[2 * st + i]};
+        double ui[3] = {u[i], u[st + i], u[2 * st + i]};
         const double wi = w ? w[i] : 1.0;
         if (p.frame == PIC_FRAME_LAB && p.match) {
             // matched entry: lab energy kept, transverse canonical momentum u_x + (q/m) A_x = 0
@@ -96,12 +104,13 @@ __global__ void k_load(SpeciesDev sp, LoadP p, const double *x, const double *u,
         }
         double X[3];
         for (int d = 0; d < 3; d++) X[d] = xp[d] / p.d[d] + p.origin[d];
+        X[2] += p.zb;
         float o[3];
         int c[3];
-        const bool ok = place(p.g, X, o, c);
+        const bool ok = place(p.g, X, o, c, p.zb);
         const long long slot = (long long)base + i;
         if (slot >= sp.cap) { atomicOr(err, ERR_CAPACITY); continue; }
-        sp.pos[slot] = make_float4(o[0], o[1], o[2], __int_as_float(ok ? pack_cell(c[0], c[1], c[2]) : -1));
+        sp.pos[slot] = make_float4(o[0], o[1], o[2], __int_as_float(ok ? p.g.cc.pack(c[0], c[1], c[2]) : -1));
         sp.mom[slot] = make_float4((float)up[0], (float)up[1], (float)up[2], (float)wi);
         sp.id[slot] = p.id_base + (int)i;
     }
@@ -126,6 +135,8 @@ struct InjP {
     int id_e, id_i;
     PlaneRec *planes;    // ions as a lattice species: plane m goes to slot m mod plane_cap
     long long plane_cap;
+    const double *run_scale;  // ensembles: density scale of each run (plane m belongs to the run
+                              // holding its unshifted row); NULL: one run
 };
 
 __device__ double profile(const double *prof, int np, double z)
@@ -166,12 +177,20 @@ __global__ void k_inject(SpeciesDev se, SpeciesDev si, InjP p, int *err)
         int r;
         double X[3];
         lattice_point(p, t, m, r, X);
-        const double zc = ((double)m + 0.5) / p.ppc[2];
-        const double dens = p.gR * profile(p.prof, p.nprof, p.gR * zc * p.dz);
+        double zc = ((double)m + 0.5) / p.ppc[2];
+        int zb = 0;
+        double scale = 1.0;
+        if (p.run_scale) {
+            const int run = (int)floor(zc / p.g.nzr);
+            zb = run * p.g.nzr;
+            zc -= zb;   // the profile is given in each run's own coordinates
+            scale = p.run_scale[run];
+        }
+        const double dens = p.gR * profile(p.prof, p.nprof, p.gR * zc * p.dz) * scale;
         float o[3];
         int c[3];
-        const bool ok = place(p.g, X, o, c) && dens > 0.0;
-        const float4 P = make_float4(o[0], o[1], o[2], __int_as_float(ok ? pack_cell(c[0], c[1], c[2]) : -1));
+        const bool ok = place(p.g, X, o, c, zb) && dens > 0.0;
+        const float4 P = make_float4(o[0], o[1], o[2], __int_as_float(ok ? p.g.cc.pack(c[0], c[1], c[2]) : -1));
         const float4 Mo = make_float4(0.f, 0.f, p.uz, (float)(dens * p.wfac));
         const long long se_slot = base_e + t;
         if (se_slot >= se.cap) { atomicOr(err, ERR_CAPACITY); continue; }
@@ -185,7 +204,7 @@ __global__ void k_inject(SpeciesDev se, SpeciesDev si, InjP p, int *err)
             if (slot.kz >= 0) { atomicOr(err, ERR_CAPACITY); continue; }
             float oz;
             int kz;
-            const bool okz = place1(p.g, 2, X[2], oz, kz) && dens > 0.0;
+            const bool okz = place1(p.g, 2, X[2], oz, kz, zb) && dens > 0.0;
             slot = PlaneRec{oz, okz ? kz : -1, Mo.w, p.id_i + (int)t};
             continue;
         }
@@ -237,20 +256,20 @@ __global__ void k_lattice_records(SpeciesDev out, const PlaneRec *planes, long l
         const bool okx = place1(p.g, 0, X[0], ox, cx);
         const bool oky = place1(p.g, 1, X[1], oy, cy);
         const bool ok = pl.kz >= 0 && okx && oky;
-        out.pos[t] = make_float4(ox, oy, pl.oz, __int_as_float(ok ? pack_cell(cx, cy, pl.kz) : -1));
+        out.pos[t] = make_float4(ox, oy, pl.oz, __int_as_float(ok ? p.g.cc.pack(cx, cy, pl.kz) : -1));
         out.mom[t] = make_float4(0.f, 0.f, p.uz, pl.w);
         out.id[t] = pl.id0 + r;
     }
 }
 
-__global__ void k_shift_particles(SpeciesDev sp, int mlo)
+__global__ void k_shift_particles(SpeciesDev sp, int mlo, CellCode cc)
 {
     const int n = sp.count[0];
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
         const int cell = __float_as_int(sp.pos[p].w);
         if (cell < 0) continue;
-        const int k = cell_k(cell) - 1;
-        sp.pos[p].w = __int_as_float(k < mlo ? -1 : pack_cell(cell_i(cell), cell_j(cell), k));
+        const int k = cc.k(cell) - 1;
+        sp.pos[p].w = __int_as_float(k < mlo ? -1 : cc.pack(cc.i(cell), cc.j(cell), k));
     }
 }
 
@@ -261,6 +280,8 @@ struct MomP {
     int frame, pass;
     double mean_t;
     double mean[7];   // x y z ux uy uz gamma
+    CellCode cc;
+    int k_lo, k_hi;   // rows of the run whose particles are summed (ensembles; whole grid otherwise)
 };
 
 constexpr int kMomK = 10;
@@ -269,9 +290,9 @@ __device__ __forceinline__ void particle_frame(const MomP &p, float4 P, float4 M
                                                double &g, double &t)
 {
     const int cell = __float_as_int(P.w);
-    x[0] = ((double)cell_i(cell) + (double)P.x) * p.d[0];
-    x[1] = ((double)cell_j(cell) + (double)P.y) * p.d[1];
-    x[2] = ((double)cell_k(cell) + (double)P.z + p.shifts) * p.d[2];
+    x[0] = ((double)p.cc.i(cell) + (double)P.x) * p.d[0];
+    x[1] = ((double)p.cc.j(cell) + (double)P.y) * p.d[1];
+    x[2] = ((double)(p.cc.k(cell) - p.k_lo) + (double)P.z + p.shifts) * p.d[2];
     u[0] = Mo.x; u[1] = Mo.y; u[2] = Mo.z;
     const double up2 = u[0] * u[0] + u[1] * u[1];
     const double gp = sqrt(1.0 + up2 + u[2] * u[2]);
@@ -303,6 +324,8 @@ __global__ void k_moments(SpeciesDev sp, MomP p, double *partial)
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
         const float4 P = sp.pos[q];
         if (__float_as_int(P.w) < 0) continue;
+        const int kc = p.cc.k(__float_as_int(P.w));
+        if (kc < p.k_lo || kc >= p.k_hi) continue;
         const float4 Mo = sp.mom[q];
         const double w = Mo.w;
         double x[3], u[3], g, t;
@@ -367,6 +390,21 @@ __global__ void k_wmax(SpeciesDev sp, double *partial)
     }
 }
 
+__global__ void k_absmax_f64(const double *a, long long n, double *partial)
+{
+    double m = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        m = fmax(m, fabs(a[i]));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+    __shared__ double ws[32];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < (int)(blockDim.x >> 5); k++) m = fmax(m, ws[k]);
+        partial[blockIdx.x] = m;
+    }
+}
+
 __global__ void k_count_live(SpeciesDev sp, unsigned long long *out)
 {
     unsigned long long cnt = 0;
@@ -386,13 +424,17 @@ PlaceP place_params(const pic_ctx *c)
     }
     g.mlo = c->order == 1 ? 1 : 2;
     g.mhi = c->order == 1 ? 2 : 3;
+    g.nzr = c->nzr;
+    g.cc = c->cc;
     return g;
 }
 
 }  // namespace
 
+// Loads n particles into run `run` (0 for a single run); dx, du: device [3][stride] arrays
+// (component stride `stride`), dw: device [n] or NULL.
 cudaError_t launch_load(pic_ctx *c, int si, int64_t n, const double *dx, const double *du, const double *dw,
-                        int frame, const double origin[3], int match, int64_t id_base)
+                        int frame, const double origin[3], int match, int64_t id_base, int run, int64_t stride)
 {
     Species &s = c->sp[si];
     LoadP p;
@@ -404,11 +446,14 @@ cudaError_t launch_load(pic_ctx *c, int si, int64_t n, const double *dx, const d
     p.frame = frame;
     p.match = match && c->ext_type == PIC_EXT_PLANAR_UNDULATOR;
     p.qm = s.q / s.m;
-    p.Aamp = c->ku > 0 ? c->B0 / c->ku : 0.0;
+    const double B0 = c->B0_run.empty() ? c->B0 : c->B0_run[run];
+    p.Aamp = c->ku > 0 ? B0 / c->ku : 0.0;
     p.ku = c->ku;
     p.phase0 = c->phase0;
     p.n = n;
+    p.stride = stride;
     p.id_base = (int)id_base;
+    p.zb = run * c->nzr;
     if (n > 0) {
         k_load<<<c->num_sms * 4, 256, 0, c->stream>>>(species_dev(c, s), p, dx, du, dw, c->err);
         c->kernels++;
@@ -445,6 +490,7 @@ cudaError_t launch_inject(pic_ctx *c, int64_t m0, int64_t m1)
     p.id_i = (int)si.next_id;
     p.planes = si.lattice ? si.planes : nullptr;
     p.plane_cap = si.plane_cap;
+    p.run_scale = c->runs > 1 ? c->dens_scale : nullptr;
     if (p.count <= 0) return cudaSuccess;
     const long long blocks = std::min<long long>((p.count + 255) / 256, (long long)c->num_sms * 16);
     k_inject<<<(unsigned)blocks, 256, 0, c->stream>>>(species_dev(c, se), species_dev(c, si), p, c->err);
@@ -517,6 +563,25 @@ cudaError_t species_wmax(pic_ctx *c, int si, double *out)
     return cudaSuccess;
 }
 
+// Largest |a[i]| of a device FP64 array (synchronous).
+cudaError_t absmax_f64(pic_ctx *c, const double *a, int64_t n, double *out)
+{
+    const int blocks = 256;
+    k_absmax_f64<<<blocks, 256, 0, c->stream>>>(a, n, c->red);
+    c->kernels++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    std::vector<double> part(blocks);
+    e = cudaMemcpyAsync(part.data(), c->red, sizeof(double) * blocks, cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return e;
+    double m = 0.0;
+    for (double v : part) m = std::max(m, v);
+    *out = m;
+    return cudaSuccess;
+}
+
 cudaError_t species_count_live(pic_ctx *c, const Species &s, int64_t *out)
 {
     unsigned long long *d = reinterpret_cast<unsigned long long *>(c->red);
@@ -534,14 +599,19 @@ cudaError_t species_count_live(pic_ctx *c, const Species &s, int64_t *out)
 
 cudaError_t launch_shift_particles(pic_ctx *c, int si)
 {
-    k_shift_particles<<<c->num_sms * 8, 256, 0, c->stream>>>(species_dev(c, c->sp[si]), c->order == 1 ? 1 : 2);
+    k_shift_particles<<<c->num_sms * 8, 256, 0, c->stream>>>(species_dev(c, c->sp[si]), c->order == 1 ? 1 : 2, c->cc);
     c->kernels++;
     return cudaGetLastError();
 }
 
-cudaError_t launch_moments(pic_ctx *c, const Species &s, int frame, double k, double *out)
+// FP64 moments of species s, over the whole grid (run < 0) or over one run of an ensemble (its
+// positions then in the run's own coordinates).
+cudaError_t launch_moments(pic_ctx *c, const Species &s, int frame, double k, double *out, int run)
 {
     MomP p{};
+    p.cc = c->cc;
+    p.k_lo = run < 0 ? 0 : run * c->nzr;
+    p.k_hi = run < 0 ? c->n[2] : (run + 1) * c->nzr;
     for (int d = 0; d < 3; d++) p.d[d] = c->d[d];
     p.shifts = (double)c->shifts;
     p.tp = (double)c->step * c->dt;

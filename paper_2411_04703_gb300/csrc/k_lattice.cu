@@ -26,7 +26,7 @@ struct LatStepP {
     PlaneRec *planes;
     long long cap;
     double *zacc;
-    int nz, mlo, mhi, periodic, order;
+    int nz, nzr, mlo, mhi, periodic, order;
     float uz, dtdz;
     double cf;
 };
@@ -51,7 +51,8 @@ __global__ void k_lattice_step(LatStepP p, int *err)
         }
         int kn = r.kz + sh;
         bool alive = true;
-        if (p.periodic) kn = kn < 0 ? kn + p.nz : (kn >= p.nz ? kn - p.nz : kn);
+        const int zb = zblock(r.kz, p.nzr);   // the plane's run (ensembles: z wraps inside it)
+        if (p.periodic) kn = zwrap(kn, zb, p.nzr);
         else if (kn < p.mlo || kn > p.nz - 1 - p.mhi) alive = false;
         if (alive) {
             // prefix sum of the shape change over the window; positions relative to the old row
@@ -62,7 +63,7 @@ __global__ void k_lattice_step(LatStepP p, int *err)
                 run += shape_weight(p.order, (double)nr - z1) - shape_weight(p.order, (double)nr - z0);
                 if (run == 0.0) continue;
                 int kk = r.kz + nr;
-                if (p.periodic) kk = kk < 0 ? kk + p.nz : (kk >= p.nz ? kk - p.nz : kk);
+                if (p.periodic) kk = zwrap(kk, zb, p.nzr);
                 if (kk < 0 || kk >= p.nz) { atomicOr(err, ERR_INDEX); continue; }
                 atomicAdd(&p.zacc[kk], fw * run);
             }
@@ -104,6 +105,7 @@ cudaError_t launch_lattice_step(pic_ctx *c, int si)
     p.cap = s.plane_cap;
     p.zacc = s.zacc;
     p.nz = c->n[2];
+    p.nzr = c->nzr;
     p.mlo = c->order == 1 ? 1 : 2;
     p.mhi = c->order == 1 ? 2 : 3;
     p.periodic = c->bc[2][0] == PIC_BC_PERIODIC;

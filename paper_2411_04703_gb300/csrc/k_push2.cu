@@ -19,7 +19,8 @@ __global__ void k_rho(SpeciesDev sp, GridDev g, float qv, float *rho)
         const int cell = __float_as_int(P.w);
         if (cell < 0) continue;
         const float w = sp.mom[p].w * qv;
-        int c[3] = {cell_i(cell), cell_j(cell), cell_k(cell)};
+        int c[3] = {g.cc.i(cell), g.cc.j(cell), g.cc.k(cell)};
+        const int zb = zblock(c[2], g.nzr);
         float o[3] = {P.x, P.y, P.z};
         int su[3];
         float wu[3][S::N];
@@ -30,11 +31,15 @@ __global__ void k_rho(SpeciesDev sp, GridDev g, float qv, float *rho)
                 for (int i = 0; i < S::N; i++) {
                     int q[3] = {c[0] + su[0] + i, c[1] + su[1] + j, c[2] + su[2] + k};
                     bool ok = true;
-                    for (int d = 0; d < 3; d++) {
+                    for (int d = 0; d < 2; d++) {
                         if (q[d] < 0 || q[d] >= g.n[d]) {
                             if (g.periodic[d]) q[d] = q[d] < 0 ? q[d] + g.n[d] : q[d] - g.n[d];
                             else ok = false;
                         }
+                    }
+                    if (q[2] < zb || q[2] >= zb + g.nzr) {
+                        if (g.periodic[2]) q[2] = zwrap(q[2], zb, g.nzr);
+                        else ok = false;
                     }
                     if (ok)
                         atomicAdd(rho + ((long long)q[2] * g.n[1] + q[1]) * g.n[0] + q[0],
@@ -43,7 +48,44 @@ __global__ void k_rho(SpeciesDev sp, GridDev g, float qv, float *rho)
     }
 }
 
+// Largest displacement per component the stored momenta give in one step, |u_c| dt / (gamma d_c).
+__global__ void k_dmax_measure(SpeciesDev sp, float tx, float ty, float tz)
+{
+    unsigned m[3] = {0u, 0u, 0u};
+    const int n = sp.count[0];
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        if (__float_as_int(sp.pos[p].w) < 0) continue;
+        const float4 u = sp.mom[p];
+        const float ig = rsqrtf(1.f + u.x * u.x + u.y * u.y + u.z * u.z);
+        m[0] = max(m[0], __float_as_uint(fabsf(u.x) * ig * tx));
+        m[1] = max(m[1], __float_as_uint(fabsf(u.y) * ig * ty));
+        m[2] = max(m[2], __float_as_uint(fabsf(u.z) * ig * tz));
+    }
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        const unsigned r = __reduce_max_sync(0xffffffffu, m[k]);
+        if ((threadIdx.x & 31) == 0 && r) atomicMax(sp.dmax + k, r);
+    }
+}
+
 }  // namespace
+
+// Sets the displacement bound of species si from its current momenta (after a load or an
+// injection): four times the largest displacement they give, as after a step.
+cudaError_t launch_dlim_from_momenta(pic_ctx *c, int si)
+{
+    const Species &s = c->sp[si];
+    if (s.lattice || !s.dlim) return cudaSuccess;
+    float light[3];
+    for (int d = 0; d < 3; d++) light[d] = (float)std::min(1.0, c->dt / c->d[d]);
+    k_dmax_measure<<<c->num_sms * 4, 256, 0, c->stream>>>(species_dev(c, s), (float)(c->dt / c->d[0]),
+                                                          (float)(c->dt / c->d[1]), (float)(c->dt / c->d[2]));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    push::k_dlim_update<<<1, 32, 0, c->stream>>>(s.dlim, s.dmax, light[0], light[1], light[2]);
+    c->kernels += 2;
+    return cudaGetLastError();
+}
 
 cudaError_t launch_push(pic_ctx *c, int si, const ExtDev &ext)
 {

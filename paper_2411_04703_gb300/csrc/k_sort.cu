@@ -17,7 +17,7 @@ constexpr int kScanSeg = 2 * kScanThreads;
 __device__ __forceinline__ int tile_key(const float4 &P, const TileDev &t)
 {
     const int cell = __float_as_int(P.w);
-    const int i = cell_i(cell), j = cell_j(cell), k = cell_k(cell);
+    const int i = t.cc.i(cell), j = t.cc.j(cell), k = t.cc.k(cell);
     const int tile = ((k / t.T[2]) * t.nt[1] + j / t.T[1]) * t.nt[0] + i / t.T[0];
     const int local = ((j % t.T[1]) * t.T[2] + k % t.T[2]) * t.T[0] + i % t.T[0];
     const int oct = (P.x >= 0.5f) | ((P.y >= 0.5f) << 1) | ((P.z >= 0.5f) << 2);
@@ -49,27 +49,37 @@ __global__ void k_sort_scatter(SpeciesDev sp, TileDev t, int n_keys, const int *
     }
 }
 
-__global__ void k_tile_chunks(const int *start, int keys_per_tile, int ntiles, int *chunk_count)
+// Work of a tile: chunks of kChunk particles for the shared-memory path, or, for a tile with
+// fewer than kSparse particles, one entry in the sparse list (global-memory path, a warp each).
+__global__ void k_tile_chunks(const int *start, int keys_per_tile, int ntiles, int *chunk_count, int *sparse_flag)
 {
     const int tl = blockIdx.x * blockDim.x + threadIdx.x;
     if (tl > ntiles) return;
-    if (tl == ntiles) { chunk_count[tl] = 0; return; }
+    if (tl == ntiles) {
+        chunk_count[tl] = 0;
+        sparse_flag[tl] = 0;
+        return;
+    }
     const int cnt = start[(tl + 1) * keys_per_tile] - start[tl * keys_per_tile];
-    chunk_count[tl] = (cnt + kChunk - 1) / kChunk;
+    const bool sparse = cnt > 0 && cnt < kSparse;
+    chunk_count[tl] = sparse ? 0 : (cnt + kChunk - 1) / kChunk;
+    sparse_flag[tl] = sparse ? 1 : 0;
 }
 
-__global__ void k_fill_items(const int *chunk_start, int ntiles, int2 *items, int *count, const int *start,
-                             int n_keys)
+__global__ void k_fill_items(const int *chunk_start, const int *sparse_start, int ntiles, int2 *items,
+                             int *sparse_tiles, int *count, const int *start, int n_keys)
 {
     const int tl = blockIdx.x * blockDim.x + threadIdx.x;
     if (tl < ntiles) {
         const int b = chunk_start[tl], e = chunk_start[tl + 1];
         for (int c = b; c < e; c++) items[c] = make_int2(tl, c - b);
+        if (sparse_start[tl + 1] > sparse_start[tl]) sparse_tiles[sparse_start[tl]] = tl;
     }
     if (tl == 0) {
         count[0] = start[n_keys];
         count[1] = start[n_keys];
         count[2] = chunk_start[ntiles];
+        count[3] = sparse_start[ntiles];
     }
 }
 
@@ -167,11 +177,12 @@ cudaError_t launch_sort(pic_ctx *c, int si)
     k_sort_scatter<<<grid, 256, 0, c->stream>>>(sd, t, n_keys, s.cell_start, s.rank, s.pos2, s.mom2, s.id2);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_tile_chunks<<<(c->ntiles + 1 + 255) / 256, 256, 0, c->stream>>>(s.cell_start, t.tile_cells * 8, c->ntiles,
-                                                                       s.chunk_start);
+                                                                       s.chunk_start, s.sparse_start);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = exclusive_scan(c, s.chunk_start, c->ntiles + 1)) != cudaSuccess) return e;
-    k_fill_items<<<(c->ntiles + 255) / 256, 256, 0, c->stream>>>(s.chunk_start, c->ntiles, s.items, s.count,
-                                                                  s.cell_start, n_keys);
+    if ((e = exclusive_scan(c, s.sparse_start, c->ntiles + 1)) != cudaSuccess) return e;
+    k_fill_items<<<(c->ntiles + 255) / 256, 256, 0, c->stream>>>(s.chunk_start, s.sparse_start, c->ntiles, s.items,
+                                                                  s.sparse_tiles, s.count, s.cell_start, n_keys);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     c->kernels += 4;   // count, scatter, tile_chunks, fill_items
     std::swap(s.pos, s.pos2);

@@ -23,10 +23,12 @@
 
 #include "gbpic_internal.cuh"
 
+#include <algorithm>
+
 namespace gbpic {
 namespace push {
 
-constexpr int kQueue = 384;   // queued crossing particles per work item (overflow: inline)
+constexpr int kQueue = 1024;  // queued crossing particles per work item (overflow: inline)
 
 // ------------------------------------------------------------------ region geometry
 // The z-plane pitch is padded to 4 (mod 16) words.  The 32 lanes of a warp work on cells 16
@@ -165,11 +167,14 @@ template <> struct Shape<2> {
 //
 // The region's current is accumulated as exact fixed point with native 32-bit integer shared
 // atomics (a float add on shared memory is not a native atomic): a contribution v becomes
-// V = round(v * jscale), an int32 with |V| <= 2^30 for the largest possible contribution of the
-// species (weight, charge and the speed-of-light bound of the displacement per step), split into
-// its 19 low bits (unsigned word) and the rest (signed word).  A work item holds at most
-// kChunk = 4096 particles, each adding at most once per node and component, so neither word
-// overflows; the flush recombines hi * 2^19 + lo.
+// V = round(v * js), an int32 with |V| <= 2^30 for the largest contribution the work item can
+// receive (largest weight of the run, charge, and the step's displacement bound dlim), split into
+// its 19 low bits (unsigned word) and the rest (signed word).  js is a power of two, so the flush
+// (hi * 2^19 + lo) / js is exact.  A work item holds at most kChunk = 4096 particles, each adding
+// at most once per node and component, so neither word overflows.  dlim adapts each step to
+// four times the largest displacement of the previous one, so a slow current component (a plasma's
+// transverse motion) keeps its precision; a particle moving further than dlim deposits with
+// float atomics instead.
 constexpr int kLoBits = 19;
 constexpr unsigned kLoMask = (1u << kLoBits) - 1u;
 static_assert(kChunk <= 4096, "fixed-point current words sized for 4096 contributions per node");
@@ -179,7 +184,7 @@ template <class Reg> struct SmemAcc {
     const float *sF;
     unsigned *sJlo;
     int *sJhi;
-    float js[3];
+    const float *js;      // shared [3]: fixed-point scale of the work item
     int base;
     __device__ __forceinline__ float scale(int comp) const { return js[comp]; }
     __device__ __forceinline__ float f(int comp, int x, int y, int z) const {
@@ -202,14 +207,19 @@ struct GlobAcc {
     GridDev g;
     int c[3];
     int *err;
+    int zb;               // first row of the particle's run
     __device__ __forceinline__ long long node(int x, int y, int z) const {
         int p[3] = {c[0] + x, c[1] + y, c[2] + z};
 #pragma unroll
-        for (int d = 0; d < 3; d++) {
+        for (int d = 0; d < 2; d++) {
             if (p[d] < 0 || p[d] >= g.n[d]) {
                 if (!g.periodic[d]) return -1;
                 p[d] = p[d] < 0 ? p[d] + g.n[d] : p[d] - g.n[d];
             }
+        }
+        if (p[2] < zb || p[2] >= zb + g.nzr) {
+            if (!g.periodic[2]) return -1;
+            p[2] = zwrap(p[2], zb, g.nzr);
         }
         return ((long long)p[2] * g.n[1] + p[1]) * g.n[0] + p[0];
     }
@@ -364,7 +374,8 @@ __device__ __forceinline__ void push_u(const Acc &acc, const float o[3], const i
             f = ext.ramp_mode == 1 ? fminf(fmaxf(r, 0.f), 1.f) : (r >= 0.f ? 1.f : 0.f);
         }
         const float ph = ext.phase_tab[c[2]] + fmaf(ext.kdz, o[2], ext.theta);
-        const float By = ext.B0g * f * cosf(ph);
+        const float amp = ext.amp_tab ? __ldg(ext.amp_tab + c[2]) : ext.B0g;
+        const float By = amp * f * cosf(ph);
         B[1] += By;
         E[0] -= ext.beta_R * By;
     }
@@ -391,7 +402,7 @@ __device__ __forceinline__ void push_u(const Acc &acc, const float o[3], const i
 template <int ORDER, bool FROZEN, class Acc>
 __device__ __forceinline__ bool push_move(const Acc &acc, const float o[3], int c[3], float4 &mo,
                                           const SpeciesDev &sp, const GridDev &g, const ExtDev &ext,
-                                          int *err, float d[3], int s[3], float o1[3])
+                                          int *err, float d[3], int s[3], float o1[3], int zb)
 {
     if (!FROZEN) push_u<ORDER>(acc, o, c, mo, sp, ext);
     const float u[3] = {mo.x, mo.y, mo.z};
@@ -408,7 +419,7 @@ __device__ __forceinline__ bool push_move(const Acc &acc, const float o[3], int 
         if (s[dd] < -1 || s[dd] > 1) { atomicOr(err, ERR_MOVE); return false; }
         int cn = c[dd] + s[dd];
         if (g.periodic[dd]) {
-            cn = cn < 0 ? cn + g.n[dd] : (cn >= g.n[dd] ? cn - g.n[dd] : cn);
+            cn = dd == 2 ? zwrap(cn, zb, g.nzr) : (cn < 0 ? cn + g.n[dd] : (cn >= g.n[dd] ? cn - g.n[dd] : cn));
         } else if (cn < g.mlo || cn > g.n[dd] - 1 - g.mhi) {
             alive = false;
         }
@@ -433,15 +444,16 @@ __device__ __forceinline__ void step_global(const SpeciesDev &sp, const GridDev 
     const int cell = __float_as_int(P.w);
     if (cell < 0) return;
     float4 mo = sp.mom[p];
-    int c[3] = {cell_i(cell), cell_j(cell), cell_k(cell)};
+    int c[3] = {g.cc.i(cell), g.cc.j(cell), g.cc.k(cell)};
     const float o[3] = {P.x, P.y, P.z};
-    GlobAcc acc{f.E, f.B, f.J, g, {c[0], c[1], c[2]}, err};
+    const int zb = g.nzr == g.n[2] ? 0 : zblock(c[2], g.nzr);
+    GlobAcc acc{f.E, f.B, f.J, g, {c[0], c[1], c[2]}, err, zb};
     float d[3], o1[3];
     int s[3];
-    if (push_move<ORDER, FROZEN>(acc, o, c, mo, sp, g, ext, err, d, s, o1)) {
+    if (push_move<ORDER, FROZEN>(acc, o, c, mo, sp, g, ext, err, d, s, o1, zb)) {
         const float fac[3] = {sp.cf[0] * mo.w, sp.cf[1] * mo.w, sp.cf[2] * mo.w};
         deposit_general<ORDER>(acc, o, d, s, fac);
-        P = make_float4(o1[0], o1[1], o1[2], __int_as_float(pack_cell(c[0], c[1], c[2])));
+        P = make_float4(o1[0], o1[1], o1[2], __int_as_float(g.cc.pack(c[0], c[1], c[2])));
         if (!FROZEN) sp.mom[p] = mo;
     } else {
         P.w = __int_as_float(-1);
@@ -449,15 +461,16 @@ __device__ __forceinline__ void step_global(const SpeciesDev &sp, const GridDev 
     sp.pos[p] = P;
 }
 
-// Linear index of grid node (x, y, z) with periodic wrap, or -1 outside a non-periodic face.
-__device__ __forceinline__ long long wrap_node(const GridDev &g, int x, int y, int z);
+// Linear index of grid node (x, y, z) with periodic wrap (z inside the run starting at row zb),
+// or -1 outside a non-periodic face.
+__device__ __forceinline__ long long wrap_node(const GridDev &g, int x, int y, int z, int zb);
 
 // Stage the six field components of a tile's region in shared memory.  A tile away from every
 // face needs no wrap or bounds test; the loop runs over the region's nodes with compile-time
 // divisions (fixed region) and each thread moves all components of its node.
 template <class Reg>
 __device__ __forceinline__ void stage_fields(const Reg &reg, const GridDev &g, const FieldsDev &f, float *sF,
-                                             const int reg0[3], bool interior, long long gbase)
+                                             const int reg0[3], bool interior, long long gbase, int zb)
 {
     const int Rx = reg.rx(), Ry = reg.ry(), R2 = reg.r2(), R3 = reg.r3();
     const long long gnx = g.n[0], gnxy = (long long)g.n[0] * g.n[1];
@@ -465,7 +478,7 @@ __device__ __forceinline__ void stage_fields(const Reg &reg, const GridDev &g, c
         const int lz = l / R2, rem = l - lz * R2, ly = rem / Rx, lx = rem - ly * Rx;
         if (ly >= Ry) continue;   // plane padding
         const long long gi = interior ? gbase + lz * gnxy + ly * gnx + lx
-                                      : wrap_node(g, reg0[0] + lx, reg0[1] + ly, reg0[2] + lz);
+                                      : wrap_node(g, reg0[0] + lx, reg0[1] + ly, reg0[2] + lz, zb);
 #pragma unroll
         for (int comp = 0; comp < 3; comp++) {
             sF[comp * R3 + l] = gi >= 0 ? __ldg(f.E + comp * g.ncell + gi) : 0.f;
@@ -475,15 +488,19 @@ __device__ __forceinline__ void stage_fields(const Reg &reg, const GridDev &g, c
 }
 
 
-__device__ __forceinline__ long long wrap_node(const GridDev &g, int x, int y, int z)
+__device__ __forceinline__ long long wrap_node(const GridDev &g, int x, int y, int z, int zb)
 {
     int p[3] = {x, y, z};
 #pragma unroll
-    for (int d = 0; d < 3; d++) {
+    for (int d = 0; d < 2; d++) {
         if (p[d] < 0 || p[d] >= g.n[d]) {
             if (!g.periodic[d]) return -1;
             p[d] = p[d] < 0 ? p[d] + g.n[d] : p[d] - g.n[d];
         }
+    }
+    if (p[2] < zb || p[2] >= zb + g.nzr) {
+        if (!g.periodic[2]) return -1;
+        p[2] = zwrap(p[2], zb, g.nzr);
     }
     return ((long long)p[2] * g.n[1] + p[1]) * g.n[0] + p[0];
 }
@@ -492,20 +509,21 @@ __device__ __forceinline__ long long wrap_node(const GridDev &g, int x, int y, i
 // shared region allows it; measured faster for the drifting ions despite a few spills).
 template <int ORDER, bool FROZEN, class Reg>
 __global__ void __launch_bounds__(kPushThreads, FROZEN ? 2 : 1)
-k_push(SpeciesDev sp, GridDev g, TileDev t, FieldsDev f, ExtDev ext, int *work, int *err, Reg reg)
+k_push(SpeciesDev sp, GridDev g, TileDev t, FieldsDev f, ExtDev ext, int *work, int *work_sparse, int *err, Reg reg)
 {
     extern __shared__ float smem[];
     __shared__ int s_item, s_qn;
+    __shared__ float s_js[3], s_jinv[3], s_dl[3];
+    __shared__ unsigned s_dm[3];
     const int Rx = reg.rx(), R3 = reg.r3();
     float *sF = smem;
     unsigned *sJlo = reinterpret_cast<unsigned *>(FROZEN ? smem : smem + 6 * R3);
     int *sJhi = reinterpret_cast<int *>(sJlo + 3 * R3);
     int *qb = sJhi + 3 * R3;                              // queue: local base index
     float *qd = reinterpret_cast<float *>(qb + kQueue);  // queue: o[3], d[3], w (SoA)
-    const float js[3] = {sp.jscale[0], sp.jscale[1], sp.jscale[2]};
     const int n_total = sp.count[0], n_sorted = sp.count[1], n_tile_items = sp.count[2];
     const int n_items = n_tile_items + (n_total - n_sorted + kChunk - 1) / kChunk;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(work, 1);
@@ -532,60 +550,90 @@ k_push(SpeciesDev sp, GridDev g, TileDev t, FieldsDev f, ExtDev ext, int *work, 
         const int p_end = min(p_begin + kChunk, t.cell_start[key0 + t.tile_cells * 8]);
         // Region of the tile: nodes reg0 + (0..R-1) per dim (plane pitch padded).
         const int R2 = reg.r2(), Ry = reg.ry(), Rz = R3 / R2;
+        const int zb = g.nzr == g.n[2] ? 0 : zblock(t0[2], g.nzr);   // the tile's run (tiles never straddle runs)
         const bool interior = reg0[0] >= 0 && reg0[0] + Rx <= g.n[0] && reg0[1] >= 0 && reg0[1] + Ry <= g.n[1] &&
-                              reg0[2] >= 0 && reg0[2] + Rz <= g.n[2];
+                              reg0[2] >= zb && reg0[2] + Rz <= zb + g.nzr;
         const long long gnx = g.n[0], gnxy = (long long)g.n[0] * g.n[1];
         const long long gbase = reg0[2] * gnxy + reg0[1] * gnx + reg0[0];
-        if (!FROZEN) stage_fields(reg, g, f, sF, reg0, interior, gbase);
+        if (!FROZEN) stage_fields(reg, g, f, sF, reg0, interior, gbase, zb);
         for (int l = threadIdx.x; l < 3 * R3; l += blockDim.x) {
             sJlo[l] = 0u;
             sJhi[l] = 0;
         }
-        if (threadIdx.x == 0) s_qn = 0;
+        if (threadIdx.x == 0) {
+            s_qn = 0;
+            // fixed-point scale of this item: the largest contribution jb w dlim maps to <= 2^30
+            const float w = sp.wrun ? sp.wrun[t0[2] / g.nzr] : sp.wmax;
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                const float dl = sp.dlim[k];
+                const float b = sp.jb[k] * w * dl;
+                int e = 0;
+                frexpf(b, &e);                       // b < 2^e
+                const int ex = b > 0.f ? min(max(30 - e, -100), 100) : 0;
+                s_js[k] = ldexpf(1.f, ex);
+                s_jinv[k] = ldexpf(1.f, -ex);
+                s_dl[k] = dl;
+                s_dm[k] = 0u;
+            }
+        }
         __syncthreads();
         // each lane takes kGroup = 8 consecutive particles: one cell of an 8-per-cell lattice,
         // visited in octant order, so at every iteration the warp's 32 lanes sit on 32
         // different cells with the same stencil shift (bank-conflict-free shared accesses, see
         // plane_pitch)
         const int len = p_end - p_begin;
-        constexpr int G = kGroup;
-        for (int k_it = 0; k_it < G; k_it++) {
+        // gq consecutive particles per lane (kGroup for a full item; 4 for a tile of a 4-per-cell
+        // lattice), so that every lane of every warp has work
+        const int gq = (len + kPushThreads - 1) / kPushThreads;
+        constexpr int NW = kPushThreads / 32;
+        for (int k_it = 0; k_it < gq; k_it++) {
             // lane-major: a warp's lanes sit kChunk/32 particles apart in the cell-sorted item, so
             // in a dense bunch (hundreds of particles per cell and octant) they still deposit into
             // different windows instead of queueing on the same shared-memory words; each lane's
             // G consecutive particles share cache lines across the warps
-            const int q = lane * (kChunk / 32) + warp * G + k_it;
-            if (q >= len) continue;
+            const int q = gq == 1 ? (int)threadIdx.x : lane * (NW * gq) + warp * gq + k_it;
+            unsigned dm[3] = {0u, 0u, 0u};   // |displacement| of this lane's particle (float bits)
+            do {
+            if (q >= len) break;
             const int p = p_begin + q;
             float4 P = sp.pos[p];
             const int cell = __float_as_int(P.w);
-            if (cell < 0) continue;
-            int c[3] = {cell_i(cell), cell_j(cell), cell_k(cell)};
+            if (cell < 0) break;
+            int c[3] = {g.cc.i(cell), g.cc.j(cell), g.cc.k(cell)};
             int rel[3];
             bool fast = true;
 #pragma unroll
             for (int dd = 0; dd < 3; dd++) {
                 int r = c[dd] - t0[dd];
                 if (g.periodic[dd]) {
-                    if (r > g.n[dd] / 2) r -= g.n[dd];
-                    else if (r < -g.n[dd] / 2) r += g.n[dd];
+                    const int per = dd == 2 ? g.nzr : g.n[dd];
+                    if (r > per / 2) r -= per;
+                    else if (r < -per / 2) r += per;
                 }
                 rel[dd] = r;
                 fast = fast && r >= -t.M && r < t.T[dd] + t.M;
             }
             if (!fast) {
                 step_global<ORDER, FROZEN>(sp, g, f, ext, err, p);
-                continue;
+                break;
             }
             float4 mo = sp.mom[p];
             const float o[3] = {P.x, P.y, P.z};
             const int base = (rel[2] + t.M + t.hl) * reg.r2() + (rel[1] + t.M + t.hl) * Rx + rel[0] + t.M + t.hl;
-            SmemAcc<Reg> acc{reg, sF, sJlo, sJhi, {js[0], js[1], js[2]}, base};
+            SmemAcc<Reg> acc{reg, sF, sJlo, sJhi, s_js, base};
             float d[3], o1[3];
             int s[3];
-            if (push_move<ORDER, FROZEN>(acc, o, c, mo, sp, g, ext, err, d, s, o1)) {
+            if (push_move<ORDER, FROZEN>(acc, o, c, mo, sp, g, ext, err, d, s, o1, zb)) {
                 const float fac[3] = {sp.cf[0] * mo.w, sp.cf[1] * mo.w, sp.cf[2] * mo.w};
-                if (stays_all<ORDER>(o, d, s)) {
+#pragma unroll
+                for (int k = 0; k < 3; k++) dm[k] = __float_as_uint(fabsf(d[k]));
+                if (!(fabsf(d[0]) <= s_dl[0] && fabsf(d[1]) <= s_dl[1] && fabsf(d[2]) <= s_dl[2])) {
+                    // beyond the item's fixed-point range: float atomics on the global current
+                    GlobAcc gacc{f.E, f.B, f.J, g, {g.cc.i(cell), g.cc.j(cell), g.cc.k(cell)}, err, zb};
+                    deposit_general<ORDER>(gacc, o, d, s, fac);
+                    atomicAdd(sp.nfall, 1ull);
+                } else if (stays_all<ORDER>(o, d, s)) {
                     deposit_simple<ORDER>(acc, o, d, fac);
                 } else {
                     const int slot = atomicAdd(&s_qn, 1);
@@ -602,14 +650,24 @@ k_push(SpeciesDev sp, GridDev g, TileDev t, FieldsDev f, ExtDev ext, int *work, 
                         deposit_general<ORDER>(acc, o, d, s, fac);
                     }
                 }
-                P = make_float4(o1[0], o1[1], o1[2], __int_as_float(pack_cell(c[0], c[1], c[2])));
+                P = make_float4(o1[0], o1[1], o1[2], __int_as_float(g.cc.pack(c[0], c[1], c[2])));
                 if (!FROZEN) sp.mom[p] = mo;
             } else {
                 P.w = __int_as_float(-1);
             }
             sp.pos[p] = P;
+            } while (false);
+            // the step's largest displacement per component (sets the next step's bound)
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                const unsigned m = __reduce_max_sync(0xffffffffu, dm[k]);
+                if (lane == 0 && m) atomicMax(&s_dm[k], m);
+            }
         }
         __syncthreads();
+        if (threadIdx.x == 0)
+            for (int k = 0; k < 3; k++)
+                if (s_dm[k]) atomicMax(sp.dmax + k, s_dm[k]);
         // queued particles that crossed a node: general window
         const int qn = min(s_qn, kQueue);
         for (int q = threadIdx.x; q < qn; q += blockDim.x) {
@@ -624,12 +682,12 @@ k_push(SpeciesDev sp, GridDev g, TileDev t, FieldsDev f, ExtDev ext, int *work, 
                 if (x1 - (float)s[dd] >= 1.f) s[dd] += 1;
             }
             const float fac[3] = {sp.cf[0] * w, sp.cf[1] * w, sp.cf[2] * w};
-            SmemAcc<Reg> acc{reg, sF, sJlo, sJhi, {js[0], js[1], js[2]}, qb[q]};
+            SmemAcc<Reg> acc{reg, sF, sJlo, sJhi, s_js, qb[q]};
             deposit_general<ORDER>(acc, o, d, s, fac);
         }
         __syncthreads();
         // one flush of the region's current to global memory: hi 2^19 + lo back to float
-        const float jinv[3] = {(float)sp.jinv[0], (float)sp.jinv[1], (float)sp.jinv[2]};
+        const float jinv[3] = {s_jinv[0], s_jinv[1], s_jinv[2]};
         for (int l = threadIdx.x; l < R3; l += blockDim.x) {
             const int lz = l / R2, rem = l - lz * R2, ly = rem / Rx, lx = rem - ly * Rx;
             if (ly >= Ry) continue;   // plane padding (never written by a particle)
@@ -637,7 +695,7 @@ k_push(SpeciesDev sp, GridDev g, TileDev t, FieldsDev f, ExtDev ext, int *work, 
             bool have = false;
             for (int comp = 0; comp < 3; comp++) have = have || sJlo[comp * R3 + l] != 0u || sJhi[comp * R3 + l] != 0;
             if (!have) continue;
-            gi = interior ? gbase + lz * gnxy + ly * gnx + lx : wrap_node(g, reg0[0] + lx, reg0[1] + ly, reg0[2] + lz);
+            gi = interior ? gbase + lz * gnxy + ly * gnx + lx : wrap_node(g, reg0[0] + lx, reg0[1] + ly, reg0[2] + lz, zb);
             if (gi < 0) { atomicOr(err, ERR_INDEX); continue; }
             for (int comp = 0; comp < 3; comp++) {
                 const unsigned lo = sJlo[comp * R3 + l];
@@ -648,6 +706,31 @@ k_push(SpeciesDev sp, GridDev g, TileDev t, FieldsDev f, ExtDev ext, int *work, 
             }
         }
     }
+    // sparse tiles (fewer than kSparse particles): staging and flushing a region would cost more
+    // than the global-memory path of their few particles; each warp takes whole tiles
+    const int n_sparse = sp.count[3];
+    const int kpt = t.tile_cells * 8;
+    for (;;) {
+        int it = 0;
+        if (lane == 0) it = atomicAdd(work_sparse, 1);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= n_sparse) break;
+        const int tile = t.sparse_tiles[it];
+        const int pe = t.cell_start[(tile + 1) * kpt];
+        for (int p = t.cell_start[tile * kpt] + lane; p < pe; p += 32) step_global<ORDER, FROZEN>(sp, g, f, ext, err, p);
+    }
+}
+
+// Next step's displacement bound per component: four times the largest displacement of this step,
+// within [light * 2^-10, light] (light: the speed-of-light bound); the measurement restarts.
+static __global__ void k_dlim_update(float *dlim, unsigned *dmax, float l0, float l1, float l2)
+{
+    const int k = threadIdx.x;
+    if (k >= 3) return;
+    const float light = k == 0 ? l0 : (k == 1 ? l1 : l2);
+    const float m = __uint_as_float(dmax[k]);
+    dlim[k] = fminf(light, fmaxf(4.f * m, light * 0x1p-10f));
+    dmax[k] = 0u;
 }
 
 template <int ORDER, bool FROZEN, class Reg>
@@ -666,8 +749,13 @@ cudaError_t launch_t(pic_ctx *c, int si, const ExtDev &ext, Reg reg, int R3)
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     FieldsDev f{c->E, c->B, c->J};
     kern<<<c->num_sms * per_sm, kPushThreads, smem, c->stream>>>(species_dev(c, s), grid_dev(c), t, f, ext,
-                                                                   c->work + si, c->err, reg);
-    c->kernels++;
+                                                                   c->work + si, c->work + kMaxSpecies + si, c->err,
+                                                                   reg);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    float light[3];
+    for (int d = 0; d < 3; d++) light[d] = (float)std::min(1.0, c->dt / c->d[d]);
+    k_dlim_update<<<1, 32, 0, c->stream>>>(s.dlim, s.dmax, light[0], light[1], light[2]);
+    c->kernels += 2;
     return cudaGetLastError();
 }
 

@@ -104,7 +104,7 @@ class Workload:
         x0, x1, y0, y1 = p.xrange
         lo = 1 if self.order == 1 else 2
         hi = 2 if self.order == 1 else 3
-        nz = self.grid[2] - lo - hi
+        nz = self.grid[2] if self.bc[2][0] == PERIODIC else self.grid[2] - lo - hi
         return (x1 - x0) * (y1 - y0) * nz * p.ppc[0] * p.ppc[1] * p.ppc[2]
 
 
@@ -213,6 +213,74 @@ def mini_plasma(seed=12, grid=(28, 26, 52), n_beam=4000, steps=20):
 def mini_long_undulator(seed=13):
     w = long_undulator(grid=(24, 20, 48), n_beam=4000, steps=20, seed=seed, pml=4,
                        name="mini long undulator 24x20x48")
+    return w
+
+
+@dataclasses.dataclass
+class Ensemble:
+    """Independent runs sharing grid, cell size, time step, boost, boundaries and shape (the
+    base workload); run r has undulator K[r], plasma density scale dens_scale[r] (times the
+    base plasma profile) and n_beam[r] beam macroparticles of the base beam's shape and charge,
+    sampled with seed base.seed * 1000 + r."""
+    base: Workload
+    K: Tuple[float, ...]
+    dens_scale: Tuple[float, ...]
+    n_beam: Tuple[int, ...]
+
+    @property
+    def runs(self) -> int:
+        return len(self.K)
+
+
+def batched_ensemble(runs=64, grid=(64, 64, 128), steps=1000, seed=4, order=2, ppc=(1, 2, 2),
+                     K_range=(0.5, 2.0), n_lab_cm3=(1e14, 1e16), n_beam_range=(1e5, 1e6),
+                     name="C4 batched ensemble 64 x (64x64x128), K and density sweep, TSC") -> Ensemble:
+    """Batched sweep: periodic runs on a cubic grid of 64 cells per RRF undulator period
+    (boost 10, lab gamma 100 beam of 30 pC, lambda_u = 2 cm; the undulator normalisation
+    w_n = 2 pi gamma_R c / lambda_u is shared by every run), undulator K uniform in
+    K_range, lab plasma density log-uniform in n_lab_cm3 (cold, lab-static, 4 per cell, frozen
+    ions), beam macroparticles log-uniform in n_beam_range (uneven), second-order shape."""
+    gR = 10.0
+    lam_u_m = 0.02
+    omega_n = 2 * math.pi * gR * C_LIGHT / lam_u_m
+    L = C_LIGHT / omega_n
+    dx = 2 * math.pi / 64
+    d = (dx, dx, dx)
+    dt = courant_dt(d, 0.5)
+    # lab rms length mapping to 12 RRF cells (elongation 19.754 at gamma 100 in a boost of 10)
+    sigma_z = 12 * dx / 19.754
+    beam = Beam(n=0, gamma=100.0, rel_spread=1e-3, emit_n=1e-6 / L, sigma_r=6 * dx, sigma_z=sigma_z,
+                weight=0.0, origin=(grid[0] / 2, grid[1] / 2, grid[2] / 2))
+    und = Undulator(K=1.0, lambda_u=lam_u_m / L, match=True)
+    nz = grid[2]
+    plasma = Plasma(ppc=ppc, xrange=(0, grid[0], 0, grid[1]), z_nodes=(-1e12, 1e12), n_nodes=(1.0, 1.0))
+    base = Workload(name=name, grid=grid, d=d, dt=dt, gamma_R=gR, bc=((PERIODIC, PERIODIC),) * 3, pml=0,
+                    order=order, moving_window=False, window_v=0.0, beam=beam, undulator=und,
+                    plasma=plasma, steps=steps, length_unit_m=L, seed=seed)
+    rng = np.random.Generator(np.random.Philox(key=seed))
+    K = tuple(float(v) for v in rng.uniform(K_range[0], K_range[1], runs))
+    n_unit_cm3 = density_unit(omega_n) * 1e-6
+    dens = tuple(float(10 ** v / n_unit_cm3) for v in rng.uniform(math.log10(n_lab_cm3[0]), math.log10(n_lab_cm3[1]), runs))
+    nb = tuple(int(round(10 ** v)) for v in rng.uniform(math.log10(n_beam_range[0]), math.log10(n_beam_range[1]), runs))
+    return Ensemble(base=base, K=K, dens_scale=dens, n_beam=nb)
+
+
+def mini_ensemble(runs=3, seed=14):
+    """Three runs of 16 x 16 x 32 cells (two 8^3 tiles in z each), uneven beams, for parity."""
+    e = batched_ensemble(runs=runs, grid=(16, 16, 32), steps=20, seed=seed, n_lab_cm3=(3e13, 3e15),
+                         n_beam_range=(300, 3000), name=f"mini ensemble {runs} x (16x16x32)")
+    e.base.beam.sigma_r = 2 * e.base.d[0]
+    e.base.beam.sigma_z = 4 * e.base.d[2] / 19.754
+    return e
+
+
+def ensemble_run(e: Ensemble, r: int) -> Workload:
+    """Run r of an ensemble as a single-run workload (its K, scaled plasma and beam size)."""
+    b = e.base
+    w = dataclasses.replace(b, name=f"{b.name} run {r}", seed=b.seed * 1000 + r)
+    w.undulator = dataclasses.replace(b.undulator, K=e.K[r])
+    w.plasma = dataclasses.replace(b.plasma, n_nodes=tuple(v * e.dens_scale[r] for v in b.plasma.n_nodes))
+    w.beam = dataclasses.replace(b.beam, n=e.n_beam[r], weight=beam_weight(30e-12, e.n_beam[r], C_LIGHT / b.length_unit_m))
     return w
 
 

@@ -16,7 +16,9 @@ def declared_functions():
 def test_header_declares_the_boundary():
     names = declared_functions()
     for need in ["pic_create", "pic_load_species", "pic_set_external_field", "pic_set_plasma", "pic_step",
-                 "pic_get_fields", "pic_get_moments", "pic_destroy", "pic_last_error"]:
+                 "pic_get_fields", "pic_get_moments", "pic_destroy", "pic_last_error", "pic_create_batch",
+                 "pic_load_species_batch", "pic_set_external_field_batch", "pic_set_plasma_batch",
+                 "pic_get_moments_run"]:
         assert need in names
 
 

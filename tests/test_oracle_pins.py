@@ -427,6 +427,55 @@ def test_moving_window_and_plasma_injection_keep_lattice_density():
     assert max(np.max(np.abs(s.field(c))) for c in range(9)) < 1e-12
 
 
+def test_periodic_box_plasma_fills_once_and_drifts_rigidly():
+    # Periodic box (reading: the lattice fills the box once and drifts around it): exactly ppc
+    # particles per cell at every step, a neutral plasma keeps zero fields, and the total
+    # weight is gamma_R times the lab profile integrated over the box's lab image (Eq. Nnormi;
+    # midpoint sums of a linear profile are exact).
+    grid = (4, 4, 12)
+    d = (1.0, 1.0, 0.7)
+    gR = 3.0
+    dt = 0.3
+    s = oracle.Sim(grid, d, dt, gR, bc=((PERIODIC, PERIODIC),) * 3, order=2)
+    se = s.add_species(-1.0, 1.0)
+    si = s.add_species(1.0, 1836.0, frozen=True)
+    zl = gR * grid[2] * d[2]
+    n_a, n_b = 0.2, 0.5
+    s.set_plasma(se, si, (1, 2, 2), (0, 4, 0, 4), (0.0, zl), (n_a, n_b))
+    per_cell = 4
+    assert s.count(se) == s.count(si) == grid[0] * grid[1] * grid[2] * per_cell
+    _, _, W, _ = s.particles(se)
+    lab_integral = 0.5 * (n_a + n_b) * zl                    # int n_lab dz_lab over the image
+    expect = gR * lab_integral / gR * d[0] * d[1] * grid[0] * grid[1]   # dz' = dz_lab / gR
+    assert np.sum(W) == pytest.approx(expect, rel=1e-12)
+    for n in range(30):
+        for sp in (se, si):
+            X, U, _, _ = s.particles(sp)
+            counts = np.bincount(np.floor(X[:, 2]).astype(int), minlength=grid[2])
+            assert np.all(counts == grid[0] * grid[1] * per_cell), (n, counts)
+        s.step(1)
+    # only a uniform plasma is neutral node by node; here the profile varies, so just check
+    # that electrons and ions still coincide (ions frozen at the electrons' initial drift)
+    Xe, Ue, _, ie = s.particles(se)
+    Xi, Ui, _, ii = s.particles(si)
+    assert np.array_equal(ie, ii)
+    assert np.max(np.abs(Ui[:, 2] + gR * math.sqrt(1 - 1 / gR ** 2))) < 1e-12
+
+
+def test_uniform_periodic_plasma_stays_field_free():
+    # uniform neutral drifting plasma in a periodic box: rho = 0 and J = 0 at every node, so the
+    # fields stay exactly zero and the electrons are never accelerated
+    grid = (4, 4, 8)
+    s = oracle.Sim(grid, (1.0, 1.0, 1.0), 0.4, 5.0, bc=((PERIODIC, PERIODIC),) * 3, order=1)
+    se = s.add_species(-1.0, 1.0)
+    si = s.add_species(1.0, 1836.0, frozen=True)
+    s.set_plasma(se, si, (2, 1, 2), (0, 4, 0, 4), (-1e9, 1e9), (0.7, 0.7))
+    s.step(25)
+    assert max(np.max(np.abs(s.field(c))) for c in range(9)) < 1e-12
+    _, U, _, _ = s.particles(se)
+    assert np.max(np.abs(U[:, :2])) < 1e-12
+
+
 def test_moments_definitions():
     grid = (4, 4, 64)
     d = (1.0, 1.0, 0.25)
