@@ -105,6 +105,28 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def oracle_sample_vacuum(steps, warmup, seed=1):
+    """FP64 oracle on the whole vacuum-undulator workload (32 x 32 x 64, 65,536 beam, CIC)."""
+    import oracle
+    from paper_2411_04703_gb300 import workloads as W
+    oracle.build()
+    w = W.vacuum_undulator(seed=seed)
+    o = oracle.Sim(w.grid, w.d, w.dt, w.gamma_R, bc=w.bc, order=w.order)
+    o.set_external(w.undulator.K, w.undulator.lambda_u)
+    sb = o.add_species(-1.0, 1.0)
+    x, u, wt = W.sample_beam(w)
+    o.load(sb, x, u, wt, frame=0, origin=w.beam.origin, match_undulator=True)
+    if warmup:
+        o.step(warmup)
+    n0 = o.count(sb)
+    t0 = time.perf_counter()
+    o.step(steps)
+    t = time.perf_counter() - t0
+    value = 0.5 * (n0 + o.count(sb)) * steps / t
+    sample = f"FP64 oracle, the whole vacuum-undulator workload ({n0} beam, CIC), {steps} steps, single thread"
+    return value, t, sample
+
+
 def oracle_sample_ensemble(steps, warmup, seed=4):
     """FP64 oracle on a bounded sample of the batched ensemble: run 0 on a 32 x 32 x 64 sub-box
     (same cells, K, plasma density and particles per cell; beam scaled with the volume)."""
@@ -218,7 +240,17 @@ def run_gbpic(args):
             dist.barrier()
 
     ens = None
-    if args.workload == "ensemble":
+    tuned = None
+    if args.workload == "vacuum":
+        # the vacuum undulator 32x32x64, 65,536 beam electrons, CIC: small enough to be bound by
+        # launches, so its step sequence runs as a replayed CUDA graph
+        w = W.vacuum_undulator(seed=1 + rank)
+        beam = W.sample_beam(w)
+        sim, ids = api.from_workload(w, device=local, beam_arrays=beam)
+        ncell_total = w.ncell
+        boundaries = "periodic"
+        l2 = "L2-resident (fields 2.4 MB, particles 2 MB): launch-bound, timed as a CUDA graph"
+    elif args.workload == "ensemble":
         # batched sweep: 64 runs of 64x64x128 stacked in one context (one launch per kernel)
         import numpy as np
         ens = W.batched_ensemble(runs=args.runs, seed=4 + rank)
@@ -228,6 +260,13 @@ def run_gbpic(args):
                 np.concatenate([q[2] for q in parts]))
         if args.sort_every:
             ens.base.sort_every = args.sort_every
+        elif not args.no_autotune:
+            # the autotuner's trials advance a run: tune on a throwaway copy, measure a fresh one
+            tmp, _ = api.from_ensemble(ens, device=local)
+            ens.base.sort_every = tuned = tmp.autotune(16)
+            tmp.close()
+            del tmp
+            torch.cuda.empty_cache()
         sim, ids = api.from_ensemble(ens, device=local)
         ncell_total = w.ncell * ens.runs
         boundaries = "periodic (each run)"
@@ -238,24 +277,30 @@ def run_gbpic(args):
         w = W.plasma_buncher(grid=grid, n_beam=nb, seed=2 + rank)
         if grid != (128, 128, 512):
             w.name = f"plasma buncher {grid[0]}x{grid[1]}x{grid[2]} (reduced), {nb} beam + 8 ppc plasma, TSC"
+        beam = W.sample_beam(w)
         if args.sort_every:
             w.sort_every = args.sort_every
-        beam = W.sample_beam(w)
+        elif args.autotune:
+            tmp, _ = api.from_workload(w, device=local, beam_arrays=beam)
+            w.sort_every = tuned = tmp.autotune(16)
+            tmp.close()
+            del tmp
+            torch.cuda.empty_cache()
         sim, ids = api.from_workload(w, device=local, beam_arrays=beam)
         ncell_total = w.ncell
         boundaries = "transverse CPML 10 cells, moving window"
         l2 = "inputs larger than L2 (particle state ~9 GB, fields 0.3 GB)"
-    tuned = None
-    if not args.no_autotune:
-        tuned = sim.autotune(16)   # timed trials of the sort cadence (untimed here, advance the run)
-    sim.trace_enable(True)
+    # periodic workloads replay their steps as CUDA graphs (tracing would turn that off): their
+    # kernel-class composition comes from a traced pass after the timed region
+    graphs = args.workload in ("vacuum", "ensemble")
+    sim.trace_enable(not graphs)
     if args.warmup:
         sim.step(args.warmup)
     sim.sync()
     sim.trace_read()
-    pushed = [ids["beam"], ids["plasma_e"]]
+    pushed = [ids[k] for k in ("beam", "plasma_e") if k in ids]
     n0 = sum(sim.get_count(s) for s in pushed)
-    frozen0 = sim.get_count(ids["plasma_i"])
+    frozen0 = sim.get_count(ids["plasma_i"]) if "plasma_i" in ids else 0
     stream = sim.stream
     clocks = ClockSampler(local)
     clocks.start()
@@ -270,9 +315,15 @@ def run_gbpic(args):
     barrier()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
-    tr = sim.trace_read()
     n1 = sum(sim.get_count(s) for s in pushed)
-    frozen1 = sim.get_count(ids["plasma_i"])
+    frozen1 = sim.get_count(ids["plasma_i"]) if "plasma_i" in ids else 0
+    kernels_timed = None
+    if graphs:
+        kernels_timed = sim.trace_read()["kernels"]
+        sim.trace_enable(True)
+        sim.step(args.steps)
+        sim.sync()
+    tr = sim.trace_read()
     psteps = 0.5 * (n0 + n1) * args.steps
     psteps_all, ms_max = aggregate(psteps, ms, world, dev)
     value = psteps_all / (ms_max / 1000.0)
@@ -284,9 +335,12 @@ def run_gbpic(args):
     n_e = 0.5 * (n0 + n1) - n_beam
     classes = tr["ms"]
     dom = max(("push", "push_frozen", "fields", "sort"), key=lambda k: classes[k])
+    shape = "CIC" if w.order == 1 else "TSC"
     if dom == "push":
+        # one launch per mobile species per step; each reads E, B of the grid and writes J once
         launches = tr["events"]["push"]
-        bytes_per = ((n_e + n_beam) * BYTES_PUSHED + 2 * ncell * BYTES_CELL_PUSH) / 2.0
+        per_step = max(1, round(launches / args.steps))
+        bytes_per = ((n_e + n_beam) * BYTES_PUSHED + per_step * ncell * BYTES_CELL_PUSH) / per_step
     elif dom == "push_frozen":
         launches = tr["events"]["push_frozen"]
         bytes_per = 0.5 * (frozen0 + frozen1) * BYTES_FROZEN + ncell * 12.0
@@ -300,8 +354,8 @@ def run_gbpic(args):
     achieved = bytes_per / (avg_ms / 1000.0) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": None,
-                "kernel": {"push": "k_push<TSC, mobile> (beam + plasma electrons)",
-                           "push_frozen": "k_push<TSC, frozen> (ions)", "fields": "k_fdtd_b/e",
+                "kernel": {"push": f"k_push<{shape}, mobile> (" + " + ".join(k for k in ("beam", "plasma_e") if k in ids) + ")",
+                           "push_frozen": f"k_lattice / k_push<{shape}, frozen> (ions)", "fields": "k_fdtd_b/e",
                            "sort": "tile sort"}[dom],
                 "peak_kind": f"{peak_kind} (hbm_gbs)",
                 "avg_launch_ms": avg_ms,
@@ -326,7 +380,7 @@ def run_gbpic(args):
         sim2.sync()
         barrier()
         torch.cuda.synchronize()
-        ne_plasma0 = sim2.get_count(ids2["plasma_e"])
+        ne_plasma0 = sim2.get_count(ids2["plasma_e"]) if "plasma_e" in ids2 else 0
         t0 = time.perf_counter()
         b = w.beam
         match = bool(w.undulator is not None and w.undulator.match)
@@ -341,7 +395,7 @@ def run_gbpic(args):
         t_e2e = time.perf_counter() - t0
         # particle counts for the metric, read outside the timed region
         ne0 = sim2.get_count(sb) + ne_plasma0
-        ne1 = int(mom["count"]) + sim2.get_count(ids2["plasma_e"])
+        ne1 = int(mom["count"]) + (sim2.get_count(ids2["plasma_e"]) if "plasma_e" in ids2 else 0)
         barrier()
         h2d = (xh.numel() + uh.numel() + wh.numel()) * 8
         e2e = {"value": 0.5 * (ne0 + ne1) * args.steps * world / t_e2e, "unit": UNIT,
@@ -353,7 +407,12 @@ def run_gbpic(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cv, ct, sample = oracle_sample_ensemble(2, 0) if ens is not None else oracle_sample(3, 0)
+        if args.workload == "vacuum":
+            cv, ct, sample = oracle_sample_vacuum(20, 0)
+        elif ens is not None:
+            cv, ct, sample = oracle_sample_ensemble(2, 0)
+        else:
+            cv, ct, sample = oracle_sample(3, 0)
         cpu = {"value": cv, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
 
     if rank == 0:
@@ -363,13 +422,14 @@ def run_gbpic(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": w.name, "grid": list(w.grid), "beam": int(n_beam),
                        "plasma_electrons": int(n_e), "frozen_ions": int(0.5 * (frozen0 + frozen1)),
-                       "shape": "TSC", "boundaries": boundaries,
+                       "shape": shape, "boundaries": boundaries,
                        "tile": list(w.tile), "sort_every": tuned if tuned else w.sort_every,
                        "sort_every_from": "autotuner" if tuned else "workload",
                        "l2": l2,
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-            "gpu_launches": int(tr["kernels"]),
+            "gpu_launches": int(kernels_timed if kernels_timed is not None else tr["kernels"]),
+            "cuda_graphs": bool(graphs),
             "fallback_deposits": int(tr.get("fallback", 0)),
         }
         print(json.dumps(line))
@@ -391,8 +451,11 @@ def main():
     ap.add_argument("--beam", type=int, default=0, help="beam macroparticles (0: scaled with the grid)")
     ap.add_argument("--sort-every", type=int, default=0, help="steps between tile sorts (0: the workload's)")
     ap.add_argument("--runs", type=int, default=64, help="ensemble runs (the batched sweep has 64)")
-    ap.add_argument("--no-autotune", action="store_true", help="keep the workload's sort cadence")
-    ap.add_argument("--workload", choices=["buncher", "ensemble"], default="buncher",
+    ap.add_argument("--no-autotune", action="store_true", help="ensemble: keep the workload's sort cadence")
+    ap.add_argument("--autotune", action="store_true",
+                    help="buncher: pick the sort cadence with the autotuner (its slow drift makes the "
+                         "cadence matter little; the default keeps 8)")
+    ap.add_argument("--workload", choices=["buncher", "ensemble", "vacuum"], default="buncher",
                     help="buncher: the plasma buncher 128x128x512 (default); ensemble: the batched sweep "
                          "of 64 runs of 64x64x128 in one context")
     args = ap.parse_args()

@@ -212,15 +212,23 @@ int pic_set_plasma_batch(pic_ctx *ctx, const pic_plasma *p, const double *densit
  * The current of a tile is summed exactly in fixed point (order-independent) with a scale set per
  * species and step from four times the largest displacement of the previous step; a particle
  * moving further, and every particle of a tile holding fewer than 32, adds its current with
- * float atomics instead.  Asynchronous on the context stream. */
+ * float atomics instead.  Without a moving window or plasma injection (periodic z) and with
+ * tracing off, whole pairs of sort periods are captured once into a CUDA graph and replayed
+ * (see pic_use_graphs); a step counter on the device gives each replayed step its time.
+ * Asynchronous on the context stream. */
 int pic_step(pic_ctx *ctx, int64_t n);
 
+/* Replay of captured step sequences in pic_step (on = 1, the default) or one launch per kernel
+ * (on = 0).  The capture is redone when species, the external field or the tuning change; if
+ * capturing fails the context falls back to launching. */
+int pic_use_graphs(pic_ctx *ctx, int on);
+
 /* Autotuner of the tile-sort cadence (tile and sort sizes picked by an autotuner the project
- * writes).  Runs trials of whole sort periods (>= 8 steps each) with sort_every = 1, 2, 3, 4, 6,
+ * writes).  Runs trials of whole sort periods (>= 32 steps each) with sort_every = 1, 2, 3, 4, 6,
  * 8, 12, 16, 24, 32 (up to max_sort_every), each starting with a sort, in two passes (ascending,
  * then descending), times them with CUDA events on the context stream and keeps the fastest per
  * step (a rarer sort must win by 2 %).  The trial steps are real steps: the simulation advances
- * by their total (about 200 steps for max_sort_every = 16).  A
+ * by their total (about 500 steps for max_sort_every = 16).  A
  * fast drift (cells per step) favours frequent sorts, a slow one rare sorts; the tile stays the
  * compiled 8x8x8 region.  *sort_every_out (may be NULL) receives the choice.  Synchronous. */
 int pic_autotune(pic_ctx *ctx, int max_sort_every, int *sort_every_out);

@@ -114,6 +114,7 @@ def lib(build_if_missing: bool = True):
             "pic_set_plasma_batch": [vp, P(pic_plasma), P(d), P(i), P(i)],
             "pic_get_moments_run": [vp, i, i, i, d, P(pic_moments)],
             "pic_autotune": [vp, i, P(i)],
+            "pic_use_graphs": [vp, i],
             "pic_set_tuning": [vp, P(pic_tuning)],
             "pic_load_species": [vp, P(pic_species), i64, vp, vp, vp, i, P(i)],
             "pic_set_external_field": [vp, P(pic_external)],
@@ -320,6 +321,10 @@ class Sim:
     # ------------------------------------------------------------------ stepping
     def step(self, n=1):
         self._check(self.L.pic_step(self.h, int(n)))
+
+    def use_graphs(self, on=True):
+        """Replay captured step sequences (CUDA graphs) where the step allows it."""
+        self._check(self.L.pic_use_graphs(self.h, int(bool(on))))
 
     def autotune(self, max_sort_every=16):
         """Pick the sort cadence by timed trials (advances the simulation); returns it."""

@@ -91,11 +91,14 @@ int check_ctx(pic_ctx *c)
     return PIC_OK;
 }
 
+void drop_graph(pic_ctx *c);
+
 // Largest displacement (cells) along d in one step: the speed of light, min(1, dt / d_d).
 double light_bound(const pic_ctx *c, int d) { return std::min(1.0, c->dt / c->d[d]); }
 
 int make_species(pic_ctx *c, double q, double m, int frozen, int64_t cap, int *sid, bool lattice = false)
 {
+    drop_graph(c);   // a captured step sequence does not know the new species
     if (c->nsp >= kMaxSpecies) return fail(c, PIC_ERR_ARG, "too many species (max 8)");
     if (cap < 1 || cap >= (int64_t)std::numeric_limits<int>::max() - kChunk)
         return fail(c, PIC_ERR_ARG, "species capacity out of range");
@@ -106,7 +109,7 @@ int make_species(pic_ctx *c, double q, double m, int frozen, int64_t cap, int *s
     s.m = m;
     s.frozen = frozen ? 1 : 0;
     s.cap = cap;
-    s.max_items = c->ntiles + cap / kChunk + 2;
+    s.max_items = c->ntiles + cap / kChunkMin + 2;
     int r;
     if (lattice) {
         // a ring of lattice planes replaces the particle records: live planes span the active z
@@ -282,18 +285,21 @@ ExtDev ext_step(const pic_ctx *c)
     x.theta = (float)std::fmod(kp * ((double)c->shifts * c->d[2] + c->bR * tp) + c->phase0, two_pi);
     x.phase_tab = c->phase_tab;
     x.amp_tab = c->amp_tab;
+    x.clock = c->dclock;
+    {
+        const double kp = c->ku * c->gR;
+        x.th_a = kp * c->bR * c->dt;
+        x.th_b = kp * (double)c->shifts * c->d[2] + c->phase0;
+    }
     if (std::isfinite(c->z_start) && c->ramp >= 0.0) {
         const double a = c->gR * c->d[2];
         const double b = c->gR * ((double)c->shifts * c->d[2] + c->bR * tp) - c->z_start;
-        if (c->ramp > 0.0) {
-            x.ramp_mode = 1;
-            x.ramp_a = (float)(a / c->ramp);
-            x.ramp_b = (float)(b / c->ramp);
-        } else {
-            x.ramp_mode = 2;
-            x.ramp_a = (float)a;
-            x.ramp_b = (float)b;
-        }
+        const double sc = c->ramp > 0.0 ? 1.0 / c->ramp : 1.0;
+        x.ramp_mode = c->ramp > 0.0 ? 1 : 2;
+        x.ramp_a = (float)(a * sc);
+        x.ramp_b = (float)(b * sc);
+        x.rb_a = c->gR * c->bR * c->dt * sc;
+        x.rb_b = (c->gR * (double)c->shifts * c->d[2] - c->z_start) * sc;
     }
     return x;
 }
@@ -334,6 +340,7 @@ TileDev tile_dev(const pic_ctx *c, const Species &s)
     t.cell_start = s.cell_start;
     t.items = s.items;
     t.sparse_tiles = s.sparse_tiles;
+    t.chunk = s.chunk;
     t.cc = c->cc;
     return t;
 }
@@ -487,6 +494,7 @@ int create_impl(pic_ctx **out, int runs, pic_grid grid, const double dx[3], doub
     int r;
     if ((r = alloc_zero(c, &c->E, 3 * c->ncell)) || (r = alloc_zero(c, &c->B, 3 * c->ncell)) ||
         (r = alloc_zero(c, &c->J, 3 * c->ncell)) || (r = alloc_zero(c, &c->err, 4)) || (r = alloc_zero(c, &c->nfall, 1)) ||
+        (r = alloc_zero(c, &c->dclock, 1)) ||
         (r = alloc_zero(c, &c->work, 2 * kMaxSpecies)) || (r = alloc_zero(c, &c->red, 512 * 16 + 1024)) ||
         (r = alloc_zero(c, &c->shift_tab, 24)) || (r = alloc_tile_scratch(c)))
         return bail(r);
@@ -575,6 +583,7 @@ int pic_set_tuning(pic_ctx *c, const pic_tuning *t)
     if (c->runs > 1 && c->nzr % t->tile[2] != 0)
         return fail(c, PIC_ERR_ARG, "ensemble: the tile's z size must divide the rows of a run");
     for (int d = 0; d < 3; d++) c->T[d] = t->tile[d];
+    drop_graph(c);
     c->sort_every = t->sort_every;
     c->M = t->margin;
     set_tiles(c);
@@ -681,6 +690,7 @@ int pic_set_external_field(pic_ctx *c, const pic_external *f)
     }
     if (f->type != PIC_EXT_PLANAR_UNDULATOR) return fail(c, PIC_ERR_ARG, "unknown external field type");
     if (!(f->lambda_u > 0)) return fail(c, PIC_ERR_ARG, "lambda_u must be > 0");
+    drop_graph(c);   // captured launches hold the field's constants
     c->ext_type = f->type;
     c->K = f->K;
     c->lam_u = f->lambda_u;
@@ -824,50 +834,155 @@ int pic_set_plasma_batch(pic_ctx *c, const pic_plasma *p, const double *density_
     return plasma_impl(c, p, density_scale, electron_id, ion_id);
 }
 
+}  // extern "C"
+
+namespace {
+
+__global__ void k_tick(long long *clock) { *clock += 1; }
+
+// One step of the method (the body of pic_step).
+int step_once(pic_ctx *c)
+{
+    int r;
+    if ((c->step - c->sort_base) % c->sort_every == 0) {
+        TraceScope ts(c, TR_SORT);
+        for (int si = 0; si < c->nsp; si++)
+            if (!c->sp[si].lattice) CK(launch_sort(c, si));
+    }
+    // the lattice species writes J_z whole, before the other species add to it
+    const bool lat = c->plasma && c->sp[c->sp_i].lattice;
+    CK(cudaMemsetAsync(c->J, 0, sizeof(float) * (lat ? 2 : 3) * c->ncell, c->stream));
+    CK(cudaMemsetAsync(c->work, 0, sizeof(int) * 2 * kMaxSpecies, c->stream));
+    if (lat) {
+        TraceScope ts(c, TR_PUSH_FROZEN);
+        CK(launch_lattice_step(c, c->sp_i));
+    }
+    const ExtDev ext = ext_step(c);
+    for (int si = 0; si < c->nsp; si++) {
+        if (c->sp[si].lattice) continue;
+        TraceScope ts(c, c->sp[si].frozen ? TR_PUSH_FROZEN : TR_PUSH);
+        CK(launch_push(c, si, ext));
+    }
+    {
+        TraceScope ts(c, TR_FIELDS);
+        CK(launch_fdtd_b(c, (float)(0.5 * c->dt)));
+        CK(launch_fdtd_e(c));
+        CK(launch_fdtd_b(c, (float)(0.5 * c->dt)));
+    }
+    k_tick<<<1, 1, 0, c->stream>>>(c->dclock);
+    CK(cudaGetLastError());
+    c->kernels++;
+    c->step++;
+    if (c->moving) {
+        const int64_t due = (int64_t)shifts_due(c, c->step);
+        while (c->shifts < due) {
+            TraceScope ts(c, TR_WINDOW);
+            CK(launch_shift_fields(c));
+            for (int si = 0; si < c->nsp; si++)
+                CK(c->sp[si].lattice ? launch_lattice_shift(c, si) : launch_shift_particles(c, si));
+            c->shifts++;
+        }
+    }
+    if (c->plasma && (r = inject_due(c))) return r;
+    return PIC_OK;
+}
+
+// A step sequence can be captured once and replayed when nothing the host decides per step
+// changes between periods: no moving window, no plasma injection (periodic z), tracing off.
+bool graph_eligible(const pic_ctx *c)
+{
+    if (!c->use_graphs || c->moving || c->trace_on || c->nsp == 0) return false;
+    if (c->plasma && c->bc[2][0] != PIC_BC_PERIODIC) return false;
+    return true;
+}
+
+void drop_graph(pic_ctx *c)
+{
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+    c->graph_steps = 0;
+    c->graph_key = nullptr;
+}
+
+const void *pointer_key(const pic_ctx *c)
+{
+    for (int si = 0; si < c->nsp; si++)
+        if (!c->sp[si].lattice) return c->sp[si].pos;
+    return nullptr;
+}
+
+// Captures `period` steps (two sort periods: every sort swaps the particle buffers, so after two
+// the buffers the graph's kernels address are current again) without executing them; the host
+// state the capture advanced is restored.
+// If capturing fails the context falls back to launching every step (graphs off) and stays usable.
+void capture_graph(pic_ctx *c, int64_t period)
+{
+    drop_graph(c);
+    const int64_t step0 = c->step, kern0 = c->kernels;
+    const bool poisoned0 = c->poisoned;
+    const std::string msg0 = c->msg;
+    if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+        cudaGetLastError();
+        c->use_graphs = 0;
+        return;
+    }
+    int r = PIC_OK;
+    for (int64_t k = 0; k < period && r == PIC_OK; k++) r = step_once(c);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    c->step = step0;
+    const int64_t captured = c->kernels - kern0;
+    c->kernels = kern0;
+    cudaGraphExec_t x = nullptr;
+    if (r == PIC_OK && e == cudaSuccess && g && cudaGraphInstantiate(&x, g, 0) == cudaSuccess) {
+        c->graph = x;
+        c->graph_steps = period;
+        c->graph_kernels = captured;
+        c->graph_key = pointer_key(c);
+    } else {
+        cudaGetLastError();
+        c->poisoned = poisoned0;
+        c->msg = msg0;
+        c->use_graphs = 0;
+    }
+    if (g) cudaGraphDestroy(g);
+}
+
+}  // namespace
+
+extern "C" {
+
 int pic_step(pic_ctx *c, int64_t nsteps)
 {
     int r = check_ctx(c);
     if (r) return r;
     if (nsteps < 0) return fail(c, PIC_ERR_ARG, "negative step count");
-    for (int64_t it = 0; it < nsteps; it++) {
-        if ((c->step - c->sort_base) % c->sort_every == 0) {
-            TraceScope ts(c, TR_SORT);
-            for (int si = 0; si < c->nsp; si++)
-                if (!c->sp[si].lattice) CK(launch_sort(c, si));
-        }
-        // the lattice species writes J_z whole, before the other species add to it
-        const bool lat = c->plasma && c->sp[c->sp_i].lattice;
-        CK(cudaMemsetAsync(c->J, 0, sizeof(float) * (lat ? 2 : 3) * c->ncell, c->stream));
-        CK(cudaMemsetAsync(c->work, 0, sizeof(int) * 2 * kMaxSpecies, c->stream));
-        if (lat) {
-            TraceScope ts(c, TR_PUSH_FROZEN);
-            CK(launch_lattice_step(c, c->sp_i));
-        }
-        const ExtDev ext = ext_step(c);
-        for (int si = 0; si < c->nsp; si++) {
-            if (c->sp[si].lattice) continue;
-            TraceScope ts(c, c->sp[si].frozen ? TR_PUSH_FROZEN : TR_PUSH);
-            CK(launch_push(c, si, ext));
-        }
-        {
-            TraceScope ts(c, TR_FIELDS);
-            CK(launch_fdtd_b(c, (float)(0.5 * c->dt)));
-            CK(launch_fdtd_e(c));
-            CK(launch_fdtd_b(c, (float)(0.5 * c->dt)));
-        }
-        c->step++;
-        if (c->moving) {
-            const int64_t due = (int64_t)shifts_due(c, c->step);
-            while (c->shifts < due) {
-                TraceScope ts(c, TR_WINDOW);
-                CK(launch_shift_fields(c));
-                for (int si = 0; si < c->nsp; si++)
-                    CK(c->sp[si].lattice ? launch_lattice_shift(c, si) : launch_shift_particles(c, si));
-                c->shifts++;
+    const int64_t period = 2 * (int64_t)c->sort_every;
+    int64_t left = nsteps;
+    while (left > 0) {
+        const bool at_start = (c->step - c->sort_base) % period == 0;
+        if (graph_eligible(c) && at_start && left >= period) {
+            if (!c->graph || c->graph_steps != period || c->graph_key != pointer_key(c)) capture_graph(c, period);
+            if (c->graph && c->graph_key == pointer_key(c)) {
+                CK(cudaGraphLaunch(c->graph, c->stream));
+                c->step += period;
+                c->kernels += c->graph_kernels;
+                left -= period;
+                continue;
             }
         }
-        if (c->plasma && (r = inject_due(c))) return r;
+        if ((r = step_once(c))) return r;
+        left--;
     }
+    return PIC_OK;
+}
+
+int pic_use_graphs(pic_ctx *c, int on)
+{
+    int r = check_ctx(c);
+    if (r) return r;
+    c->use_graphs = on ? 1 : 0;
+    if (!on) drop_graph(c);
     return PIC_OK;
 }
 
@@ -893,8 +1008,9 @@ int pic_autotune(pic_ctx *c, int max_sort_every, int *sort_every_out)
         for (int q = 0; q < nc; q++) {
             const int idx = pass == 0 ? q : nc - 1 - q;
             const int se = cand[idx];
-            // each trial starts right after a sort and covers whole sort periods (>= 8 steps)
-            const int64_t steps = ((std::max(8, se) + se - 1) / se) * (int64_t)se;
+            // each trial starts right after a sort and covers whole sort periods (>= 32 steps, so
+            // that rare costly steps such as a window shift average out)
+            const int64_t steps = ((std::max(32, se) + se - 1) / se) * (int64_t)se;
             c->sort_every = se;
             c->sort_base = c->step;   // the trial's first step sorts
             cudaEventRecord(a, c->stream);
@@ -1149,6 +1265,7 @@ int pic_destroy(pic_ctx *c)
 {
     if (!c) return PIC_OK;
     if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->graph) cudaGraphExecDestroy(c->graph);
     for (auto &p : c->ev_pending) {
         cudaEventDestroy(p.second.first);
         cudaEventDestroy(p.second.second);

@@ -13,7 +13,8 @@
 namespace gbpic {
 
 constexpr int kMaxSpecies = 8;
-constexpr int kChunk = 4096;         // particles per work item of the particle kernel
+constexpr int kChunk = 4096;         // particles per work item of the particle kernel (at most)
+constexpr int kChunkMin = 512;       // smallest work item (small species are split finer)
 constexpr int kPushThreads = 512;
 constexpr int kGroup = kChunk / kPushThreads;   // consecutive particles of one lane per work item
 constexpr int kSparse = 32;   // a tile with fewer particles takes the global-memory path, one warp per tile
@@ -72,7 +73,23 @@ struct ExtDev {
     int ramp_mode;        // 0: f = 1; 1: linear ramp; 2: step
     float ramp_a, ramp_b; // ramp argument r = ramp_a (k + off_z) + ramp_b
     const float *amp_tab; // ensembles: gamma_R B0 of the run that owns row k; NULL: B0g everywhere
+    // the step's phase and ramp offset from the device step counter (so that a captured CUDA
+    // graph replays correctly): theta = (th_a n + th_b) mod 2 pi, ramp_b = rb_a n + rb_b
+    const long long *clock;
+    double th_a, th_b, rb_a, rb_b;
 };
+
+// The external field of the current step, from the device step counter.
+__device__ __forceinline__ ExtDev ext_at_clock(const ExtDev &e)
+{
+    ExtDev x = e;
+    if (e.type && e.clock) {
+        const double n = (double)*e.clock;
+        x.theta = (float)fmod(e.th_a * n + e.th_b, 6.283185307179586);
+        x.ramp_b = (float)(e.rb_a * n + e.rb_b);
+    }
+    return x;
+}
 
 struct SpeciesDev {
     float4 *pos;          // (off_x, off_y, off_z, cell bits)
@@ -105,6 +122,7 @@ struct TileDev {
     const int *cell_start;   // [n_keys + 1]: first sorted slot of each key (8 keys per cell)
     const int2 *items;       // (tile, chunk) work items of the tiles with >= kSparse particles
     const int *sparse_tiles; // tiles with 1 .. kSparse-1 particles (count[3] of them)
+    int chunk;               // particles per work item (kChunkMin .. kChunk), fixed at the sort
     CellCode cc;
 };
 
@@ -148,6 +166,7 @@ struct Species {
     int *chunk_start = nullptr; // device [ntiles + 1]
     int *sparse_start = nullptr;  // device [ntiles + 1]: scan of the sparse-tile flags
     int *sparse_tiles = nullptr;  // device [ntiles]: the sparse tiles
+    int chunk = kChunk;           // particles per work item, chosen at each sort
     int64_t bound = 0;        // host upper bound of count[0]
     int64_t next_id = 0;
     double wmax = 0;          // largest |weight| ever held (sets the fixed-point current scale)
@@ -214,6 +233,13 @@ struct pic_ctx {
     int64_t step = 0, shifts = 0, m_last = -1;
     // bookkeeping
     int *err = nullptr;           // device error word
+    long long *dclock = nullptr;  // device step counter (equals step; advanced by a kernel per step)
+    // CUDA graph of whole sort periods (no moving window, no injection, tracing off)
+    int use_graphs = 1;
+    cudaGraphExec_t graph = nullptr;
+    int64_t graph_steps = 0;      // steps one replay advances
+    int64_t graph_kernels = 0;    // kernels one replay runs
+    const void *graph_key = nullptr;   // first species' particle array when captured (pointer parity)
     unsigned long long *nfall = nullptr;   // device counter of fallback deposits (tracing)
     int *work = nullptr;          // device work counters [2 * kMaxSpecies]
     double *red = nullptr;        // reduction partials

@@ -51,7 +51,8 @@ __global__ void k_sort_scatter(SpeciesDev sp, TileDev t, int n_keys, const int *
 
 // Work of a tile: chunks of kChunk particles for the shared-memory path, or, for a tile with
 // fewer than kSparse particles, one entry in the sparse list (global-memory path, a warp each).
-__global__ void k_tile_chunks(const int *start, int keys_per_tile, int ntiles, int *chunk_count, int *sparse_flag)
+__global__ void k_tile_chunks(const int *start, int keys_per_tile, int ntiles, int chunk, int *chunk_count,
+                              int *sparse_flag)
 {
     const int tl = blockIdx.x * blockDim.x + threadIdx.x;
     if (tl > ntiles) return;
@@ -62,7 +63,7 @@ __global__ void k_tile_chunks(const int *start, int keys_per_tile, int ntiles, i
     }
     const int cnt = start[(tl + 1) * keys_per_tile] - start[tl * keys_per_tile];
     const bool sparse = cnt > 0 && cnt < kSparse;
-    chunk_count[tl] = sparse ? 0 : (cnt + kChunk - 1) / kChunk;
+    chunk_count[tl] = sparse ? 0 : (cnt + chunk - 1) / chunk;
     sparse_flag[tl] = sparse ? 1 : 0;
 }
 
@@ -165,6 +166,9 @@ cudaError_t exclusive_scan(pic_ctx *c, int *data, int64_t n)
 cudaError_t launch_sort(pic_ctx *c, int si)
 {
     Species &s = c->sp[si];
+    // work items small enough that a small species still spreads over every SM (4 per SM)
+    s.chunk = kChunk;
+    while (s.chunk > kChunkMin && s.bound / s.chunk < 4 * (int64_t)c->num_sms) s.chunk /= 2;
     TileDev t = tile_dev(c, s);
     SpeciesDev sd = species_dev(c, s);
     const int n_keys = (int)c->n_keys;
@@ -177,7 +181,7 @@ cudaError_t launch_sort(pic_ctx *c, int si)
     k_sort_scatter<<<grid, 256, 0, c->stream>>>(sd, t, n_keys, s.cell_start, s.rank, s.pos2, s.mom2, s.id2);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_tile_chunks<<<(c->ntiles + 1 + 255) / 256, 256, 0, c->stream>>>(s.cell_start, t.tile_cells * 8, c->ntiles,
-                                                                       s.chunk_start, s.sparse_start);
+                                                                       s.chunk, s.chunk_start, s.sparse_start);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = exclusive_scan(c, s.chunk_start, c->ntiles + 1)) != cudaSuccess) return e;
     if ((e = exclusive_scan(c, s.sparse_start, c->ntiles + 1)) != cudaSuccess) return e;

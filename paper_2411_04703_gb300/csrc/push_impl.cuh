@@ -509,8 +509,9 @@ __device__ __forceinline__ long long wrap_node(const GridDev &g, int x, int y, i
 // shared region allows it; measured faster for the drifting ions despite a few spills).
 template <int ORDER, bool FROZEN, class Reg>
 __global__ void __launch_bounds__(kPushThreads, FROZEN ? 2 : 1)
-k_push(SpeciesDev sp, GridDev g, TileDev t, FieldsDev f, ExtDev ext, int *work, int *work_sparse, int *err, Reg reg)
+k_push(SpeciesDev sp, GridDev g, TileDev t, FieldsDev f, ExtDev ext0, int *work, int *work_sparse, int *err, Reg reg)
 {
+    const ExtDev ext = ext_at_clock(ext0);
     extern __shared__ float smem[];
     __shared__ int s_item, s_qn;
     __shared__ float s_js[3], s_jinv[3], s_dl[3];
@@ -522,7 +523,8 @@ k_push(SpeciesDev sp, GridDev g, TileDev t, FieldsDev f, ExtDev ext, int *work, 
     int *qb = sJhi + 3 * R3;                              // queue: local base index
     float *qd = reinterpret_cast<float *>(qb + kQueue);  // queue: o[3], d[3], w (SoA)
     const int n_total = sp.count[0], n_sorted = sp.count[1], n_tile_items = sp.count[2];
-    const int n_items = n_tile_items + (n_total - n_sorted + kChunk - 1) / kChunk;
+    const int chunk = t.chunk;
+    const int n_items = n_tile_items + (n_total - n_sorted + chunk - 1) / chunk;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
     for (;;) {
@@ -533,8 +535,8 @@ k_push(SpeciesDev sp, GridDev g, TileDev t, FieldsDev f, ExtDev ext, int *work, 
         if (item >= n_items) break;
 
         if (item >= n_tile_items) {
-            const int p_begin = n_sorted + (item - n_tile_items) * kChunk;
-            const int p_end = min(p_begin + kChunk, n_total);
+            const int p_begin = n_sorted + (item - n_tile_items) * chunk;
+            const int p_end = min(p_begin + chunk, n_total);
             for (int p = p_begin + threadIdx.x; p < p_end; p += blockDim.x)
                 step_global<ORDER, FROZEN>(sp, g, f, ext, err, p);
             continue;
@@ -546,8 +548,8 @@ k_push(SpeciesDev sp, GridDev g, TileDev t, FieldsDev f, ExtDev ext, int *work, 
         const int t0[3] = {tx * t.T[0], ty * t.T[1], tz * t.T[2]};
         const int reg0[3] = {t0[0] - t.M - t.hl, t0[1] - t.M - t.hl, t0[2] - t.M - t.hl};
         const int key0 = tile * t.tile_cells * 8;
-        const int p_begin = t.cell_start[key0] + wi.y * kChunk;
-        const int p_end = min(p_begin + kChunk, t.cell_start[key0 + t.tile_cells * 8]);
+        const int p_begin = t.cell_start[key0] + wi.y * chunk;
+        const int p_end = min(p_begin + chunk, t.cell_start[key0 + t.tile_cells * 8]);
         // Region of the tile: nodes reg0 + (0..R-1) per dim (plane pitch padded).
         const int R2 = reg.r2(), Ry = reg.ry(), Rz = R3 / R2;
         const int zb = g.nzr == g.n[2] ? 0 : zblock(t0[2], g.nzr);   // the tile's run (tiles never straddle runs)
@@ -741,11 +743,19 @@ cudaError_t launch_t(pic_ctx *c, int si, const ExtDev &ext, Reg reg, int R3)
     const size_t smem = (size_t)(FROZEN ? 0 : 6) * R3 * sizeof(float) + (size_t)3 * R3 * 2 * sizeof(int) +
                         (size_t)kQueue * 8 * sizeof(float);
     auto kern = k_push<ORDER, FROZEN, Reg>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPushThreads, smem);
-    if (e != cudaSuccess) return e;
+    // attribute and occupancy once per kernel and region size (nothing but launches is then issued
+    // while a step sequence is captured into a CUDA graph)
+    static size_t smem_set = 0;
+    static int per_sm = 0, dev_set = -1;
+    cudaError_t e = cudaSuccess;
+    if (smem_set != smem || dev_set != c->dev.device) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPushThreads, smem);
+        if (e != cudaSuccess) return e;
+        smem_set = smem;
+        dev_set = c->dev.device;
+    }
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     FieldsDev f{c->E, c->B, c->J};
     kern<<<c->num_sms * per_sm, kPushThreads, smem, c->stream>>>(species_dev(c, s), grid_dev(c), t, f, ext,

@@ -125,17 +125,22 @@ def test_ensemble_whole_run_tracks_oracle_per_run():
 
 def test_autotuner_picks_a_cadence_and_keeps_physics():
     # the trials are real steps: the run advances by their total and still tracks a twin context
-    # that steps the same number of times with the default cadence
+    # that steps the same number of times with the default cadence (ensemble diagnostics per run
+    # within 1e-3, the long-run tolerance)
     e = W.mini_ensemble()
     sim, ids = api.from_ensemble(e)
     twin, tids = api.from_ensemble(e)
     se = sim.autotune(8)
     assert se in (1, 2, 3, 4, 6, 8)
     n = sim.get_time()[0]
-    assert n >= 6 * 8
+    assert n >= 2 * 6 * 32
     twin.step(n)
     sim.sync()
     twin.sync()
-    for c in range(6):
-        # ~80 steps of two FP32 runs whose reductions differ in order (another sort cadence)
-        assert parity.rel_err(sim.get_field(c).astype(np.float64), twin.get_field(c).astype(np.float64)) < 1e-3
+    for r in range(e.runs):
+        for frame in (api.PIC_FRAME_BOOSTED, api.PIC_FRAME_LAB):
+            ma = sim.get_moments_run(ids["beam"], r, frame, k_bunch=1.0)
+            mb = twin.get_moments_run(tids["beam"], r, frame, k_bunch=1.0)
+            assert ma["count"] == mb["count"]
+            for key in ("mean_gamma", "rel_energy_spread", "emit_nx", "emit_ny", "rms_z", "field_energy"):
+                assert ma[key] == pytest.approx(mb[key], rel=1e-3), (r, frame, key)
