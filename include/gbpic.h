@@ -328,6 +328,38 @@ int pic_trace_read(pic_ctx *ctx, pic_trace *out);
 int pic_tile_sort_noalloc(const int32_t *cells, int64_t n, const int grid[3], const int tile[3],
                           int32_t *order, int32_t *key_start, void *stream);
 
+/* Adjoint (reverse-mode gradient) of a beam diagnostic with respect to the undulator K and the
+ * plasma density profile, by a hand-written discrete adjoint of the step: the field update's
+ * transpose runs time-reversed (the transpose of the forward-difference curl is the
+ * backward-difference curl), the deposit's transpose gathers the adjoint current, the gather's
+ * transpose scatters into the field adjoints, and Boris and the move are reversed per particle
+ * from the recorded state.  Memory is traded for recomputation: pic_checkpoint(every_k) saves the
+ * state at the start of the differentiated interval and every every_k steps after (pic_step then
+ * also sorts at those steps); pic_backward restores each checkpoint in reverse order, recomputes
+ * its segment recording every step, and runs the segment's adjoint.  Requirements: first-order
+ * shape, one run, periodic grid, no moving window or PML, undulator without entrance ramp.
+ * every_k <= 0 turns recording off and frees the checkpoints. */
+int pic_checkpoint(pic_ctx *ctx, int every_k);
+
+/* Loss: the bunching factor of species_id in the boosted frame at the current step,
+ * L = |sum w exp(-i k z')| / sum w (k = k_bunch, z' including window shifts).  The initial state
+ * of the interval is held fixed: dL/dK is through the undulator field seen during the steps (a
+ * beam loaded matched to the undulator keeps its loaded momenta), dL/dprofile through the
+ * weights of the plasma electrons and the frozen ions, w = gamma_R n_lab(z_lab) dV / ppc with
+ * n_lab piecewise linear through the profile nodes (Eq. Nnormi).  The context is left at the
+ * state it had before the call.  Synchronous. */
+typedef struct {
+    int species_id;
+    double k_bunch;
+} pic_adjoint_seed;
+typedef struct {
+    double loss;
+    double dL_dK;
+    int n_profile;               /* profile nodes given to pic_set_plasma (0 without plasma) */
+    double dL_dprofile[64];
+} pic_grads;
+int pic_backward(pic_ctx *ctx, const pic_adjoint_seed *seed, pic_grads *out);
+
 /* Release every device allocation of the context.  NULL is accepted. */
 int pic_destroy(pic_ctx *ctx);
 

@@ -82,6 +82,15 @@ class pic_trace(C.Structure):
 TRACE_CLASSES = ["sort", "push", "push_frozen", "fields", "window", "inject", "other", "unused"]
 
 
+class pic_adjoint_seed(C.Structure):
+    _fields_ = [("species_id", C.c_int), ("k_bunch", C.c_double)]
+
+
+class pic_grads(C.Structure):
+    _fields_ = [("loss", C.c_double), ("dL_dK", C.c_double), ("n_profile", C.c_int),
+                ("dL_dprofile", C.c_double * 64)]
+
+
 class pic_moments(C.Structure):
     _fields_ = [("v", C.c_double * 20)]
 
@@ -115,6 +124,8 @@ def lib(build_if_missing: bool = True):
             "pic_get_moments_run": [vp, i, i, i, d, P(pic_moments)],
             "pic_autotune": [vp, i, P(i)],
             "pic_use_graphs": [vp, i],
+            "pic_checkpoint": [vp, i],
+            "pic_backward": [vp, P(pic_adjoint_seed), P(pic_grads)],
             "pic_set_tuning": [vp, P(pic_tuning)],
             "pic_load_species": [vp, P(pic_species), i64, vp, vp, vp, i, P(i)],
             "pic_set_external_field": [vp, P(pic_external)],
@@ -321,6 +332,18 @@ class Sim:
     # ------------------------------------------------------------------ stepping
     def step(self, n=1):
         self._check(self.L.pic_step(self.h, int(n)))
+
+    def checkpoint(self, every_k):
+        """Start recording for the adjoint: checkpoints now and every every_k steps."""
+        self._check(self.L.pic_checkpoint(self.h, int(every_k)))
+
+    def backward(self, species_id, k_bunch):
+        """Gradient of the boosted-frame bunching factor of a species at the current step with
+        respect to K and the plasma profile nodes: {loss, dL_dK, dL_dprofile}."""
+        seed = pic_adjoint_seed(int(species_id), float(k_bunch))
+        g = pic_grads()
+        self._check(self.L.pic_backward(self.h, C.byref(seed), C.byref(g)))
+        return {"loss": g.loss, "dL_dK": g.dL_dK, "dL_dprofile": np.array(g.dL_dprofile[:g.n_profile])}
 
     def use_graphs(self, on=True):
         """Replay captured step sequences (CUDA graphs) where the step allows it."""

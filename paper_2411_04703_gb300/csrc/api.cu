@@ -840,14 +840,27 @@ namespace {
 
 __global__ void k_tick(long long *clock) { *clock += 1; }
 
+int save_state(pic_ctx *c, StateSnap &st, bool alloc);
+int ad_checkpoint_due(pic_ctx *c);
+
 // One step of the method (the body of pic_step).
 int step_once(pic_ctx *c)
 {
     int r;
-    if ((c->step - c->sort_base) % c->sort_every == 0) {
+    if ((r = ad_checkpoint_due(c))) return r;
+    // the adjoint records sort at every checkpoint, so a recomputed segment repeats its sorts
+    const bool ad_sort = c->ad_on && (c->step - c->ad_step0) % c->ad_every == 0;
+    const bool sorted = ad_sort || (c->step - c->sort_base) % c->sort_every == 0;
+    if (sorted) {
         TraceScope ts(c, TR_SORT);
         for (int si = 0; si < c->nsp; si++)
             if (!c->sp[si].lattice) CK(launch_sort(c, si));
+    }
+    if (c->ad_rec_n >= 0) {
+        if (c->ad_rec_n >= (int)c->ad_rec.size()) return fail(c, PIC_ERR_STATE, "adjoint record overflow");
+        StateSnap &st = c->ad_rec[c->ad_rec_n++];
+        if ((r = save_state(c, st, false))) return r;
+        st.sorted = sorted;
     }
     // the lattice species writes J_z whole, before the other species add to it
     const bool lat = c->plasma && c->sp[c->sp_i].lattice;
@@ -891,7 +904,7 @@ int step_once(pic_ctx *c)
 // changes between periods: no moving window, no plasma injection (periodic z), tracing off.
 bool graph_eligible(const pic_ctx *c)
 {
-    if (!c->use_graphs || c->moving || c->trace_on || c->nsp == 0) return false;
+    if (!c->use_graphs || c->moving || c->trace_on || c->nsp == 0 || c->ad_on) return false;
     if (c->plasma && c->bc[2][0] != PIC_BC_PERIODIC) return false;
     return true;
 }
@@ -909,6 +922,109 @@ const void *pointer_key(const pic_ctx *c)
     for (int si = 0; si < c->nsp; si++)
         if (!c->sp[si].lattice) return c->sp[si].pos;
     return nullptr;
+}
+
+// ------------------------------------------------------------------ adjoint state
+
+void free_state(pic_ctx *c, StateSnap &st)
+{
+    dfree(c, st.E);
+    dfree(c, st.B);
+    for (auto &q : st.sp) {
+        dfree(c, q.pos);
+        dfree(c, q.mom);
+        dfree(c, q.id);
+        dfree(c, q.planes);
+    }
+    st = StateSnap();
+}
+
+// Copy the run's state (fields E, B; every species' records, counts, displacement bounds and
+// lattice planes) into st, allocating its buffers first when alloc (or when st is empty).
+int save_state(pic_ctx *c, StateSnap &st, bool alloc)
+{
+    const size_t f3 = sizeof(float) * 3 * (size_t)c->ncell;
+    if (alloc || !st.E) {
+        free_state(c, st);
+        st.E = static_cast<float *>(dalloc(c, f3));
+        st.B = static_cast<float *>(dalloc(c, f3));
+        if (!st.E || !st.B) return fail(c, PIC_ERR_ALLOC, "adjoint state allocation failed");
+        st.sp.assign(c->nsp, SpeciesSnap());
+        for (int si = 0; si < c->nsp; si++) {
+            const Species &s = c->sp[si];
+            SpeciesSnap &q = st.sp[si];
+            if (s.lattice) {
+                q.planes = static_cast<PlaneRec *>(dalloc(c, sizeof(PlaneRec) * s.plane_cap));
+                if (!q.planes) return fail(c, PIC_ERR_ALLOC, "adjoint state allocation failed");
+                continue;
+            }
+            q.pos = static_cast<float4 *>(dalloc(c, sizeof(float4) * s.cap));
+            q.mom = static_cast<float4 *>(dalloc(c, sizeof(float4) * s.cap));
+            q.id = static_cast<int *>(dalloc(c, sizeof(int) * s.cap));
+            if (!q.pos || !q.mom || !q.id) return fail(c, PIC_ERR_ALLOC, "adjoint state allocation failed");
+        }
+    }
+    st.step = c->step;
+    CK(cudaMemcpyAsync(st.E, c->E, f3, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(st.B, c->B, f3, cudaMemcpyDeviceToDevice, c->stream));
+    for (int si = 0; si < c->nsp; si++) {
+        const Species &s = c->sp[si];
+        SpeciesSnap &q = st.sp[si];
+        if (s.lattice) {
+            CK(cudaMemcpyAsync(q.planes, s.planes, sizeof(PlaneRec) * s.plane_cap, cudaMemcpyDeviceToDevice, c->stream));
+            continue;
+        }
+        // the host bound of the slots in use sizes the copy (no injection in the differentiated
+        // runs); q.n becomes the device count once the copies are done
+        const size_t nb = (size_t)std::min<int64_t>(s.bound, s.cap);
+        CK(cudaMemcpyAsync(q.count, s.count, sizeof(int) * 4, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaMemcpyAsync(q.dlim, s.dlim, sizeof(float) * 4, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaMemcpyAsync(q.pos, s.pos, sizeof(float4) * nb, cudaMemcpyDeviceToDevice, c->stream));
+        CK(cudaMemcpyAsync(q.mom, s.mom, sizeof(float4) * nb, cudaMemcpyDeviceToDevice, c->stream));
+        CK(cudaMemcpyAsync(q.id, s.id, sizeof(int) * nb, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    for (int si = 0; si < c->nsp; si++)
+        if (!c->sp[si].lattice) st.sp[si].n = st.sp[si].count[0];
+    return PIC_OK;
+}
+
+int restore_state(pic_ctx *c, const StateSnap &st)
+{
+    const size_t f3 = sizeof(float) * 3 * (size_t)c->ncell;
+    CK(cudaMemcpyAsync(c->E, st.E, f3, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->B, st.B, f3, cudaMemcpyDeviceToDevice, c->stream));
+    for (int si = 0; si < c->nsp; si++) {
+        Species &s = c->sp[si];
+        const SpeciesSnap &q = st.sp[si];
+        if (s.lattice) {
+            CK(cudaMemcpyAsync(s.planes, q.planes, sizeof(PlaneRec) * s.plane_cap, cudaMemcpyDeviceToDevice, c->stream));
+            continue;
+        }
+        CK(cudaMemcpyAsync(s.pos, q.pos, sizeof(float4) * q.n, cudaMemcpyDeviceToDevice, c->stream));
+        CK(cudaMemcpyAsync(s.mom, q.mom, sizeof(float4) * q.n, cudaMemcpyDeviceToDevice, c->stream));
+        CK(cudaMemcpyAsync(s.id, q.id, sizeof(int) * q.n, cudaMemcpyDeviceToDevice, c->stream));
+        CK(cudaMemcpyAsync(s.count, q.count, sizeof(int) * 4, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(s.dlim, q.dlim, sizeof(float) * 4, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemsetAsync(s.dmax, 0, sizeof(unsigned) * 4, c->stream));
+    }
+    const long long clk = st.step;
+    CK(cudaMemcpyAsync(c->dclock, &clk, sizeof(clk), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->step = st.step;
+    return PIC_OK;
+}
+
+// While recording for the adjoint, a checkpoint is saved at the start of every ad_every-th step.
+int ad_checkpoint_due(pic_ctx *c)
+{
+    if (!c->ad_on || c->ad_rec_n >= 0) return PIC_OK;
+    const int64_t rel = c->step - c->ad_step0;
+    if (rel < 0 || rel % c->ad_every) return PIC_OK;
+    const size_t j = (size_t)(rel / c->ad_every);
+    if (j < c->ad_ckpt.size()) return PIC_OK;
+    c->ad_ckpt.emplace_back();
+    return save_state(c, c->ad_ckpt.back(), true);
 }
 
 // Captures `period` steps (two sort periods: every sort swaps the particle buffers, so after two
@@ -1259,6 +1375,172 @@ int pic_trace_read(pic_ctx *c, pic_trace *out)
     CK(cudaStreamSynchronize(c->stream));
     out->fallback = (int64_t)nf;
     return PIC_OK;
+}
+
+int pic_checkpoint(pic_ctx *c, int every_k)
+{
+    int r = check_ctx(c);
+    if (r) return r;
+    for (auto &st : c->ad_ckpt) free_state(c, st);
+    for (auto &st : c->ad_rec) free_state(c, st);
+    c->ad_ckpt.clear();
+    c->ad_rec.clear();
+    c->ad_rec_n = -1;
+    c->ad_on = 0;
+    if (every_k <= 0) return PIC_OK;
+    if (c->order != 1) return fail(c, PIC_ERR_ARG, "the adjoint is built for the first-order shape");
+    if (c->runs != 1 || c->moving || c->pml) return fail(c, PIC_ERR_ARG, "the adjoint needs one run, no window, no PML");
+    for (int d = 0; d < 3; d++)
+        if (c->bc[d][0] != PIC_BC_PERIODIC) return fail(c, PIC_ERR_ARG, "the adjoint needs a periodic grid");
+    if (c->ext_type && std::isfinite(c->z_start) && c->ramp >= 0.0)
+        return fail(c, PIC_ERR_ARG, "the adjoint needs an undulator without entrance ramp");
+    drop_graph(c);
+    c->ad_on = 1;
+    c->ad_every = every_k;
+    c->ad_step0 = c->step;
+    return PIC_OK;
+}
+
+int pic_backward(pic_ctx *c, const pic_adjoint_seed *seed, pic_grads *out)
+{
+    int r = check_ctx(c);
+    if (r) return r;
+    if (!seed || !out) return fail(c, PIC_ERR_ARG, "seed and out are required");
+    if (!c->ad_on || c->ad_ckpt.empty()) return fail(c, PIC_ERR_STATE, "call pic_checkpoint before stepping");
+    const int sid = seed->species_id;
+    if (sid < 0 || sid >= c->nsp || c->sp[sid].lattice) return fail(c, PIC_ERR_ARG, "bad seed species");
+    if (c->plasma && c->nprof > (int)(sizeof(out->dL_dprofile) / sizeof(double)))
+        return fail(c, PIC_ERR_ARG, "profile has more nodes than pic_grads holds");
+    CK(cudaStreamSynchronize(c->stream));
+    const int64_t N = c->step, S0 = c->ad_step0, K = c->ad_every;
+    std::memset(out, 0, sizeof(*out));
+    // buffers
+    const size_t f3 = 3 * (size_t)c->ncell;
+    float *lE = nullptr, *lB = nullptr, *lJ = nullptr;
+    double *lK = nullptr, *R = nullptr, *sums = nullptr, *grad = nullptr, *lw_plane = nullptr;
+    std::vector<float4 *> lx(c->nsp, nullptr), lu(c->nsp, nullptr), lx2(c->nsp, nullptr), lu2(c->nsp, nullptr);
+    std::vector<double *> lw(c->nsp, nullptr);
+    int *inv = nullptr;
+    int64_t max_ids = 1;
+    for (int si = 0; si < c->nsp; si++) max_ids = std::max<int64_t>(max_ids, c->sp[si].next_id);
+    if ((r = alloc_zero(c, &lE, f3)) || (r = alloc_zero(c, &lB, f3)) || (r = alloc_zero(c, &lJ, f3)) ||
+        (r = alloc_zero(c, &lK, 1)) || (r = alloc_zero(c, &R, (size_t)c->n[2])) || (r = alloc_zero(c, &sums, 3)) ||
+        (r = alloc_zero(c, &grad, 64)) || (r = alloc_zero(c, &inv, (size_t)max_ids)))
+        return r;
+    if (c->plasma && (r = alloc_zero(c, &lw_plane, (size_t)c->sp[c->sp_i].plane_cap))) return r;
+    for (int si = 0; si < c->nsp; si++) {
+        const Species &s = c->sp[si];
+        if (s.lattice) continue;
+        if ((r = alloc_zero(c, &lx[si], (size_t)s.cap)) || (r = alloc_zero(c, &lu[si], (size_t)s.cap)) ||
+            (r = alloc_zero(c, &lx2[si], (size_t)s.cap)) || (r = alloc_zero(c, &lu2[si], (size_t)s.cap)) ||
+            (r = alloc_zero(c, &lw[si], (size_t)std::max<int64_t>(s.next_id, 1))))
+            return r;
+    }
+    // the final state, restored at the end
+    StateSnap fin;
+    if ((r = save_state(c, fin, true))) return r;
+    // records for one segment
+    if ((int64_t)c->ad_rec.size() < K) c->ad_rec.resize((size_t)K);
+    const int nseg = (int)((N - S0 + K - 1) / K);
+    for (int j = nseg - 1; j >= 0 && r == PIC_OK; j--) {
+        const int64_t s0 = S0 + (int64_t)j * K, e0 = std::min(N, s0 + K);
+        if ((size_t)j >= c->ad_ckpt.size()) { r = fail(c, PIC_ERR_STATE, "missing adjoint checkpoint"); break; }
+        if ((r = restore_state(c, c->ad_ckpt[(size_t)j]))) break;
+        c->ad_rec_n = 0;
+        for (int64_t n = s0; n < e0 && r == PIC_OK; n++) r = step_once(c);
+        c->ad_rec_n = -1;
+        if (r) break;
+        // The recomputed segment ends in the state the next checkpoint (or the final state) holds,
+        // but the sort's order among particles is not reproducible: the adjoints carried over are
+        // indexed in that checkpoint's order and are moved to the order the recomputed run has.
+        const StateSnap &last = c->ad_rec[(size_t)(e0 - 1 - s0)];
+        if (j == nseg - 1) {
+            double h3[3] = {0, 0, 0};   // seed: the loss's gradient on the final positions
+            CK(adj_bunch_seed(c, c->sp[sid], seed->k_bunch, sums, h3, lx[sid]));
+            const double rr = std::sqrt(h3[0] * h3[0] + h3[1] * h3[1]);
+            out->loss = h3[2] > 0 ? rr / h3[2] : 0.0;
+        } else {
+            const StateSnap &next = c->ad_ckpt[(size_t)j + 1];
+            for (int si = 0; si < c->nsp && r == PIC_OK; si++) {
+                if (c->sp[si].lattice) continue;
+                const cudaError_t e = adj_remap(c, c->sp[si].id, last.sp[si].n, next.sp[si].id, next.sp[si].n, inv, lx[si],
+                                                lu[si], lx2[si], lu2[si]);
+                if (e != cudaSuccess) { r = fail_cuda(c, e, "adjoint remap"); break; }
+                std::swap(lx[si], lx2[si]);
+                std::swap(lu[si], lu2[si]);
+            }
+            if (r) break;
+        }
+        for (int64_t n = e0 - 1; n >= s0 && r == PIC_OK; n--) {
+            const StateSnap &rec = c->ad_rec[(size_t)(n - s0)];
+            if ((r = adj_fields(c, lE, lB, lJ) ? fail_cuda(c, cudaGetLastError(), "adjoint fields") : PIC_OK)) break;
+            c->step = n;                 // the external field of step n
+            ExtDev ext = ext_step(c);
+            ext.clock = nullptr;
+            for (int si = 0; si < c->nsp && r == PIC_OK; si++) {
+                const Species &s = c->sp[si];
+                if (s.lattice) {
+                    const cudaError_t e = adj_ions(c, s, rec.sp[si].planes, lJ, R, lw_plane);
+                    if (e != cudaSuccess) r = fail_cuda(c, e, "adjoint ions");
+                    continue;
+                }
+                Species view = s;
+                view.pos = rec.sp[si].pos;
+                view.mom = rec.sp[si].mom;
+                view.id = rec.sp[si].id;
+                const cudaError_t e = adj_particles(c, view, rec.E, rec.B, lJ, lE, lB, lx[si], lu[si], lw[si], lK, ext,
+                                                    rec.sp[si].n);
+                if (e != cudaSuccess) r = fail_cuda(c, e, "adjoint particles");
+            }
+            if (r) break;
+            if (rec.sorted) {
+                // back to the order before the step's sort (the previous step's, or the checkpoint's)
+                const StateSnap &before = n > s0 ? c->ad_rec[(size_t)(n - s0 - 1)] : c->ad_ckpt[(size_t)j];
+                for (int si = 0; si < c->nsp && r == PIC_OK; si++) {
+                    if (c->sp[si].lattice) continue;
+                    // slots of particles the sort dropped (dummies) keep a zero adjoint
+                    const cudaError_t e = adj_remap(c, before.sp[si].id, before.sp[si].n, rec.sp[si].id, rec.sp[si].n,
+                                                    inv, lx[si], lu[si], lx2[si], lu2[si]);
+                    if (e != cudaSuccess) { r = fail_cuda(c, e, "adjoint remap"); break; }
+                    std::swap(lx[si], lx2[si]);
+                    std::swap(lu[si], lu2[si]);
+                }
+            }
+        }
+    }
+    c->step = N;
+    if (r == PIC_OK && c->plasma) {
+        const cudaError_t e = adj_profile_grad(c, lw[c->sp_e], c->sp[c->sp_e].next_id, lw_plane, grad);
+        if (e != cudaSuccess) r = fail_cuda(c, e, "profile gradient");
+    }
+    if (r == PIC_OK) {
+        double gk = 0.0, gp[64];
+        CK(cudaMemcpyAsync(&gk, lK, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaMemcpyAsync(gp, grad, sizeof(double) * 64, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        out->dL_dK = gk;
+        out->n_profile = c->plasma ? c->nprof : 0;
+        for (int q = 0; q < out->n_profile; q++) out->dL_dprofile[q] = gp[q];
+        r = restore_state(c, fin);
+    }
+    free_state(c, fin);
+    for (int si = 0; si < c->nsp; si++) {
+        dfree(c, lx[si]);
+        dfree(c, lu[si]);
+        dfree(c, lx2[si]);
+        dfree(c, lu2[si]);
+        dfree(c, lw[si]);
+    }
+    dfree(c, lE);
+    dfree(c, lB);
+    dfree(c, lJ);
+    dfree(c, lK);
+    dfree(c, R);
+    dfree(c, sums);
+    dfree(c, grad);
+    dfree(c, inv);
+    dfree(c, lw_plane);
+    return r;
 }
 
 int pic_destroy(pic_ctx *c)

@@ -182,6 +182,22 @@ struct Species {
     double *zacc = nullptr;      // device [n2]: J_z per unit transverse weight, one step
 };
 
+// Saved state of the run (a checkpoint of the adjoint, or one recorded step of a segment).
+struct SpeciesSnap {
+    float4 *pos = nullptr, *mom = nullptr;
+    int *id = nullptr;
+    int n = 0;                 // slots in use
+    int count[4] = {0, 0, 0, 0};
+    float dlim[4] = {0, 0, 0, 0};
+    PlaneRec *planes = nullptr;   // lattice species
+};
+struct StateSnap {
+    int64_t step = 0;
+    bool sorted = false;       // recorded step: the step began with a sort
+    float *E = nullptr, *B = nullptr;
+    std::vector<SpeciesSnap> sp;
+};
+
 }  // namespace gbpic
 
 struct pic_ctx {
@@ -240,6 +256,13 @@ struct pic_ctx {
     int64_t graph_steps = 0;      // steps one replay advances
     int64_t graph_kernels = 0;    // kernels one replay runs
     const void *graph_key = nullptr;   // first species' particle array when captured (pointer parity)
+    // adjoint: checkpoints every ad_every steps from ad_step0; while a segment is recomputed,
+    // every step's post-sort state is recorded into ad_rec[ad_rec_n++]
+    int ad_on = 0, ad_every = 0;
+    int64_t ad_step0 = 0;
+    std::vector<gbpic::StateSnap> ad_ckpt;
+    std::vector<gbpic::StateSnap> ad_rec;
+    int ad_rec_n = -1;         // < 0: not recording
     unsigned long long *nfall = nullptr;   // device counter of fallback deposits (tracing)
     int *work = nullptr;          // device work counters [2 * kMaxSpecies]
     double *red = nullptr;        // reduction partials
@@ -294,5 +317,14 @@ cudaError_t launch_moments(pic_ctx *c, const Species &s, int frame, double k, do
 cudaError_t species_wmax(pic_ctx *c, int si, double *out);
 cudaError_t species_count_live(pic_ctx *c, const Species &s, int64_t *out);
 cudaError_t absmax_f64(pic_ctx *c, const double *a, int64_t n, double *out);
+// k_adjoint.cu
+cudaError_t adj_fields(pic_ctx *c, float *lE, float *lB, float *lJ);
+cudaError_t adj_particles(pic_ctx *c, const Species &rec, const float *E, const float *B, const float *lJ, float *lE,
+                          float *lB, float4 *lx, float4 *lu, double *lw, double *lK, const ExtDev &ext, int n);
+cudaError_t adj_ions(pic_ctx *c, const Species &s, const PlaneRec *planes, const float *lJ, double *R, double *lw_plane);
+cudaError_t adj_bunch_seed(pic_ctx *c, const Species &s, double k, double *sums_dev, double *host3, float4 *lx);
+cudaError_t adj_remap(pic_ctx *c, const int *id_before, int n_before, const int *id_after, int n_after, int *inv,
+                      const float4 *lx, const float4 *lu, float4 *lx_out, float4 *lu_out);
+cudaError_t adj_profile_grad(pic_ctx *c, const double *lw_e, long long n_ids, const double *lw_plane, double *grad);
 
 }  // namespace gbpic

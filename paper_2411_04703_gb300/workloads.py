@@ -284,6 +284,31 @@ def ensemble_run(e: Ensemble, r: int) -> Workload:
     return w
 
 
+def adjoint_workload(grid=(64, 64, 256), n_beam=2097152, steps=1000, seed=5, n_nodes=32, ppc=(1, 2, 2),
+                     name="C5 adjoint 64x64x256, 2M beam + 4 ppc plasma, CIC") -> Workload:
+    """Differentiated run: the vacuum-undulator physics (boost 10, lab gamma 100 beam of 30 pC,
+    K = 1, lambda_u = 2 cm, 32 cells per RRF undulator period, first-order shape, periodic) with
+    a cold lab-static plasma of 4 particles per cell whose lab density is a piecewise-linear
+    profile of n_nodes nodes spread over the box's lab image (seeded values around n_n)."""
+    w = vacuum_undulator(grid=grid, n_beam=n_beam, steps=steps, seed=seed, order=1, name=name)
+    zl = w.gamma_R * grid[2] * w.d[2]
+    rng = np.random.Generator(np.random.Philox(key=seed))
+    zn = tuple(float(v) for v in np.linspace(0.0, zl, n_nodes))
+    dn = tuple(float(v) for v in 1.0 * (1.0 + 0.3 * rng.uniform(-1.0, 1.0, n_nodes)))
+    w.plasma = Plasma(ppc=ppc, xrange=(0, grid[0], 0, grid[1]), z_nodes=zn, n_nodes=dn)
+    w.beam.weight = beam_weight(30e-12, n_beam, C_LIGHT / w.length_unit_m)
+    return w
+
+
+def mini_adjoint(seed=15, steps=30):
+    """The oracle-sized reduction of the differentiated run: 16 x 16 x 32, 2000 beam electrons."""
+    w = adjoint_workload(grid=(16, 16, 32), n_beam=2000, steps=steps, seed=seed,
+                         name="mini adjoint 16x16x32")
+    w.beam.sigma_r = 2 * w.d[0]
+    w.beam.sigma_z = 4 * w.d[2] / 19.754
+    return w
+
+
 # ----------------------------------------------------------------------------- generators
 
 def sample_beam(w: Workload, n: Optional[int] = None, seed: Optional[int] = None):
