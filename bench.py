@@ -41,6 +41,10 @@ HBM_FALLBACK = 6800.0
 BYTES_PUSHED = 60.0
 BYTES_FROZEN = 36.0
 BYTES_CELL_PUSH = 36.0
+# DRAM bytes (read + write) per particle-kernel launch of the plasma buncher 128x128x512, averaged
+# over its two launches per step (plasma electrons 4.148 GB, beam 0.235 GB), from one ncu pass of
+# dram__bytes_read.sum and dram__bytes_write.sum on the full-size bench run of this kernel
+TRAFFIC_PUSH_BUNCHER = 0.5 * (2205063680 + 1943472384 + 154195968 + 80768512)
 
 
 def peaks():
@@ -224,6 +228,61 @@ def aggregate(psteps, ms, world, device="cpu"):
     return float(a[0]), float(b[0])
 
 
+def run_adjoint(args):
+    """Adjoint/forward cost on the differentiated run (64x64x256, 2M beam + 4 ppc plasma, CIC):
+    K forward steps recording checkpoints every 50, then pic_backward (segment recompute + the
+    adjoint sweep); the line's value is the forward's pushed particle-steps/s, and "adjoint" gives
+    the backward's time per step and the adjoint/forward ratio."""
+    import torch
+    from paper_2411_04703_gb300 import api, workloads as W
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    w = W.adjoint_workload(seed=5 + rank)
+    sim, ids = api.from_workload(w, device=local)
+    if args.warmup:
+        sim.step(args.warmup)
+    sim.sync()
+    n0 = sim.get_count(ids["beam"]) + sim.get_count(ids["plasma_e"])
+    sim.checkpoint(50)
+    stream = sim.stream
+    clocks = ClockSampler(local)
+    clocks.start()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(args.steps)
+    e1.record(stream)
+    sim.sync()
+    torch.cuda.synchronize()
+    fwd_ms = e0.elapsed_time(e1)
+    un = w.undulator
+    k_lab = api.resonant_wavenumber(un.lambda_u, un.K, w.beam.gamma)
+    bz = 1.0 - (1.0 + 0.5 * un.K ** 2) / (2.0 * w.beam.gamma ** 2)
+    k_rrf = k_lab * w.gamma_R * (1.0 - bz * math.sqrt(1.0 - 1.0 / w.gamma_R ** 2))
+    t0 = time.perf_counter()
+    g = sim.backward(ids["beam"], k_rrf)
+    torch.cuda.synchronize()
+    bwd_ms = 1000.0 * (time.perf_counter() - t0)
+    clk = clocks.stop()
+    value = n0 * args.steps / (fwd_ms / 1000.0)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": fwd_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "grid": list(w.grid), "beam": w.beam.n, "plasma_electrons": int(n0 - w.beam.n),
+                       "shape": "CIC", "boundaries": "periodic", "checkpoint_every": 50,
+                       "l2": "inputs larger than L2 (particle state ~0.5 GB, checkpoints and records ~15 GB)"},
+            "adjoint": {"forward_ms_per_step": fwd_ms / args.steps, "backward_ms_per_step": bwd_ms / args.steps,
+                        "ratio": bwd_ms / fwd_ms, "includes": "segment recompute with per-step records, adjoint sweep",
+                        "loss": g["loss"], "dL_dK": g["dL_dK"],
+                        "dL_dprofile_norm": float(sum(v * v for v in g["dL_dprofile"]) ** 0.5)},
+            "clocks": clk,
+        }
+        print(json.dumps(line))
+    return 0
+
+
 def run_gbpic(args):
     import torch
     import torch.distributed as dist
@@ -352,8 +411,9 @@ def run_gbpic(args):
         bytes_per = 3 * (n0 + frozen0) * 36.0
     avg_ms = classes[dom] / max(launches, 1)
     achieved = bytes_per / (avg_ms / 1000.0) / 1e9
+    traffic = TRAFFIC_PUSH_BUNCHER if (dom == "push" and args.workload == "buncher" and w.grid == (128, 128, 512)) else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": None,
+                "frac": achieved / hbm, "traffic": traffic,
                 "kernel": {"push": f"k_push<{shape}, mobile> (" + " + ".join(k for k in ("beam", "plasma_e") if k in ids) + ")",
                            "push_frozen": f"k_lattice / k_push<{shape}, frozen> (ions)", "fields": "k_fdtd_b/e",
                            "sort": "tile sort"}[dom],
@@ -455,7 +515,7 @@ def main():
     ap.add_argument("--autotune", action="store_true",
                     help="buncher: pick the sort cadence with the autotuner (its slow drift makes the "
                          "cadence matter little; the default keeps 8)")
-    ap.add_argument("--workload", choices=["buncher", "ensemble", "vacuum"], default="buncher",
+    ap.add_argument("--workload", choices=["buncher", "ensemble", "vacuum", "adjoint"], default="buncher",
                     help="buncher: the plasma buncher 128x128x512 (default); ensemble: the batched sweep "
                          "of 64 runs of 64x64x128 in one context")
     args = ap.parse_args()
@@ -463,6 +523,8 @@ def main():
         raise SystemExit("need --steps >= 1 and --warmup >= 0")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "adjoint":
+        return run_adjoint(args)
     return run_gbpic(args)
 
 

@@ -166,9 +166,10 @@ cudaError_t exclusive_scan(pic_ctx *c, int *data, int64_t n)
 cudaError_t launch_sort(pic_ctx *c, int si)
 {
     Species &s = c->sp[si];
-    // work items small enough that a small species still spreads over every SM (4 per SM)
+    // work items small enough that a small species still gives every SM one (each item stages a
+    // whole tile region, so items are kept as large as that allows)
     s.chunk = kChunk;
-    while (s.chunk > kChunkMin && s.bound / s.chunk < 4 * (int64_t)c->num_sms) s.chunk /= 2;
+    while (s.chunk > kChunkMin && s.bound / s.chunk < (int64_t)c->num_sms) s.chunk /= 2;
     TileDev t = tile_dev(c, s);
     SpeciesDev sd = species_dev(c, s);
     const int n_keys = (int)c->n_keys;

@@ -79,13 +79,17 @@ def test_ensemble_runs_are_independent_of_each_other():
         one, oids = api.from_workload(w)
         one.step(steps)
         one.sync()
+        gs = [sim.get_field(c)[r * nzr:(r + 1) * nzr].astype(np.float64) for c in range(9)]
+        ss = [one.get_field(c).astype(np.float64) for c in range(9)]
         for c in range(9):
-            g = sim.get_field(c)[r * nzr:(r + 1) * nzr].astype(np.float64)
-            s = one.get_field(c).astype(np.float64)
             # two FP32 runs that differ in the order of float atomics and in the fixed-point scale
             # of the current (the ensemble's bound spans every run) drift apart by rounding over
-            # 12 steps; a current or field leaking between runs would be O(1)
-            assert parity.rel_err(g, s) < TOL_MULTI, (r, c)
+            # 12 steps, measured against the largest component of the same field (a component
+            # that is nearly zero carries only that rounding); a current or field leaking between
+            # runs would be O(1)
+            grp = range(3 * (c // 3), 3 * (c // 3) + 3)
+            floor = max(float(np.max(np.abs(ss[q]))) for q in grp)
+            assert parity.rel_err_scaled(gs[c], ss[c], floor) < TOL_MULTI, (r, c)
         for name, keys in (("beam", ("mean_z", "rms_z", "mean_gamma", "emit_nx", "field_energy")),
                            ("plasma_e", ("mean_z", "rms_z", "mean_gamma"))):
             mr = sim.get_moments_run(ids[name], r, api.PIC_FRAME_BOOSTED, k_bunch=1.0)
