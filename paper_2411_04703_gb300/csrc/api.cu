@@ -840,7 +840,7 @@ namespace {
 
 __global__ void k_tick(long long *clock) { *clock += 1; }
 
-int save_state(pic_ctx *c, StateSnap &st, bool alloc);
+int save_state(pic_ctx *c, StateSnap &st, bool alloc, bool quick = false);
 int ad_checkpoint_due(pic_ctx *c);
 
 // One step of the method (the body of pic_step).
@@ -859,7 +859,8 @@ int step_once(pic_ctx *c)
     if (c->ad_rec_n >= 0) {
         if (c->ad_rec_n >= (int)c->ad_rec.size()) return fail(c, PIC_ERR_STATE, "adjoint record overflow");
         StateSnap &st = c->ad_rec[c->ad_rec_n++];
-        if ((r = save_state(c, st, false))) return r;
+        if (!st.E && (r = save_state(c, st, true))) return r;   // first use allocates (and syncs)
+        if ((r = save_state(c, st, false, true))) return r;
         st.sorted = sorted;
     }
     // the lattice species writes J_z whole, before the other species add to it
@@ -935,13 +936,16 @@ void free_state(pic_ctx *c, StateSnap &st)
         dfree(c, q.mom);
         dfree(c, q.id);
         dfree(c, q.planes);
+        dfree(c, q.dcount);
     }
     st = StateSnap();
 }
 
 // Copy the run's state (fields E, B; every species' records, counts, displacement bounds and
 // lattice planes) into st, allocating its buffers first when alloc (or when st is empty).
-int save_state(pic_ctx *c, StateSnap &st, bool alloc)
+// quick: a recorded step (no host synchronisation; counts stay on the device until
+// finish_records reads them).
+int save_state(pic_ctx *c, StateSnap &st, bool alloc, bool quick)
 {
     const size_t f3 = sizeof(float) * 3 * (size_t)c->ncell;
     if (alloc || !st.E) {
@@ -961,7 +965,8 @@ int save_state(pic_ctx *c, StateSnap &st, bool alloc)
             q.pos = static_cast<float4 *>(dalloc(c, sizeof(float4) * s.cap));
             q.mom = static_cast<float4 *>(dalloc(c, sizeof(float4) * s.cap));
             q.id = static_cast<int *>(dalloc(c, sizeof(int) * s.cap));
-            if (!q.pos || !q.mom || !q.id) return fail(c, PIC_ERR_ALLOC, "adjoint state allocation failed");
+            q.dcount = static_cast<int *>(dalloc(c, sizeof(int) * 4));
+            if (!q.pos || !q.mom || !q.id || !q.dcount) return fail(c, PIC_ERR_ALLOC, "adjoint state allocation failed");
         }
     }
     st.step = c->step;
@@ -977,15 +982,35 @@ int save_state(pic_ctx *c, StateSnap &st, bool alloc)
         // the host bound of the slots in use sizes the copy (no injection in the differentiated
         // runs); q.n becomes the device count once the copies are done
         const size_t nb = (size_t)std::min<int64_t>(s.bound, s.cap);
-        CK(cudaMemcpyAsync(q.count, s.count, sizeof(int) * 4, cudaMemcpyDeviceToHost, c->stream));
-        CK(cudaMemcpyAsync(q.dlim, s.dlim, sizeof(float) * 4, cudaMemcpyDeviceToHost, c->stream));
+        if (quick) {
+            CK(cudaMemcpyAsync(q.dcount, s.count, sizeof(int) * 4, cudaMemcpyDeviceToDevice, c->stream));
+        } else {
+            CK(cudaMemcpyAsync(q.count, s.count, sizeof(int) * 4, cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaMemcpyAsync(q.dlim, s.dlim, sizeof(float) * 4, cudaMemcpyDeviceToHost, c->stream));
+        }
         CK(cudaMemcpyAsync(q.pos, s.pos, sizeof(float4) * nb, cudaMemcpyDeviceToDevice, c->stream));
         CK(cudaMemcpyAsync(q.mom, s.mom, sizeof(float4) * nb, cudaMemcpyDeviceToDevice, c->stream));
         CK(cudaMemcpyAsync(q.id, s.id, sizeof(int) * nb, cudaMemcpyDeviceToDevice, c->stream));
     }
+    if (quick) return PIC_OK;
     CK(cudaStreamSynchronize(c->stream));
     for (int si = 0; si < c->nsp; si++)
         if (!c->sp[si].lattice) st.sp[si].n = st.sp[si].count[0];
+    return PIC_OK;
+}
+
+// After a segment is recomputed: the recorded steps' particle counts, read once.
+int finish_records(pic_ctx *c, int nrec)
+{
+    for (int k = 0; k < nrec; k++)
+        for (int si = 0; si < c->nsp; si++)
+            if (!c->sp[si].lattice)
+                CK(cudaMemcpyAsync(c->ad_rec[k].sp[si].count, c->ad_rec[k].sp[si].dcount, sizeof(int) * 4,
+                                   cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < nrec; k++)
+        for (int si = 0; si < c->nsp; si++)
+            if (!c->sp[si].lattice) c->ad_rec[k].sp[si].n = c->ad_rec[k].sp[si].count[0];
     return PIC_OK;
 }
 
@@ -1449,7 +1474,7 @@ int pic_backward(pic_ctx *c, const pic_adjoint_seed *seed, pic_grads *out)
         c->ad_rec_n = 0;
         for (int64_t n = s0; n < e0 && r == PIC_OK; n++) r = step_once(c);
         c->ad_rec_n = -1;
-        if (r) break;
+        if (r || (r = finish_records(c, (int)(e0 - s0)))) break;
         // The recomputed segment ends in the state the next checkpoint (or the final state) holds,
         // but the sort's order among particles is not reproducible: the adjoints carried over are
         // indexed in that checkpoint's order and are moved to the order the recomputed run has.

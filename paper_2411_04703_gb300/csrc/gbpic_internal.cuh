@@ -186,6 +186,7 @@ struct Species {
 struct SpeciesSnap {
     float4 *pos = nullptr, *mom = nullptr;
     int *id = nullptr;
+    int *dcount = nullptr;     // device copy of the species' count[4] (recorded steps)
     int n = 0;                 // slots in use
     int count[4] = {0, 0, 0, 0};
     float dlim[4] = {0, 0, 0, 0};
