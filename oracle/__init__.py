@@ -87,6 +87,8 @@ def lib():
                 "osim_gather_at": (None, [vp, pd, pd]),
                 "osim_moments": (None, [vp, i, i, d, pd]),
                 "oracle_boris": (None, [d, d, pd, pd, pd]),
+                "oracle_vay": (None, [d, d, pd, pd, pd]),
+                "osim_set_pusher": (None, [vp, i]),
                 "oracle_field_transform": (None, [pd, pd, d, pd, pd]),
                 "oracle_lab_to_boosted": (None, [d, pd, pd, pd, pd]),
                 "oracle_boosted_to_lab": (None, [d, pd, d, pd, pd, pd, pd]),
@@ -120,6 +122,13 @@ def _f64(a):
 
 
 # ----------------------------------------------------------------- single-step helpers
+
+def vay(qm: float, dt: float, E, B, u):
+    """One Vay push of momentum u (copied) in E, B; returns the new momentum."""
+    u = np.array(u, dtype=np.float64)
+    lib().oracle_vay(qm, dt, _pd(_f64(E)), _pd(_f64(B)), _pd(u))
+    return u
+
 
 def boris(qm: float, dt: float, E, B, u):
     u = _f64(u).copy()
@@ -275,6 +284,10 @@ class Sim:
 
     def step(self, n=1):
         self.L.osim_step(self.h, int(n))
+
+    def set_pusher(self, pusher):
+        """0: Boris (default), 1: Vay."""
+        self.L.osim_set_pusher(self.h, int(pusher))
 
     def fdtd(self):
         self.L.osim_fdtd(self.h)

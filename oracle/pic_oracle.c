@@ -73,6 +73,7 @@ typedef struct {
     int nsp;
     osp sp[O_MAXSP];
     long dropped; /* deposit contributions outside a non-periodic grid (should stay 0) */
+    int pusher;   /* 0: Boris, 1: Vay */
 } osim;
 
 /* ------------------------------------------------------------------ shapes */
@@ -307,6 +308,8 @@ void osim_set_external(void *h, int type, double K, double lambda_u, double phas
     s->z_start = z_start;
     s->ramp = ramp;
 }
+
+void osim_set_pusher(void *h, int pusher) { ((osim *)h)->pusher = pusher; }
 
 void osim_external_at(void *h, double zp, double tp, double *E, double *B)
 {
@@ -598,6 +601,31 @@ void oracle_boris(double qm, double dt, const double E[3], const double B[3], do
     u[2] = upl[2] + h * E[2];
 }
 
+/* Vay's leap-frog push (the modified pusher the paper cites for boosted-frame runs, Sec. 1):
+ * a half step with the old velocity, u_h = u + h (E + v x B); u' = u_h + h E; then the
+ * new Lorentz factor solves gamma^2 = (sigma + sqrt(sigma^2 + 4 (tau^2 + (u'.tau)^2))) / 2 with
+ * tau = h B, sigma = gamma'^2 - tau^2, and u+ = s (u' + (u'.t) t + u' x t), t = tau / gamma,
+ * s = 1 / (1 + t^2); h = qm dt / 2.  It keeps E + v x B = 0 drifts exact. */
+void oracle_vay(double qm, double dt, const double E[3], const double B[3], double u[3])
+{
+    double h = 0.5 * qm * dt;
+    double g = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    double v[3] = {u[0] / g, u[1] / g, u[2] / g};
+    double vxb[3] = {v[1] * B[2] - v[2] * B[1], v[2] * B[0] - v[0] * B[2], v[0] * B[1] - v[1] * B[0]};
+    double up[3];
+    for (int c = 0; c < 3; c++) up[c] = u[c] + h * (E[c] + vxb[c]) + h * E[c];
+    double tau[3] = {h * B[0], h * B[1], h * B[2]};
+    double tau2 = tau[0] * tau[0] + tau[1] * tau[1] + tau[2] * tau[2];
+    double ust = up[0] * tau[0] + up[1] * tau[1] + up[2] * tau[2];
+    double sigma = 1.0 + up[0] * up[0] + up[1] * up[1] + up[2] * up[2] - tau2;
+    double g1 = sqrt(0.5 * (sigma + sqrt(sigma * sigma + 4.0 * (tau2 + ust * ust))));
+    double t[3] = {tau[0] / g1, tau[1] / g1, tau[2] / g1};
+    double s = 1.0 / (1.0 + t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+    double ut = up[0] * t[0] + up[1] * t[1] + up[2] * t[2];
+    double uxt[3] = {up[1] * t[2] - up[2] * t[1], up[2] * t[0] - up[0] * t[2], up[0] * t[1] - up[1] * t[0]};
+    for (int c = 0; c < 3; c++) u[c] = s * (up[c] + ut * t[c] + uxt[c]);
+}
+
 /* Interpolate grid component f, whose nodes sit at index + stag (cells), to X with the
  * particle shape (same weighting as the deposit). */
 static double o_gather(const osim *s, const double *f, const double stag[3], const double X[3])
@@ -709,7 +737,8 @@ static void o_push_species(osim *s, osp *p)
             }
             o_external(s, (X[2] + (double)s->shifts) * s->d[2], tp, Ee, Be);
             for (int c = 0; c < 3; c++) { E[c] += Ee[c]; B[c] += Be[c]; }
-            oracle_boris(qm, s->dt, E, B, U);
+            if (s->pusher == 1) oracle_vay(qm, s->dt, E, B, U);
+            else oracle_boris(qm, s->dt, E, B, U);
         }
         double g = sqrt(1.0 + U[0] * U[0] + U[1] * U[1] + U[2] * U[2]);
         double X1[3];

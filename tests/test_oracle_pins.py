@@ -156,6 +156,38 @@ def test_boris_uniform_magnetic_rotation_angle():
         assert ang == pytest.approx(expect, rel=1e-12)
 
 
+def test_vay_keeps_force_free_relativistic_drift_exact():
+    # E + v x B = 0 (a lab-static plasma in the undulator seen from the RRF is this case): Vay's
+    # pusher keeps u exactly; Boris does not for gamma >> 1 (the defect Vay's scheme removes),
+    # which also shows the check discriminates
+    for gam in (10.0, 100.0):
+        u0 = np.array([0.0, 0.0, math.sqrt(gam * gam - 1.0)])
+        v = u0 / gam
+        B = np.array([0.0, 3.0, 0.0])
+        E = -np.cross(v, B)
+        uv, ub = u0.copy(), u0.copy()
+        for _ in range(100):
+            uv = oracle.vay(-1.0, 0.05, E, B, uv)
+            ub = oracle.boris(-1.0, 0.05, E, B, ub)
+        assert np.max(np.abs(uv - u0)) < 1e-10 * gam
+        assert np.max(np.abs(ub - u0)) > 1e-6
+
+
+def test_vay_uniform_fields_and_nonrelativistic_limit():
+    rng = np.random.default_rng(14)
+    for _ in range(10):
+        u, E, B = rng.normal(size=3) * 3, rng.normal(size=3), rng.normal(size=3) * 2
+        qm, dt = -1.0, 0.2
+        # uniform E: the two half kicks add (q/m) E dt exactly
+        np.testing.assert_allclose(oracle.vay(qm, dt, E, [0, 0, 0], u), u + qm * E * dt, rtol=1e-14, atol=1e-14)
+        # uniform B: |u| (the energy) is conserved
+        assert np.linalg.norm(oracle.vay(qm, dt, [0, 0, 0], B, u)) == pytest.approx(np.linalg.norm(u), rel=1e-13)
+        # slow particle (v ~ 1e-4): Vay and Boris agree to O(v^2)
+        us = u * 1e-4
+        d = oracle.vay(qm, dt, E * 1e-4, B, us) - oracle.boris(qm, dt, E * 1e-4, B, us)
+        assert np.max(np.abs(d)) < 1e-7 * np.linalg.norm(us)
+
+
 def _single_particle_sim(grid, d, dt, gR, order=1):
     s = oracle.Sim(grid, d, dt, gR, bc=((PERIODIC, PERIODIC),) * 3, order=order)
     sid = s.add_species(-1.0, 1.0)
