@@ -53,6 +53,7 @@ enum {
     PIC_EX = 0, PIC_EY, PIC_EZ, PIC_BX, PIC_BY, PIC_BZ, PIC_JX, PIC_JY, PIC_JZ, PIC_RHO
 };
 enum { PIC_EXT_NONE = 0, PIC_EXT_PLANAR_UNDULATOR = 1 };
+enum { PIC_PUSHER_BORIS = 0, PIC_PUSHER_VAY = 1 };
 
 typedef struct pic_ctx pic_ctx;
 
@@ -217,6 +218,13 @@ int pic_set_plasma_batch(pic_ctx *ctx, const pic_plasma *p, const double *densit
  * (see pic_use_graphs); a step counter on the device gives each replayed step its time.
  * Asynchronous on the context stream. */
 int pic_step(pic_ctx *ctx, int64_t n);
+
+/* Momentum push of every mobile species.  PIC_PUSHER_BORIS (default): the Boris rotation, the
+ * reading of the paper's second-order leap-frog.  PIC_PUSHER_VAY: Vay's pusher, the modified
+ * pusher the paper cites for boosted-frame runs (Sec. 1): a half kick with the old velocity and
+ * a rotation whose Lorentz factor solves a quadratic, exact for E + v x B = 0 drifts (a
+ * lab-static plasma inside the undulator, seen from the RRF).  The adjoint needs Boris. */
+int pic_set_pusher(pic_ctx *ctx, int pusher);
 
 /* Replay of captured step sequences in pic_step (on = 1, the default) or one launch per kernel
  * (on = 0).  The capture is redone when species, the external field or the tuning change; if

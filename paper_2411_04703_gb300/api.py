@@ -31,6 +31,9 @@ MOMENT_NAMES = [
 ]
 
 
+PIC_PUSHER_BORIS, PIC_PUSHER_VAY = 0, 1
+
+
 class PicError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{ERRORS.get(code, code)}: {msg}")
@@ -124,6 +127,7 @@ def lib(build_if_missing: bool = True):
             "pic_get_moments_run": [vp, i, i, i, d, P(pic_moments)],
             "pic_autotune": [vp, i, P(i)],
             "pic_use_graphs": [vp, i],
+            "pic_set_pusher": [vp, i],
             "pic_checkpoint": [vp, i],
             "pic_backward": [vp, P(pic_adjoint_seed), P(pic_grads)],
             "pic_set_tuning": [vp, P(pic_tuning)],
@@ -344,6 +348,10 @@ class Sim:
         g = pic_grads()
         self._check(self.L.pic_backward(self.h, C.byref(seed), C.byref(g)))
         return {"loss": g.loss, "dL_dK": g.dL_dK, "dL_dprofile": np.array(g.dL_dprofile[:g.n_profile])}
+
+    def set_pusher(self, pusher):
+        """PIC_PUSHER_BORIS (0, default) or PIC_PUSHER_VAY (1)."""
+        self._check(self.L.pic_set_pusher(self.h, int(pusher)))
 
     def use_graphs(self, on=True):
         """Replay captured step sequences (CUDA graphs) where the step allows it."""

@@ -365,6 +365,7 @@ SpeciesDev species_dev(const pic_ctx *c, const Species &s)
     d.dlim = s.dlim;
     d.dmax = s.dmax;
     d.nfall = c->nfall;
+    d.pusher = c->pusher;
     d.frozen = s.frozen;
     d.cap = (int)s.cap;
     return d;
@@ -1118,6 +1119,17 @@ int pic_step(pic_ctx *c, int64_t nsteps)
     return PIC_OK;
 }
 
+int pic_set_pusher(pic_ctx *c, int pusher)
+{
+    int r = check_ctx(c);
+    if (r) return r;
+    if (pusher != PIC_PUSHER_BORIS && pusher != PIC_PUSHER_VAY) return fail(c, PIC_ERR_ARG, "unknown pusher");
+    if (c->ad_on && pusher != PIC_PUSHER_BORIS) return fail(c, PIC_ERR_STATE, "the adjoint reverses the Boris push");
+    drop_graph(c);   // captured launches hold the species parameters
+    c->pusher = pusher;
+    return PIC_OK;
+}
+
 int pic_use_graphs(pic_ctx *c, int on)
 {
     int r = check_ctx(c);
@@ -1414,6 +1426,7 @@ int pic_checkpoint(pic_ctx *c, int every_k)
     c->ad_on = 0;
     if (every_k <= 0) return PIC_OK;
     if (c->order != 1) return fail(c, PIC_ERR_ARG, "the adjoint is built for the first-order shape");
+    if (c->pusher != PIC_PUSHER_BORIS) return fail(c, PIC_ERR_ARG, "the adjoint reverses the Boris push");
     if (c->runs != 1 || c->moving || c->pml) return fail(c, PIC_ERR_ARG, "the adjoint needs one run, no window, no PML");
     for (int d = 0; d < 3; d++)
         if (c->bc[d][0] != PIC_BC_PERIODIC) return fail(c, PIC_ERR_ARG, "the adjoint needs a periodic grid");

@@ -108,6 +108,7 @@ struct SpeciesDev {
     const float *dlim;    // device [3]: displacement bound of this step (cells)
     unsigned *dmax;       // device [3]: largest |displacement| of this step (float bits, atomicMax)
     unsigned long long *nfall;  // device counter of particles that took the float-atomic fallback
+    int pusher;           // PIC_PUSHER_BORIS or PIC_PUSHER_VAY
     int frozen;
     int cap;
 };
@@ -253,6 +254,7 @@ struct pic_ctx {
     long long *dclock = nullptr;  // device step counter (equals step; advanced by a kernel per step)
     // CUDA graph of whole sort periods (no moving window, no injection, tracing off)
     int use_graphs = 1;
+    int pusher = 0;               // PIC_PUSHER_*
     cudaGraphExec_t graph = nullptr;
     int64_t graph_steps = 0;      // steps one replay advances
     int64_t graph_kernels = 0;    // kernels one replay runs

@@ -380,6 +380,31 @@ __device__ __forceinline__ void push_u(const Acc &acc, const float o[3], const i
         E[0] -= ext.beta_R * By;
     }
     const float h = sp.h_qm;
+    if (sp.pusher == PIC_PUSHER_VAY) {
+        // Vay: half kick with the old velocity, then the rotation whose Lorentz factor solves
+        // gamma^2 = (sigma + sqrt(sigma^2 + 4 (tau^2 + (u'.tau)^2))) / 2
+        const float u0[3] = {mo.x, mo.y, mo.z};
+        const float ig0 = rsqrtf(1.f + u0[0] * u0[0] + u0[1] * u0[1] + u0[2] * u0[2]);
+        const float v[3] = {u0[0] * ig0, u0[1] * ig0, u0[2] * ig0};
+        const float vxb[3] = {v[1] * B[2] - v[2] * B[1], v[2] * B[0] - v[0] * B[2], v[0] * B[1] - v[1] * B[0]};
+        float up[3], tau[3];
+#pragma unroll
+        for (int dd = 0; dd < 3; dd++) {
+            up[dd] = u0[dd] + h * (E[dd] + vxb[dd]) + h * E[dd];
+            tau[dd] = h * B[dd];
+        }
+        const float tau2 = tau[0] * tau[0] + tau[1] * tau[1] + tau[2] * tau[2];
+        const float ust = up[0] * tau[0] + up[1] * tau[1] + up[2] * tau[2];
+        const float sig = 1.f + up[0] * up[0] + up[1] * up[1] + up[2] * up[2] - tau2;
+        const float ig1 = rsqrtf(0.5f * (sig + sqrtf(sig * sig + 4.f * (tau2 + ust * ust))));
+        const float t[3] = {tau[0] * ig1, tau[1] * ig1, tau[2] * ig1};
+        const float s = 1.f / (1.f + t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+        const float ut = up[0] * t[0] + up[1] * t[1] + up[2] * t[2];
+        mo.x = s * (up[0] + ut * t[0] + up[1] * t[2] - up[2] * t[1]);
+        mo.y = s * (up[1] + ut * t[1] + up[2] * t[0] - up[0] * t[2]);
+        mo.z = s * (up[2] + ut * t[2] + up[0] * t[1] - up[1] * t[0]);
+        return;
+    }
     float um[3];
 #pragma unroll
     for (int dd = 0; dd < 3; dd++) um[dd] = fmaf(h, E[dd], dd == 0 ? mo.x : (dd == 1 ? mo.y : mo.z));

@@ -79,6 +79,40 @@ def test_one_step_from_identical_state(case):
         assert f[k] < TOL_STEP, (k, f)
 
 
+@pytest.mark.parametrize("case", ["vacuum_tsc", "plasma_tsc_pml_window"])
+def test_one_step_vay_pusher_from_identical_state(case):
+    w = CASES[case]()
+    sim, ids = api.from_workload(w)
+    sim.set_pusher(api.PIC_PUSHER_VAY)
+    random_fields(sim, w, seed=31)
+    o, oid = parity.oracle_from_gpu(w, sim, ids)
+    o.set_pusher(1)
+    sim.step(1)
+    sim.sync()
+    o.step(1)
+    for name in ids:
+        r = parity.compare_species(w, sim, ids[name], o, oid[name])
+        assert r["only_gpu"] == 0 and r["only_oracle"] == 0 and r["cell_mismatch"] == 0, (name, r)
+        assert r["u_rel_err"] < TOL_STEP, (name, r)
+    f = parity.compare_fields(sim, o)
+    assert max(f.values()) < TOL_STEP, f
+
+
+def test_vay_keeps_the_lab_static_plasma_at_rest_in_the_undulator():
+    # in the RRF a lab-static plasma drifts at -beta_R through E'_x = -beta_R B'_y: the force
+    # vanishes.  Boris leaves a spurious transverse momentum; Vay's pusher only FP32 rounding.
+    e = W.mini_ensemble()
+    ux = {}
+    for pusher in (api.PIC_PUSHER_BORIS, api.PIC_PUSHER_VAY):
+        sim, ids = api.from_ensemble(e, beam=False)
+        sim.set_pusher(pusher)
+        sim.step(20)
+        ux[pusher] = float(np.max(np.abs(sim.get_particles(ids["plasma_e"])["u"][:, 0])))
+        sim.close()
+    assert ux[api.PIC_PUSHER_BORIS] > 1e-7, ux
+    assert ux[api.PIC_PUSHER_VAY] < 0.1 * ux[api.PIC_PUSHER_BORIS], ux
+
+
 @pytest.mark.parametrize("case", ["vacuum_cic", "plasma_tsc_pml_window"])
 def test_identical_state_after_gpu_steps(case):
     # run the GPU alone, then hand its state to the oracle and compare one more step
