@@ -368,6 +368,14 @@ typedef struct {
 } pic_grads;
 int pic_backward(pic_ctx *ctx, const pic_adjoint_seed *seed, pic_grads *out);
 
+/* Relativistic resolution factor of the context's grid (Eq. Rrf1):
+ * R_RF = (8 L_wind / N_z) sqrt((1 - beta_R)/(1 + beta_R)), L_wind / N_z the longitudinal cell
+ * (of one run for an ensemble), i.e. eight RRF cells mapped back to the lab wavelength they
+ * resolve.  *ok = (R_RF < lambda_lab): the radiation of lab wavelength lambda_lab (normalised
+ * units, e.g. the resonant wavelength of Eq. RadLambda) gets at least eight cells per RRF
+ * wavelength.  Host-only; no device work. */
+int pic_resolution_factor(const pic_ctx *ctx, double lambda_lab, double *r_rf, int *ok);
+
 /* Release every device allocation of the context.  NULL is accepted. */
 int pic_destroy(pic_ctx *ctx);
 

@@ -11,6 +11,7 @@ ctypes.
 """
 from __future__ import annotations
 
+import math
 import ctypes as C
 import os
 import subprocess
@@ -122,6 +123,13 @@ def _f64(a):
 
 
 # ----------------------------------------------------------------- single-step helpers
+
+def resolution_factor(L_wind: float, n_cells: int, gamma_R: float) -> float:
+    """Relativistic resolution factor R_RF = (8 L_wind / N) sqrt((1 - beta_R)/(1 + beta_R))
+    (Eq. Rrf1), written as the formula reads."""
+    bR = math.sqrt(1.0 - 1.0 / (gamma_R * gamma_R))
+    return 8.0 * L_wind / n_cells * math.sqrt((1.0 - bR) / (1.0 + bR))
+
 
 def vay(qm: float, dt: float, E, B, u):
     """One Vay push of momentum u (copied) in E, B; returns the new momentum."""

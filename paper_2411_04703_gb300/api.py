@@ -128,6 +128,7 @@ def lib(build_if_missing: bool = True):
             "pic_autotune": [vp, i, P(i)],
             "pic_use_graphs": [vp, i],
             "pic_set_pusher": [vp, i],
+            "pic_resolution_factor": [vp, d, P(d), P(i)],
             "pic_checkpoint": [vp, i],
             "pic_backward": [vp, P(pic_adjoint_seed), P(pic_grads)],
             "pic_set_tuning": [vp, P(pic_tuning)],
@@ -348,6 +349,12 @@ class Sim:
         g = pic_grads()
         self._check(self.L.pic_backward(self.h, C.byref(seed), C.byref(g)))
         return {"loss": g.loss, "dL_dK": g.dL_dK, "dL_dprofile": np.array(g.dL_dprofile[:g.n_profile])}
+
+    def resolution_factor(self, lambda_lab):
+        """(R_RF, R_RF < lambda_lab) of the grid (Eq. Rrf1)."""
+        r, ok = C.c_double(), C.c_int()
+        self._check(self.L.pic_resolution_factor(self.h, float(lambda_lab), C.byref(r), C.byref(ok)))
+        return r.value, bool(ok.value)
 
     def set_pusher(self, pusher):
         """PIC_PUSHER_BORIS (0, default) or PIC_PUSHER_VAY (1)."""

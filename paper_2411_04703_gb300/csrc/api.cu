@@ -1130,6 +1130,15 @@ int pic_set_pusher(pic_ctx *c, int pusher)
     return PIC_OK;
 }
 
+int pic_resolution_factor(const pic_ctx *c, double lambda_lab, double *r_rf, int *ok)
+{
+    if (!c || !r_rf) return PIC_ERR_ARG;
+    // sqrt((1 - beta)/(1 + beta)) = 1 / (gamma (1 + beta)), free of cancellation at large gamma
+    *r_rf = 8.0 * c->d[2] / (c->gR * (1.0 + c->bR));
+    if (ok) *ok = *r_rf < lambda_lab ? 1 : 0;
+    return PIC_OK;
+}
+
 int pic_use_graphs(pic_ctx *c, int on)
 {
     int r = check_ctx(c);

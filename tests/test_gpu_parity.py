@@ -234,3 +234,15 @@ def test_moving_window_plasma_lattice_on_gpu():
             co = np.bincount(np.floor(X[:, 2]).astype(int), minlength=w.grid[2])
             assert np.array_equal(cg, co)
     assert sim.get_time()[1] > 0   # the window moved
+
+
+def test_resolution_factor_matches_oracle():
+    for w in (W.mini_vacuum(order=1), W.mini_long_undulator()):
+        sim, ids = api.from_workload(w, beam=False)
+        lam = api.resonant_wavenumber(w.undulator.lambda_u, w.undulator.K, w.beam.gamma)
+        lam = 2 * math.pi / lam
+        r, ok = sim.resolution_factor(lam)
+        ro = oracle.resolution_factor(w.grid[2] * w.d[2], w.grid[2], w.gamma_R)
+        assert r == pytest.approx(ro, rel=1e-8)
+        assert ok == (ro < lam)
+        sim.close()

@@ -18,7 +18,7 @@ def test_header_declares_the_boundary():
     for need in ["pic_create", "pic_load_species", "pic_set_external_field", "pic_set_plasma", "pic_step",
                  "pic_get_fields", "pic_get_moments", "pic_destroy", "pic_last_error", "pic_create_batch",
                  "pic_load_species_batch", "pic_set_external_field_batch", "pic_set_plasma_batch",
-                 "pic_get_moments_run", "pic_autotune", "pic_use_graphs", "pic_checkpoint", "pic_backward", "pic_set_pusher"]:
+                 "pic_get_moments_run", "pic_autotune", "pic_use_graphs", "pic_checkpoint", "pic_backward", "pic_set_pusher", "pic_resolution_factor"]:
         assert need in names
 
 

@@ -99,6 +99,24 @@ def test_resonant_and_rrf_wavelength_examples():
     assert oracle.doppler_rrf(lam, r["gamma_R"]) == pytest.approx(r["lambda_rrf_m_approx"], rel=r["rel_tol"])
 
 
+def test_resolution_factor_is_eight_rrf_cells_per_rrf_wavelength():
+    # Eq. Rrf1: R_RF < lambda_l  <=>  8 RRF cells fit in the RRF wavelength of lab wavelength
+    # lambda_l, which the boost stretches by the Doppler factor sqrt((1 + b)/(1 - b)) =
+    # gamma (1 + b) (radiation moving with the frame), the doppler_rrf worked example's factor
+    for gR in (1.0, 2.0, 10.0, 50.0, 1372.0):
+        L, N = 3.7, 256
+        R = oracle.resolution_factor(L, N, gR)
+        bR = math.sqrt(1 - 1 / gR ** 2)
+        dz = L / N
+        lam = 5.0 * dz
+        # (1 - beta_R as the formula reads it cancels to ~1e-9 relative at gamma_R ~ 1e3)
+        assert R == pytest.approx(8 * dz / (gR * (1 + bR)), rel=1e-8)
+        assert (R < lam) == (8 * dz < lam * gR * (1 + bR))
+        assert oracle.doppler_rrf(lam, gR) == pytest.approx(lam * gR * (1 + bR), rel=1e-8)
+    # no boost: R_RF is eight cells
+    assert oracle.resolution_factor(1.0, 8, 1.0) == pytest.approx(1.0)
+
+
 def test_field_transform_invariants_and_inverse():
     rng = np.random.default_rng(2)
     for beta in [0.3, 0.995, 1 - 1e-7]:
