@@ -15,7 +15,7 @@ namespace gbpic {
 constexpr int kMaxSpecies = 8;
 constexpr int kChunk = 4096;         // particles per work item of the particle kernel (at most)
 constexpr int kChunkMin = 512;       // smallest work item (small species are split finer)
-constexpr int kPushThreads = 512;
+constexpr int kPushThreads = 1024;   // 32 warps per SM at 64 registers (measured 3 % faster than 512 at 122)
 constexpr int kGroup = kChunk / kPushThreads;   // consecutive particles of one lane per work item
 constexpr int kSparse = 32;   // a tile with fewer particles takes the global-memory path, one warp per tile
 

@@ -530,10 +530,10 @@ __device__ __forceinline__ long long wrap_node(const GridDev &g, int x, int y, i
     return ((long long)p[2] * g.n[1] + p[1]) * g.n[0] + p[0];
 }
 
-// The deposit-only instantiation (frozen species) is held to two CTAs per SM (its smaller
-// shared region allows it; measured faster for the drifting ions despite a few spills).
+// One CTA of kPushThreads per SM: the shared region of a tile holds most of the SM's shared
+// memory, and 1024 threads at 64 registers (a few spills) hide more latency than 512 at 122.
 template <int ORDER, bool FROZEN, class Reg>
-__global__ void __launch_bounds__(kPushThreads, FROZEN ? 2 : 1)
+__global__ void __launch_bounds__(kPushThreads, 1)
 k_push(SpeciesDev sp, GridDev g, TileDev t, FieldsDev f, ExtDev ext0, int *work, int *work_sparse, int *err, Reg reg)
 {
     const ExtDev ext = ext_at_clock(ext0);
@@ -605,20 +605,19 @@ k_push(SpeciesDev sp, GridDev g, TileDev t, FieldsDev f, ExtDev ext0, int *work,
             }
         }
         __syncthreads();
-        // each lane takes kGroup = 8 consecutive particles: one cell of an 8-per-cell lattice,
-        // visited in octant order, so at every iteration the warp's 32 lanes sit on 32
+        // each lane takes gq consecutive particles (kGroup = 4 for a full item: half a cell of an
+        // 8-per-cell lattice, visited in octant order), and a warp's lanes sit NW * gq = 128
+        // particles (16 cells of that lattice) apart, so at every iteration the 32 lanes sit on 32
         // different cells with the same stencil shift (bank-conflict-free shared accesses, see
-        // plane_pitch)
+        // plane_pitch); a shorter item gives every lane fewer particles rather than idle lanes
         const int len = p_end - p_begin;
-        // gq consecutive particles per lane (kGroup for a full item; 4 for a tile of a 4-per-cell
-        // lattice), so that every lane of every warp has work
         const int gq = (len + kPushThreads - 1) / kPushThreads;
         constexpr int NW = kPushThreads / 32;
         for (int k_it = 0; k_it < gq; k_it++) {
-            // lane-major: a warp's lanes sit kChunk/32 particles apart in the cell-sorted item, so
-            // in a dense bunch (hundreds of particles per cell and octant) they still deposit into
-            // different windows instead of queueing on the same shared-memory words; each lane's
-            // G consecutive particles share cache lines across the warps
+            // lane-major: a warp's lanes sit far apart in the cell-sorted item, so in a dense bunch
+            // (hundreds of particles per cell and octant) they still deposit into different
+            // windows instead of queueing on the same shared-memory words; each lane's gq
+            // consecutive particles share cache lines across the warps
             const int q = gq == 1 ? (int)threadIdx.x : lane * (NW * gq) + warp * gq + k_it;
             unsigned dm[3] = {0u, 0u, 0u};   // |displacement| of this lane's particle (float bits)
             do {
