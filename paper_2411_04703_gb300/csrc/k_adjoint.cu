@@ -125,15 +125,21 @@ __device__ __forceinline__ void cross(const float a[3], const float b[3], float 
 __global__ void __launch_bounds__(kAdjThreads, 2) k_adj_particles(AdjP a)
 {
     const GridDev &g = a.g;
+    const unsigned lane = threadIdx.x & 31u;
     double kacc = 0.0;
     // consecutive threads take consecutive (cell-sorted) particles: coalesced record loads; the
     // scatters of a warp then often hit the same nodes, which measured cheaper than spreading the
-    // lanes over the records (uncoalesced loads: 5.1 vs 3.7 ms per step on the 64x64x256 run)
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < a.n; p += gridDim.x * blockDim.x) {
-        const float4 P = a.sp.pos[p];
+    // lanes over the records (uncoalesced loads: 5.1 vs 3.7 ms per step on the 64x64x256 run).
+    // Whole warps iterate together (the scatter below shuffles between lanes): a lane past the
+    // end or on an empty slot computes a stand-in particle at cell 0 and neither scatters nor
+    // stores.
+    for (int base = blockIdx.x * blockDim.x; base < a.n; base += gridDim.x * blockDim.x) {
+        const int p = base + (int)threadIdx.x;
+        float4 P = p < a.n ? a.sp.pos[p] : make_float4(0.5f, 0.5f, 0.5f, __int_as_float(-1));
+        const bool live = __float_as_int(P.w) >= 0;
+        if (!live) P = make_float4(0.5f, 0.5f, 0.5f, __int_as_float(0));
         const int cell = __float_as_int(P.w);
-        if (cell < 0) continue;
-        const float4 Mo = a.sp.mom[p];
+        const float4 Mo = live ? a.sp.mom[p] : make_float4(0.f, 0.f, 0.f, 0.f);
         const int c[3] = {g.cc.i(cell), g.cc.j(cell), g.cc.k(cell)};
         const float o[3] = {P.x, P.y, P.z};
         // wrapped node coordinates for the offsets -1 .. 2 the gather and deposit windows use,
@@ -149,11 +155,13 @@ __global__ void __launch_bounds__(kAdjThreads, 2) k_adj_particles(AdjP a)
         // ---- recompute the forward step: gather (+ external field), Boris, move
         float wu[3][2], ws[3][2], dwu[3][2], dws[3][2];
         int nu[3][2], ns[3][2];    // node offsets of the unstaggered / staggered gather windows
+        int oct = 0;               // which staggered window each dim takes (with the cell: all 48 nodes)
 #pragma unroll
         for (int d = 0; d < 3; d++) {
             int su, ss;
             w_unst(o[d], su, wu[d], dwu[d]);
             w_stag(o[d], ss, ws[d], dws[d]);
+            oct |= (ss != 0) << d;
             nu[d][0] = on[d][1];
             nu[d][1] = on[d][2];
             ns[d][0] = ss ? on[d][0] : on[d][1];
@@ -279,7 +287,8 @@ __global__ void __launch_bounds__(kAdjThreads, 2) k_adj_particles(AdjP a)
                 ld[d] += lSn * dS1(o[d] + dd[d] - m);
             }
         // ---- adjoint of the move x^{n+1} = x^n + d(u+)
-        const float4 LX = a.lx[p], LU = a.lu[p];
+        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 LX = live ? a.lx[p] : z4, LU = live ? a.lu[p] : z4;
         const float lx1[3] = {LX.x, LX.y, LX.z};
         for (int d = 0; d < 3; d++) {
             lo[d] += lx1[d];
@@ -316,37 +325,101 @@ __global__ void __launch_bounds__(kAdjThreads, 2) k_adj_particles(AdjP a)
         for (int d = 0; d < 3; d++) lE[d] += h * lum[d];
         const float lu0[3] = {lum[0], lum[1], lum[2]};
         // ---- adjoint of the gather and the external field
-        const float lF[6] = {lE[0], lE[1], lE[2], lB[0], lB[1], lB[2]};
+        const float lF[6] = {live ? lE[0] : 0.f, live ? lE[1] : 0.f, live ? lE[2] : 0.f,
+                             live ? lB[0] : 0.f, live ? lB[1] : 0.f, live ? lB[2] : 0.f};
+        // The 48 scatter targets follow from the cell and the staggered-window choice.  Where
+        // all 32 lanes of the warp share both (the core of a dense beam, ~1000 particles per
+        // cell, sorted by cell and octant), the warp sums the 48 values by a transpose
+        // reduction: each exchange halves the values a lane holds (24, 12, 6, 3 for lane bits
+        // 4..1; the last pair swaps all three), 48 shuffles in all; lane L ends with the totals
+        // of value indices 3 (L >> 1) .. 3 (L >> 1) + 2 and issues one or two atomics.  Other
+        // warps scatter their own values, 48 atomics per particle.
+        const long long key = live ? (((long long)cell << 3) | oct) : -1ll - (long long)lane;
+        const bool uniform = __all_sync(0xffffffffu, key == __shfl_sync(0xffffffffu, key, 0));
 #pragma unroll
-        for (int comp = 0; comp < 6; comp++) {
+        for (int comp = 0; comp < 6; comp++)
 #pragma unroll
             for (int d = 0; d < 3; d++) lo[d] = fmaf(lF[comp], dF[comp][d], lo[d]);
-            const bool st0 = comp < 3 ? comp == 0 : comp != 3;
-            const bool st1 = comp < 3 ? comp == 1 : comp != 4;
-            const bool st2 = comp < 3 ? comp == 2 : comp != 5;
-            float *lf = comp < 3 ? a.lE + comp * g.ncell : a.lB + (comp - 3) * g.ncell;
-            if (lF[comp] != 0.f)
+        if (uniform) {
+            // value index vi = comp * 8 + k * 4 + j * 2 + i: its weight, then its node
+            auto val = [&](int vi) {
+                const int comp = vi >> 3, i = vi & 1, j = (vi >> 1) & 1, k = (vi >> 2) & 1;
+                const bool st0 = comp < 3 ? comp == 0 : comp != 3;
+                const bool st1 = comp < 3 ? comp == 1 : comp != 4;
+                const bool st2 = comp < 3 ? comp == 2 : comp != 5;
+                const float wx = st0 ? ws[0][i] : wu[0][i];
+                const float wy = st1 ? ws[1][j] : wu[1][j];
+                const float wz = st2 ? ws[2][k] : wu[2][k];
+                return wx * wy * wz * lF[comp];
+            };
+            float h24[24], h12[12], h6[6], h3[3];
+            const bool b4 = lane & 16u, b3 = lane & 8u, b2 = lane & 4u, b1 = lane & 2u;
 #pragma unroll
-                for (int k = 0; k < 2; k++)
+            for (int q = 0; q < 24; q++) {
+                const float lo_ = val(q), hi_ = val(24 + q);
+                h24[q] = (b4 ? hi_ : lo_) + __shfl_xor_sync(0xffffffffu, b4 ? lo_ : hi_, 16);
+            }
 #pragma unroll
-                    for (int j = 0; j < 2; j++)
+            for (int q = 0; q < 12; q++)
+                h12[q] = (b3 ? h24[12 + q] : h24[q]) + __shfl_xor_sync(0xffffffffu, b3 ? h24[q] : h24[12 + q], 8);
 #pragma unroll
-                        for (int i = 0; i < 2; i++) {
-                            const float wx = st0 ? ws[0][i] : wu[0][i];
-                            const float wy = st1 ? ws[1][j] : wu[1][j];
-                            const float wz = st2 ? ws[2][k] : wu[2][k];
-                            const int ix = (st0 ? ns[0][i] : nu[0][i]) + (st1 ? ns[1][j] : nu[1][j]) + (st2 ? ns[2][k] : nu[2][k]);
-                            atomicAdd(lf + ix, wx * wy * wz * lF[comp]);
-                        }
+            for (int q = 0; q < 6; q++)
+                h6[q] = (b2 ? h12[6 + q] : h12[q]) + __shfl_xor_sync(0xffffffffu, b2 ? h12[q] : h12[6 + q], 4);
+#pragma unroll
+            for (int q = 0; q < 3; q++)
+                h3[q] = (b1 ? h6[3 + q] : h6[q]) + __shfl_xor_sync(0xffffffffu, b1 ? h6[q] : h6[3 + q], 2);
+#pragma unroll
+            for (int q = 0; q < 3; q++) h3[q] += __shfl_xor_sync(0xffffffffu, h3[q], 1);
+            const int vbase = 3 * (int)(lane >> 1);
+#pragma unroll
+            for (int q = 0; q < 3; q++) {
+                if ((q < 2) == ((lane & 1u) == 0u)) {
+                    const int vi = vbase + q;
+                    const int comp = vi >> 3;
+                    const int qq[3] = {vi & 1, (vi >> 1) & 1, (vi >> 2) & 1};
+                    int ix = 0;
+#pragma unroll
+                    for (int d = 0; d < 3; d++) {
+                        const bool st = comp < 3 ? comp == d : comp - 3 != d;
+                        const int x = wrapi(c[d] + qq[d] - ((st && ((oct >> d) & 1)) ? 1 : 0), g.n[d]);
+                        ix += d == 0 ? x : (d == 1 ? x * g.n[0] : x * g.n[0] * g.n[1]);
+                    }
+                    float *lf = comp < 3 ? a.lE + comp * g.ncell : a.lB + (comp - 3) * g.ncell;
+                    atomicAdd(lf + ix, h3[q]);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int comp = 0; comp < 6; comp++) {
+                const bool st0 = comp < 3 ? comp == 0 : comp != 3;
+                const bool st1 = comp < 3 ? comp == 1 : comp != 4;
+                const bool st2 = comp < 3 ? comp == 2 : comp != 5;
+                float *lf = comp < 3 ? a.lE + comp * g.ncell : a.lB + (comp - 3) * g.ncell;
+                if (lF[comp] != 0.f)
+#pragma unroll
+                    for (int k = 0; k < 2; k++)
+#pragma unroll
+                        for (int j = 0; j < 2; j++)
+#pragma unroll
+                            for (int i = 0; i < 2; i++) {
+                                const float wx = st0 ? ws[0][i] : wu[0][i];
+                                const float wy = st1 ? ws[1][j] : wu[1][j];
+                                const float wz = st2 ? ws[2][k] : wu[2][k];
+                                const int ix = (st0 ? ns[0][i] : nu[0][i]) + (st1 ? ns[1][j] : nu[1][j]) + (st2 ? ns[2][k] : nu[2][k]);
+                                atomicAdd(lf + ix, wx * wy * wz * lF[comp]);
+                            }
+            }
         }
         if (a.ext.type == PIC_EXT_PLANAR_UNDULATOR) {
             const float lBy = lF[4] - a.ext.beta_R * lF[0];
             lo[2] = fmaf(lBy, dBy_dz, lo[2]);
-            if (a.K != 0.f) kacc += (double)lBy * (double)By_ext / (double)a.K;
+            if (live && a.K != 0.f) kacc += (double)lBy * (double)By_ext / (double)a.K;
         }
-        a.lx[p] = make_float4(lo[0], lo[1], lo[2], 0.f);
-        a.lu[p] = make_float4(lu0[0], lu0[1], lu0[2], 0.f);
-        a.lw[a.sp.id[p]] += (double)lw_step;
+        if (live) {
+            a.lx[p] = make_float4(lo[0], lo[1], lo[2], 0.f);
+            a.lu[p] = make_float4(lu0[0], lu0[1], lu0[2], 0.f);
+            a.lw[a.sp.id[p]] += (double)lw_step;
+        }
     }
     // adjoint of K: block reduction, one atomic per block
     for (int off = 16; off > 0; off >>= 1) kacc += __shfl_down_sync(0xffffffffu, kacc, off);
