@@ -485,3 +485,77 @@ def from_ensemble(e, device=0, stream=None, tuning=None, beam=True):
                                              frame=PIC_FRAME_LAB, origin=b.beam.origin,
                                              match_undulator=bool(b.undulator is not None and b.undulator.match))
     return sim, ids
+
+
+def rrf_resonant_wavenumber(w) -> float:
+    """The boosted-frame image of the lab resonant wavenumber of workload ``w`` (its undulator's
+    K and period, the beam's gamma): k' = gamma_R (1 - beta_z beta_R) k, beta_z the beam's mean
+    longitudinal velocity in the undulator (Eq. RadLambda and the Lorentz transformation of a wave)."""
+    un = w.undulator
+    k_lab = resonant_wavenumber(un.lambda_u, un.K, w.beam.gamma)
+    bz = 1.0 - (1.0 + 0.5 * un.K ** 2) / (2.0 * w.beam.gamma ** 2)
+    return k_lab * w.gamma_R * (1.0 - bz * math.sqrt(1.0 - 1.0 / w.gamma_R ** 2))
+
+
+_BUNCHING_FN = None
+
+
+def _bunching_fn():
+    global _BUNCHING_FN
+    if _BUNCHING_FN is not None:
+        return _BUNCHING_FN
+    import copy
+
+    import torch
+
+    class BunchingLoss(torch.autograd.Function):
+        """Forward: run the workload with (K, profile) and return the bunching factor; backward:
+        the gradients pic_backward computed during the forward, times the incoming gradient."""
+
+        @staticmethod
+        def forward(ctx, K, profile, w, species, every, k_bunch, device):
+            nodes = tuple(float(v) for v in profile.detach().to("cpu", torch.float64).reshape(-1).tolist())
+            if w.plasma is None or len(nodes) != len(w.plasma.z_nodes):
+                raise ValueError("profile needs one density per plasma profile node of the workload")
+            wk = copy.deepcopy(w)
+            wk.plasma.n_nodes = nodes
+            sim, ids = from_workload(wk, device=device)
+            try:
+                un = wk.undulator
+                sim.set_external_field(float(K), un.lambda_u, un.phase, un.z_start, un.ramp)
+                sim.checkpoint(every)
+                sim.step(wk.steps)
+                g = sim.backward(ids[species], k_bunch)
+            finally:
+                sim.close()
+            ctx.meta = (K.dtype, K.device, profile.dtype, profile.device, profile.shape)
+            ctx.save_for_backward(torch.tensor(float(g["dL_dK"]), dtype=torch.float64),
+                                  torch.tensor(np.asarray(g["dL_dprofile"], np.float64)))
+            return torch.tensor(float(g["loss"]), dtype=torch.float64)
+
+        @staticmethod
+        def backward(ctx, grad):
+            dK, dP = ctx.saved_tensors
+            kt, kd, pt, pd, ps = ctx.meta
+            grad = grad.to("cpu", torch.float64)
+            return ((grad * dK).to(kd, kt), (grad * dP).reshape(ps).to(pd, pt),
+                    None, None, None, None, None)
+
+    _BUNCHING_FN = BunchingLoss
+    return BunchingLoss
+
+
+def bunching_loss(w, K, profile, species="beam", checkpoint_every=10, k_bunch=None, device=0):
+    """Differentiable loss for torch: the boosted-frame bunching factor of ``species`` after
+    ``w.steps`` steps of workload ``w``, run with undulator strength ``K`` and plasma profile node
+    densities ``profile`` (lab, units of n_n, one per node of ``w.plasma.z_nodes``).
+
+    ``K`` (0-d) and ``profile`` are tensors; ``loss.backward()`` gives their gradients from
+    pic_backward (checkpoints every ``checkpoint_every`` steps, segment recompute, adjoint sweep).
+    K enters through the undulator field seen during the steps; the beam is loaded matched to
+    ``w.undulator.K`` and held fixed.  ``k_bunch`` defaults to the boosted-frame image of the
+    resonant wavenumber at ``w.undulator.K`` (fixed, so it carries no gradient).  The forward runs
+    the whole simulation on the GPU; only the loss and the gradients come back.
+    """
+    kb = rrf_resonant_wavenumber(w) if k_bunch is None else float(k_bunch)
+    return _bunching_fn().apply(K, profile, w, species, int(checkpoint_every), kb, device)
