@@ -120,7 +120,7 @@ def beam_weight(charge_C: float, n_macro: int, omega_n: float) -> float:
 # ----------------------------------------------------------------------------- workloads
 
 def vacuum_undulator(grid=(32, 32, 64), n_beam=65536, steps=200, seed=1, order=1,
-                     name="C1 vacuum undulator 32x32x64, 65,536 beam, CIC") -> Workload:
+                     name="vacuum undulator 32x32x64, 65,536 beam, CIC") -> Workload:
     """Plain method: periodic 3D grid, boost 10, lab gamma 100 beam, planar undulator
     K = 1 (lambda_u = 2 cm, two RRF periods across 64 cells), first-order shape."""
     gR = 10.0
@@ -145,7 +145,7 @@ def vacuum_undulator(grid=(32, 32, 64), n_beam=65536, steps=200, seed=1, order=1
 
 def plasma_buncher(grid=(128, 128, 512), n_beam=4194304, steps=5000, seed=2, pml=10,
                    ppc=(2, 2, 2), dx_m=2.5e-6, dz_m=75e-6,
-                   name="C2 plasma buncher 128x128x512, 4M beam + 8 ppc plasma, TSC") -> Workload:
+                   name="plasma buncher 128x128x512, 4M beam + 8 ppc plasma, TSC") -> Workload:
     """Plasma buncher: boost 20, lab gamma 400 beam (sigma_r 10 um, sigma_z 30 um lab),
     cold lab-static plasma of 1e15 cm^-3 with immobile (frozen) neutralising ions, 8
     particles per cell, transverse PML, longitudinal moving window, second-order shape."""
@@ -170,7 +170,7 @@ def plasma_buncher(grid=(128, 128, 512), n_beam=4194304, steps=5000, seed=2, pml
 
 
 def long_undulator(grid=(256, 256, 1024), n_beam=33554432, steps=20000, seed=3, pml=10,
-                   name="C3 long undulator 256x256x1024, 32M beam, TSC") -> Workload:
+                   name="long undulator 256x256x1024, 32M beam, TSC") -> Workload:
     """Long undulator: lab gamma 2000, K = 1.5, lambda_u = 2 cm, boost gamma/sqrt(1+K^2/2)
     (beam at rest on average), PML on all faces, static window, undulator entrance ramp of
     one lab period, second-order shape, 64 cells per RRF undulator period."""
@@ -234,7 +234,7 @@ class Ensemble:
 
 def batched_ensemble(runs=64, grid=(64, 64, 128), steps=1000, seed=4, order=2, ppc=(1, 2, 2),
                      K_range=(0.5, 2.0), n_lab_cm3=(1e14, 1e16), n_beam_range=(1e5, 1e6),
-                     name="C4 batched ensemble 64 x (64x64x128), K and density sweep, TSC") -> Ensemble:
+                     name="batched ensemble 64 x (64x64x128), K and density sweep, TSC") -> Ensemble:
     """Batched sweep: periodic runs on a cubic grid of 64 cells per RRF undulator period
     (boost 10, lab gamma 100 beam of 30 pC, lambda_u = 2 cm; the undulator normalisation
     w_n = 2 pi gamma_R c / lambda_u is shared by every run), undulator K uniform in
@@ -285,7 +285,7 @@ def ensemble_run(e: Ensemble, r: int) -> Workload:
 
 
 def adjoint_workload(grid=(64, 64, 256), n_beam=2097152, steps=1000, seed=5, n_nodes=32, ppc=(1, 2, 2),
-                     name="C5 adjoint 64x64x256, 2M beam + 4 ppc plasma, CIC") -> Workload:
+                     name="differentiated run 64x64x256, 2M beam + 4 ppc plasma, CIC") -> Workload:
     """Differentiated run: the vacuum-undulator physics (boost 10, lab gamma 100 beam of 30 pC,
     K = 1, lambda_u = 2 cm, 32 cells per RRF undulator period, first-order shape, periodic) with
     a cold lab-static plasma of 4 particles per cell whose lab density is a piecewise-linear
