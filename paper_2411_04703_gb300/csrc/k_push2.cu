@@ -1,10 +1,15 @@
-// Second-order (TSC) instantiation of the fused particle kernel (see push_impl.cuh), the
-// dispatcher over shape orders, and the charge-density deposit used by pic_get_fields(RHO).
+// The dispatcher over the particle kernel's variants (shape order, frozen or mobile, region
+// shape; the second-order variants are compiled in k_push2_*.cu, the first-order ones in
+// k_push1.cu) and the charge-density deposit used by pic_get_fields(RHO).
 #include "push_impl.cuh"
 
 namespace gbpic {
 
 cudaError_t launch_push_order1(pic_ctx *c, int si, const ExtDev &ext);
+cudaError_t launch_push2_mobile_fixed(pic_ctx *c, int si, const ExtDev &ext);
+cudaError_t launch_push2_frozen_fixed(pic_ctx *c, int si, const ExtDev &ext);
+cudaError_t launch_push2_mobile_dyn(pic_ctx *c, int si, const ExtDev &ext);
+cudaError_t launch_push2_frozen_dyn(pic_ctx *c, int si, const ExtDev &ext);
 
 namespace {
 
@@ -89,7 +94,10 @@ cudaError_t launch_dlim_from_momenta(pic_ctx *c, int si)
 
 cudaError_t launch_push(pic_ctx *c, int si, const ExtDev &ext)
 {
-    return c->order == 1 ? launch_push_order1(c, si, ext) : push::launch_order<2>(c, si, ext);
+    if (c->order == 1) return launch_push_order1(c, si, ext);
+    const bool fr = c->sp[si].frozen != 0;
+    if (push::default_region(c)) return fr ? launch_push2_frozen_fixed(c, si, ext) : launch_push2_mobile_fixed(c, si, ext);
+    return fr ? launch_push2_frozen_dyn(c, si, ext) : launch_push2_mobile_dyn(c, si, ext);
 }
 
 // Adds the charge density of species s to rho.

@@ -795,20 +795,37 @@ cudaError_t launch_t(pic_ctx *c, int si, const ExtDev &ext, Reg reg, int R3)
 
 // Compile-time region for the default tile (8^3 cells, drift margin 1); any other tuning uses
 // the runtime-sized region.
+inline bool default_region(const pic_ctx *c)
+{
+    return c->T[0] == 8 && c->T[1] == 8 && c->T[2] == 8 && c->M == 1;
+}
+
+// One kernel variant: shape order, frozen or mobile species, compile-time (FIXED) or runtime
+// region.  The second-order variants each sit in a translation unit of their own, so that the
+// build compiles them in parallel.
+template <int ORDER, bool FROZEN, bool FIXED>
+cudaError_t launch_variant(pic_ctx *c, int si, const ExtDev &ext)
+{
+    if constexpr (FIXED) {
+        constexpr int R = 8 + 2 * 1 + (ORDER == 1 ? 3 : 5);
+        RegFix<R, R, R> reg;
+        constexpr int R3 = plane_pitch(R, R) * R;
+        return launch_t<ORDER, FROZEN>(c, si, ext, reg, R3);
+    } else {
+        const TileDev t = tile_dev(c, c->sp[si]);
+        const int P2 = plane_pitch(t.R[0], t.R[1]);
+        RegDyn reg{t.R[0], t.R[1], P2, P2 * t.R[2]};
+        return launch_t<ORDER, FROZEN>(c, si, ext, reg, reg.R3);
+    }
+}
+
 template <int ORDER>
 cudaError_t launch_order(pic_ctx *c, int si, const ExtDev &ext)
 {
-    constexpr int R = 8 + 2 * 1 + (ORDER == 1 ? 3 : 5);
     const bool fr = c->sp[si].frozen != 0;
-    const TileDev t = tile_dev(c, c->sp[si]);
-    if (c->T[0] == 8 && c->T[1] == 8 && c->T[2] == 8 && c->M == 1) {
-        RegFix<R, R, R> reg;
-        constexpr int R3 = plane_pitch(R, R) * R;
-        return fr ? launch_t<ORDER, true>(c, si, ext, reg, R3) : launch_t<ORDER, false>(c, si, ext, reg, R3);
-    }
-    const int P2 = plane_pitch(t.R[0], t.R[1]);
-    RegDyn reg{t.R[0], t.R[1], P2, P2 * t.R[2]};
-    return fr ? launch_t<ORDER, true>(c, si, ext, reg, reg.R3) : launch_t<ORDER, false>(c, si, ext, reg, reg.R3);
+    if (default_region(c))
+        return fr ? launch_variant<ORDER, true, true>(c, si, ext) : launch_variant<ORDER, false, true>(c, si, ext);
+    return fr ? launch_variant<ORDER, true, false>(c, si, ext) : launch_variant<ORDER, false, false>(c, si, ext);
 }
 
 }  // namespace push
