@@ -231,8 +231,7 @@ int pic_set_pusher(pic_ctx *ctx, int pusher);
  * capturing fails the context falls back to launching. */
 int pic_use_graphs(pic_ctx *ctx, int on);
 
-/* Autotuner of the tile-sort cadence (tile and sort sizes picked by an autotuner the project
- * writes).  Runs trials of whole sort periods (>= 32 steps each) with sort_every = 1, 2, 3, 4, 6,
+/* Autotuner of the tile-sort cadence (the tile itself is the compiled 8x8x8 region).  Runs trials of whole sort periods (>= 32 steps each) with sort_every = 1, 2, 3, 4, 6,
  * 8, 12, 16, 24, 32 (up to max_sort_every), each starting with a sort, in two passes (ascending,
  * then descending), times them with CUDA events on the context stream and keeps the fastest per
  * step (a rarer sort must win by 2 %).  The trial steps are real steps: the simulation advances
@@ -345,8 +344,10 @@ int pic_tile_sort_noalloc(const int32_t *cells, int64_t n, const int grid[3], co
  * state at the start of the differentiated interval and every every_k steps after (pic_step then
  * also sorts at those steps); pic_backward restores each checkpoint in reverse order, recomputes
  * its segment recording every step, and runs the segment's adjoint.  Requirements: first-order
- * shape, one run, periodic grid, no moving window or PML, undulator without entrance ramp.
- * every_k <= 0 turns recording off and frees the checkpoints. */
+ * shape, Boris pusher, one run, periodic grid, no moving window or PML, undulator without
+ * entrance ramp; otherwise PIC_ERR_ARG and nothing is recorded.  every_k <= 0 turns recording off
+ * and frees the checkpoints.  The checkpoints and the per-step records of one segment are device
+ * allocations of the context (about 250 MB per recorded step for 6.3M particles on 64x64x256). */
 int pic_checkpoint(pic_ctx *ctx, int every_k);
 
 /* Loss: the bunching factor of species_id in the boosted frame at the current step,
@@ -355,7 +356,11 @@ int pic_checkpoint(pic_ctx *ctx, int every_k);
  * beam loaded matched to the undulator keeps its loaded momenta), dL/dprofile through the
  * weights of the plasma electrons and the frozen ions, w = gamma_R n_lab(z_lab) dV / ppc with
  * n_lab piecewise linear through the profile nodes (Eq. Nnormi).  The context is left at the
- * state it had before the call.  Synchronous. */
+ * state it had before the call.  Synchronous.  Errors: PIC_ERR_ARG for a NULL seed or out, a
+ * seed species that is not a particle species, or more profile nodes than pic_grads holds;
+ * PIC_ERR_STATE when pic_checkpoint was not called before the steps; PIC_ERR_ALLOC,
+ * PIC_ERR_CUDA or PIC_ERR_DEVICE from the recomputation and the sweep.  out is caller-owned; its
+ * contents are meaningful only when PIC_OK is returned. */
 typedef struct {
     int species_id;
     double k_bunch;
