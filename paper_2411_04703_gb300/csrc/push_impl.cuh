@@ -21,6 +21,7 @@
 // deposited with the general window of order+2 nodes after the main loop.
 #pragma once
 
+#include <mutex>
 #include "gbpic_internal.cuh"
 
 #include <algorithm>
@@ -768,17 +769,33 @@ cudaError_t launch_t(pic_ctx *c, int si, const ExtDev &ext, Reg reg, int R3)
                         (size_t)kQueue * 8 * sizeof(float);
     auto kern = k_push<ORDER, FROZEN, Reg>;
     // attribute and occupancy once per kernel and region size (nothing but launches is then issued
-    // while a step sequence is captured into a CUDA graph)
-    static size_t smem_set = 0;
-    static int per_sm = 0, dev_set = -1;
+    // while a step sequence is captured into a CUDA graph).  The cache is shared by every context
+    // of the process: host threads driving contexts at once take it under a lock, and the shared-
+    // memory attribute only grows, so a launch issued after the lock is released never meets a
+    // smaller limit set by another thread.
+    constexpr int kMaxDevices = 64;
+    static std::mutex mu;
+    static size_t attr_max[kMaxDevices] = {};
+    static size_t occ_smem = 0;
+    static int occ_dev = -1, occ_per_sm = 0;
     cudaError_t e = cudaSuccess;
-    if (smem_set != smem || dev_set != c->dev.device) {
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPushThreads, smem);
-        if (e != cudaSuccess) return e;
-        smem_set = smem;
-        dev_set = c->dev.device;
+    int per_sm = 0;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        const int dv = c->dev.device;
+        if (dv < 0 || dv >= kMaxDevices) return cudaErrorInvalidDevice;
+        if (attr_max[dv] < smem) {
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            attr_max[dv] = smem;
+        }
+        if (occ_smem != smem || occ_dev != dv) {
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_per_sm, kern, kPushThreads, smem);
+            if (e != cudaSuccess) return e;
+            occ_smem = smem;
+            occ_dev = dv;
+        }
+        per_sm = occ_per_sm;
     }
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     FieldsDev f{c->E, c->B, c->J};
