@@ -1470,22 +1470,48 @@ int pic_backward(pic_ctx *c, const pic_adjoint_seed *seed, pic_grads *out)
     int *inv = nullptr;
     int64_t max_ids = 1;
     for (int si = 0; si < c->nsp; si++) max_ids = std::max<int64_t>(max_ids, c->sp[si].next_id);
+    StateSnap fin;   // the final state, restored at the end
+    // every exit releases the scratch buffers and the saved final state (partial ones included)
+    auto release = [&]() {
+        free_state(c, fin);
+        for (int si = 0; si < c->nsp; si++) {
+            dfree(c, lx[si]);
+            dfree(c, lu[si]);
+            dfree(c, lx2[si]);
+            dfree(c, lu2[si]);
+            dfree(c, lw[si]);
+        }
+        dfree(c, lE);
+        dfree(c, lB);
+        dfree(c, lJ);
+        dfree(c, lK);
+        dfree(c, R);
+        dfree(c, sums);
+        dfree(c, grad);
+        dfree(c, inv);
+        dfree(c, lw_plane);
+    };
     if ((r = alloc_zero(c, &lE, f3)) || (r = alloc_zero(c, &lB, f3)) || (r = alloc_zero(c, &lJ, f3)) ||
         (r = alloc_zero(c, &lK, 1)) || (r = alloc_zero(c, &R, (size_t)c->n[2])) || (r = alloc_zero(c, &sums, 3)) ||
-        (r = alloc_zero(c, &grad, 64)) || (r = alloc_zero(c, &inv, (size_t)max_ids)))
+        (r = alloc_zero(c, &grad, 64)) || (r = alloc_zero(c, &inv, (size_t)max_ids)) ||
+        (c->plasma && (r = alloc_zero(c, &lw_plane, (size_t)c->sp[c->sp_i].plane_cap)))) {
+        release();
         return r;
-    if (c->plasma && (r = alloc_zero(c, &lw_plane, (size_t)c->sp[c->sp_i].plane_cap))) return r;
+    }
     for (int si = 0; si < c->nsp; si++) {
         const Species &s = c->sp[si];
         if (s.lattice) continue;
         if ((r = alloc_zero(c, &lx[si], (size_t)s.cap)) || (r = alloc_zero(c, &lu[si], (size_t)s.cap)) ||
             (r = alloc_zero(c, &lx2[si], (size_t)s.cap)) || (r = alloc_zero(c, &lu2[si], (size_t)s.cap)) ||
-            (r = alloc_zero(c, &lw[si], (size_t)std::max<int64_t>(s.next_id, 1))))
+            (r = alloc_zero(c, &lw[si], (size_t)std::max<int64_t>(s.next_id, 1)))) {
+            release();
             return r;
+        }
     }
-    // the final state, restored at the end
-    StateSnap fin;
-    if ((r = save_state(c, fin, true))) return r;
+    if ((r = save_state(c, fin, true))) {
+        release();
+        return r;
+    }
     // records for one segment
     if ((int64_t)c->ad_rec.size() < K) c->ad_rec.resize((size_t)K);
     const int nseg = (int)((N - S0 + K - 1) / K);
@@ -1503,7 +1529,8 @@ int pic_backward(pic_ctx *c, const pic_adjoint_seed *seed, pic_grads *out)
         const StateSnap &last = c->ad_rec[(size_t)(e0 - 1 - s0)];
         if (j == nseg - 1) {
             double h3[3] = {0, 0, 0};   // seed: the loss's gradient on the final positions
-            CK(adj_bunch_seed(c, c->sp[sid], seed->k_bunch, sums, h3, lx[sid]));
+            const cudaError_t e = adj_bunch_seed(c, c->sp[sid], seed->k_bunch, sums, h3, lx[sid]);
+            if (e != cudaSuccess) { r = fail_cuda(c, e, "adjoint seed"); break; }
             const double rr = std::sqrt(h3[0] * h3[0] + h3[1] * h3[1]);
             out->loss = h3[2] > 0 ? rr / h3[2] : 0.0;
         } else {
@@ -1562,31 +1589,19 @@ int pic_backward(pic_ctx *c, const pic_adjoint_seed *seed, pic_grads *out)
     }
     if (r == PIC_OK) {
         double gk = 0.0, gp[64];
-        CK(cudaMemcpyAsync(&gk, lK, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-        CK(cudaMemcpyAsync(gp, grad, sizeof(double) * 64, cudaMemcpyDeviceToHost, c->stream));
-        CK(cudaStreamSynchronize(c->stream));
-        out->dL_dK = gk;
-        out->n_profile = c->plasma ? c->nprof : 0;
-        for (int q = 0; q < out->n_profile; q++) out->dL_dprofile[q] = gp[q];
-        r = restore_state(c, fin);
+        cudaError_t e = cudaMemcpyAsync(&gk, lK, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(gp, grad, sizeof(double) * 64, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) {
+            r = fail_cuda(c, e, "adjoint gradients");
+        } else {
+            out->dL_dK = gk;
+            out->n_profile = c->plasma ? c->nprof : 0;
+            for (int q = 0; q < out->n_profile; q++) out->dL_dprofile[q] = gp[q];
+            r = restore_state(c, fin);
+        }
     }
-    free_state(c, fin);
-    for (int si = 0; si < c->nsp; si++) {
-        dfree(c, lx[si]);
-        dfree(c, lu[si]);
-        dfree(c, lx2[si]);
-        dfree(c, lu2[si]);
-        dfree(c, lw[si]);
-    }
-    dfree(c, lE);
-    dfree(c, lB);
-    dfree(c, lJ);
-    dfree(c, lK);
-    dfree(c, R);
-    dfree(c, sums);
-    dfree(c, grad);
-    dfree(c, inv);
-    dfree(c, lw_plane);
+    release();
     return r;
 }
 
