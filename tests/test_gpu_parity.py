@@ -122,15 +122,25 @@ def test_identical_state_after_gpu_steps(case):
     sim.step(9)
     sim.sync()
     o, oid = parity.oracle_from_gpu(w, sim, ids)
-    if w.pml:
-        pytest.skip("PML auxiliary state is not exported; covered by the whole-run case")
     sim.step(1)
     sim.sync()
     o.step(1)
     for name in ids:
         r = parity.compare_species(w, sim, ids[name], o, oid[name])
         assert r["cell_mismatch"] == 0 and r["u_rel_err"] < TOL_STEP, (name, r)
-    f = parity.compare_fields(sim, o)
+    if not w.pml:
+        f = parity.compare_fields(sim, o)
+        assert max(f.values()) < TOL_STEP, f
+        return
+    # The CPML's auxiliary (psi) state is not exported: the oracle restarts it at zero.  That
+    # changes E and B inside the absorbing layers and, through the three sub-steps of one update
+    # (B half, E, B half), at most two cells beyond them.  The particles (pushed with the exported
+    # E^n, B^n) and the currents are compared everywhere, E and B three cells clear of the layers.
+    m = w.pml + 3
+    keep = tuple(slice(m, w.grid[d] - m) if w.bc[d][0] == W.PML else slice(None) for d in (2, 1, 0))
+    f = parity.compare_fields(sim, o, comps=range(6, 9))
+    for c in range(6):
+        f[c] = parity.rel_err(sim.get_field(c).astype(np.float64)[keep], o.field(c)[keep])
     assert max(f.values()) < TOL_STEP, f
 
 
