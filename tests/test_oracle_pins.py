@@ -146,6 +146,32 @@ def test_undulator_in_rrf_is_a_moving_magnet():
         np.testing.assert_allclose(E, -np.cross(V, B), rtol=1e-12, atol=1e-12)
 
 
+def test_undulator_entrance_ramp_sits_at_its_lab_position():
+    # The entrance ramp ("gentle slope", Sec. "Electron propagation") is a property of the lab
+    # element: no field before z_start, full field after z_start + ramp, half amplitude at
+    # mid-ramp, whatever RRF (z', t') maps there.  Placing it at z' instead of the lab z would move
+    # it by a factor gamma_R.
+    gR = 20.0
+    full = oracle.Sim((4, 4, 4), (1, 1, 1), 0.1, gR)
+    full.set_external(K=1.3, lambda_u=5.0)
+    z0, L = 40.0, 10.0
+    ramped = oracle.Sim((4, 4, 4), (1, 1, 1), 0.1, gR)
+    ramped.set_external(K=1.3, lambda_u=5.0, z_start=z0, ramp=L)
+    step = oracle.Sim((4, 4, 4), (1, 1, 1), 0.1, gR)
+    step.set_external(K=1.3, lambda_u=5.0, z_start=z0, ramp=0.0)
+    bR = full.beta_R
+    for zlab, f_ramp, f_step in [(z0 - 3.0, 0.0, 0.0), (z0 + 0.5 * L, 0.5, 1.0), (z0 + 0.25 * L, 0.25, 1.0),
+                                 (z0 + L + 2.0, 1.0, 1.0), (z0 - 0.01, 0.0, 0.0)]:
+        for tp in (0.0, 1.5):
+            zp = zlab / gR - bR * tp          # the RRF point whose lab position is zlab
+            Ef, Bf = full.external_at(zp, tp)
+            Er, Br = ramped.external_at(zp, tp)
+            Es, Bs = step.external_at(zp, tp)
+            np.testing.assert_allclose(Br, f_ramp * Bf, rtol=1e-9, atol=1e-12)
+            np.testing.assert_allclose(Er, f_ramp * Ef, rtol=1e-9, atol=1e-12)
+            np.testing.assert_allclose(Bs, f_step * Bf, rtol=1e-9, atol=1e-12)
+
+
 # ------------------------------------------------------------------ push
 
 def test_boris_uniform_electric_field_exact():
@@ -571,3 +597,49 @@ def test_tile_sort_groups_tiles_cells_and_octants():
     same = np.diff(keys) == 0
     assert np.all(np.diff(order)[same] > 0)           # stable among equal keys
     assert np.all(same == (same_cell & (np.diff(octant) == 0)))
+
+
+# ------------------------------------------------------------------ gather
+
+# Yee positions (cells): E_c half a cell along c, B_c half a cell along the other two axes.
+YEE = {EX: (0.5, 0, 0), EY: (0, 0.5, 0), EZ: (0, 0, 0.5), BX: (0, 0.5, 0.5), BY: (0.5, 0, 0.5), BZ: (0.5, 0.5, 0)}
+
+
+def _node_positions(n, stag):
+    k, j, i = np.meshgrid(np.arange(n[2]), np.arange(n[1]), np.arange(n[0]), indexing="ij")
+    return i + stag[0], j + stag[1], k + stag[2]
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_gather_reproduces_linear_fields_at_yee_positions(order):
+    # CIC and TSC are partitions of unity with zero first moment, so a field that is linear in
+    # position, sampled at each component's Yee positions, is gathered exactly at any point.
+    # A wrong stagger, a transposed axis or a wrong shape fails this.
+    n = (16, 16, 16)
+    s = oracle.Sim(n, (1, 1, 1), 0.1, 1.0, order=order)
+    rng = np.random.default_rng(5)
+    a = rng.uniform(-1, 1, 6)
+    b = rng.uniform(-1, 1, (6, 3))
+    for c, stag in YEE.items():
+        x, y, z = _node_positions(n, stag)
+        s.set_field(c, a[c] + b[c, 0] * x + b[c, 1] * y + b[c, 2] * z)
+    for X in rng.uniform(5.0, 11.0, (20, 3)):
+        got = s.gather_at(X)
+        for c in YEE:
+            assert got[c] == pytest.approx(a[c] + b[c] @ X, rel=1e-12, abs=1e-12), (order, c, X)
+
+
+def test_tsc_gather_of_a_quadratic_adds_the_shape_variance():
+    # The quadratic B-spline (three unit boxes convolved) has variance 3/12: sampling x^2 at the
+    # nodes and gathering with it gives x^2 + 1/4 at every point.
+    n = (16, 16, 16)
+    s = oracle.Sim(n, (1, 1, 1), 0.1, 1.0, order=2)
+    for c, stag in YEE.items():
+        x, y, z = _node_positions(n, stag)
+        s.set_field(c, (x - 8.0) ** 2 + 0.5 * (z - 8.0) ** 2)
+    rng = np.random.default_rng(6)
+    for X in rng.uniform(5.0, 11.0, (20, 3)):
+        got = s.gather_at(X)
+        expect = (X[0] - 8.0) ** 2 + 0.25 + 0.5 * ((X[2] - 8.0) ** 2 + 0.25)
+        for c in YEE:
+            assert got[c] == pytest.approx(expect, rel=1e-12, abs=1e-12), (c, X)
