@@ -538,6 +538,31 @@ def test_periodic_box_plasma_fills_once_and_drifts_rigidly():
     assert np.max(np.abs(Ui[:, 2] + gR * math.sqrt(1 - 1 / gR ** 2))) < 1e-12
 
 
+def test_multi_node_profile_weights_follow_piecewise_linear_interpolation():
+    # Every plasma electron at t' = 0 sits at lab z = gamma_R z' and carries
+    # w = gamma_R n_lab(z) dV / ppc (Eq. Nnormi), n_lab piecewise linear through the nodes and 0
+    # outside them; numpy's interp is that definition.  Seven uneven nodes, some inside the box's
+    # lab image and some beyond it, exercise the segment search.
+    grid = (4, 4, 16)
+    d = (1.0, 1.0, 0.6)
+    gR = 4.0
+    s = oracle.Sim(grid, d, 0.25, gR, bc=((PERIODIC, PERIODIC),) * 3, order=1)
+    se = s.add_species(-1.0, 1.0)
+    si = s.add_species(1.0, 1836.0, frozen=True)
+    zl = gR * grid[2] * d[2]
+    zn = (0.05 * zl, 0.2 * zl, 0.23 * zl, 0.5 * zl, 0.71 * zl, 0.9 * zl, 1.3 * zl)
+    nn = (0.4, 1.1, 0.2, 0.9, 0.9, 0.05, 0.6)
+    ppc = (1, 2, 2)
+    s.set_plasma(se, si, ppc, (0, 4, 0, 4), zn, nn)
+    X, _, W, _ = s.particles(se)
+    zlab = gR * X[:, 2] * d[2]
+    expect = gR * np.interp(zlab, zn, nn, left=0.0, right=0.0) * d[0] * d[1] * d[2] / (ppc[0] * ppc[1] * ppc[2])
+    live = expect > 0
+    assert np.count_nonzero(live) > 0.8 * len(W)
+    np.testing.assert_allclose(W[live], expect[live], rtol=1e-12)
+    assert np.all(W[~live] == 0.0)
+
+
 def test_uniform_periodic_plasma_stays_field_free():
     # uniform neutral drifting plasma in a periodic box: rho = 0 and J = 0 at every node, so the
     # fields stay exactly zero and the electrons are never accelerated
