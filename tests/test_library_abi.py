@@ -34,3 +34,81 @@ def test_binding_loads_without_gpu():
     from paper_2411_04703_gb300 import api
     L = api.lib()
     assert L.pic_last_error(None) is not None or True
+
+
+# ------------------------------------------------------------------ argument validation
+# pic_create checks its arguments before any CUDA call, so its error behaviour (PIC_ERR_ARG and
+# the message kept for pic_last_error(NULL)) is testable without a GPU.
+
+PIC_ERR_ARG, PIC_ERR_CUDA = -1, -2
+
+
+def _create(L, api, grid=(16, 16, 16), dx=(1.0, 1.0, 1.0), dt=0.4, gamma=10.0, faces=((0, 0),) * 3, pml=0,
+            moving=0, window_v=0.0, order=1, runs=None):
+    h = ctypes.c_void_p()
+    bc = api.pic_boundaries()
+    for d in range(3):
+        for f in range(2):
+            bc.face[d][f] = faces[d][f]
+    bc.pml_cells, bc.moving_window, bc.window_v = pml, moving, window_v
+    g = api.pic_grid(*grid)
+    d3 = (ctypes.c_double * 3)(*dx)
+    if runs is None:
+        r = L.pic_create(ctypes.byref(h), g, d3, dt, gamma, ctypes.byref(bc), order, None)
+    else:
+        r = L.pic_create_batch(ctypes.byref(h), runs, g, d3, dt, gamma, ctypes.byref(bc), order, None)
+    return r, h
+
+
+def _message(L):
+    m = L.pic_last_error(None)
+    return m.decode() if isinstance(m, bytes) else str(m)
+
+
+def test_create_rejects_bad_arguments_before_touching_the_device():
+    from paper_2411_04703_gb300 import api
+    L = api.lib()
+    PML, OPEN = 1, 2
+    cases = [
+        (dict(order=3), "shape_order"),
+        (dict(dt=0.6), "Courant"),                       # 1/sqrt(3) = 0.577 for unit cells
+        (dict(gamma=0.5), "gamma_boost"),
+        (dict(dx=(1.0, 0.0, 1.0)), "cell sizes"),
+        (dict(grid=(2048, 16, 16)), "nx and ny"),
+        (dict(faces=((0, 1), (0, 0), (0, 0))), "periodic on both faces"),
+        (dict(faces=((PML, PML), (0, 0), (0, 0)), pml=0), "pml_cells"),
+        (dict(faces=((PML, PML), (0, 0), (0, 0)), pml=8), "thicker than half"),
+        (dict(moving=1, window_v=0.5), "non-periodic z"),
+        (dict(faces=((0, 0), (0, 0), (OPEN, OPEN)), moving=1, window_v=3.0), "window_v"),
+        (dict(runs=0), "runs must be"),
+        (dict(runs=4, faces=((0, 0), (0, 0), (OPEN, OPEN))), "z must be periodic"),
+        (dict(runs=4, grid=(16, 16, 12)), "multiple of the tile size"),
+    ]
+    for kw, words in cases:
+        r, h = _create(L, api, **kw)
+        assert r == PIC_ERR_ARG, (kw, r)
+        assert not h.value, kw
+        assert words in _message(L), (kw, _message(L))
+
+
+def test_null_handles_are_refused_and_destroy_accepts_null():
+    from paper_2411_04703_gb300 import api
+    L = api.lib()
+    assert L.pic_destroy(None) == 0
+    assert L.pic_step(None, 1) == PIC_ERR_ARG
+    assert L.pic_sync(None) == PIC_ERR_ARG
+    r, h = ctypes.c_double(), ctypes.c_int()
+    assert L.pic_resolution_factor(None, 1.0, ctypes.byref(r), ctypes.byref(h)) == PIC_ERR_ARG
+
+
+def test_valid_create_without_a_gpu_fails_loudly():
+    # no CPU fallback: with valid arguments and no device, creation reports the CUDA failure
+    import pytest
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2411_04703_gb300 import api
+    L = api.lib()
+    r, h = _create(L, api)
+    assert r == PIC_ERR_CUDA and not h.value, r
+    assert "cuda" in _message(L).lower()
