@@ -112,3 +112,28 @@ def test_valid_create_without_a_gpu_fails_loudly():
     r, h = _create(L, api)
     assert r == PIC_ERR_CUDA and not h.value, r
     assert "cuda" in _message(L).lower()
+
+
+def test_noalloc_sort_rejects_out_of_range_sizes_before_any_device_work():
+    # every case fails its host-side checks, so the (placeholder, never dereferenced) buffer
+    # addresses are not touched
+    from paper_2411_04703_gb300 import api, build
+    L = api.lib()                                      # pic_last_error(NULL) with its signature
+    S = ctypes.CDLL(build.build()).pic_tile_sort_noalloc
+    S.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    S.restype = ctypes.c_int
+    fake = ctypes.c_void_p(256)
+    g = (ctypes.c_int * 3)(64, 64, 64)
+    t = (ctypes.c_int * 3)(8, 8, 8)
+    cases = [
+        ((None, 10, g, t, fake, fake), "null pointer"),
+        ((fake, -1, g, t, fake, fake), "negative n"),
+        ((fake, (1 << 20) + 1, g, t, fake, fake), "exceeds the maximum"),
+        ((fake, 10, g, (ctypes.c_int * 3)(8, 128, 8), fake, fake), "out of range"),
+        ((fake, 10, (ctypes.c_int * 3)(1024, 1024, 8), (ctypes.c_int * 3)(1, 1, 1), fake, fake), "keys exceed"),
+    ]
+    for (cells, n, grid, tile, order, key_start), words in cases:
+        r = S(cells, n, grid, tile, order, key_start, None)
+        assert r == PIC_ERR_ARG, (words, r)
+        assert words in _message(L), (words, _message(L))
