@@ -256,3 +256,22 @@ def test_resolution_factor_matches_oracle():
         assert r == pytest.approx(ro, rel=1e-8)
         assert ok == (ro < lam)
         sim.close()
+
+
+def test_empty_species_steps_as_vacuum():
+    # degenerate input: a context whose only particle species is empty (loaded with n = 0) steps
+    # as the vacuum FDTD, which the oracle (no species at all) computes; the species stays empty
+    w = W.mini_vacuum(order=2)
+    sim, ids = api.from_workload(w, beam=False)
+    sid = sim.load_species(-1.0, 1.0, None, None, None, frame=api.PIC_FRAME_LAB, origin=w.beam.origin)
+    random_fields(sim, w, seed=11)
+    o = oracle.Sim(w.grid, w.d, w.dt, w.gamma_R, bc=w.bc, order=w.order)
+    for c in range(6):
+        o.set_field(c, sim.get_field(c).astype(np.float64))
+    sim.step(3)
+    sim.sync()
+    o.step(3)
+    assert sim.get_count(sid) == 0
+    f = parity.compare_fields(sim, o)
+    assert max(f.values()) < TOL_STEP, f
+    sim.close()
