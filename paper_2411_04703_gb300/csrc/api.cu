@@ -1212,7 +1212,9 @@ int pic_sync(pic_ctx *c)
     int e = 0;
     CK(cudaMemcpy(&e, c->err, sizeof(int), cudaMemcpyDeviceToHost));
     if (e) {
-        std::string m = "device error word 0x" + std::to_string(e) + ":";
+        char hex[16];
+        std::snprintf(hex, sizeof(hex), "0x%x", (unsigned)e);
+        std::string m = std::string("device error word ") + hex + ":";
         if (e & ERR_INDEX) m += " stencil node outside a non-periodic grid;";
         if (e & ERR_CAPACITY) m += " species capacity exceeded;";
         if (e & ERR_MOVE) m += " particle moved one cell or more in a step;";
