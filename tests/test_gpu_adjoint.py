@@ -119,18 +119,3 @@ def test_adjoint_matches_gpu_central_differences(adjoint):
     assert g["dL_dK"] == pytest.approx(dK, rel=3e-2), (g["dL_dK"], dK)
     # (the profile's effect on the loss, ~1e-7 per node, is below the FP32 forward's rounding at
     # h = 1e-4; the oracle's FP64 differences check that part)
-
-
-def test_torch_autograd_wrapper_gives_the_adjoint(adjoint):
-    # api.bunching_loss runs the same simulation through torch.autograd: its loss and gradients
-    # are those of pic_backward (checked against the oracle above), up to FP32 run-to-run rounding
-    torch = pytest.importorskip("torch")
-    w, g, _ = adjoint
-    K = torch.tensor(w.undulator.K, dtype=torch.float64, requires_grad=True)
-    prof = torch.tensor(w.plasma.n_nodes, dtype=torch.float64, requires_grad=True)
-    loss = api.bunching_loss(w, K, prof, checkpoint_every=10, k_bunch=_k_rrf(w))
-    loss.backward()
-    assert loss.item() == pytest.approx(g["loss"], rel=1e-4)
-    assert K.grad.item() == pytest.approx(g["dL_dK"], rel=2e-3)
-    scale = np.max(np.abs(g["dL_dprofile"]))
-    assert np.max(np.abs(prof.grad.numpy() - g["dL_dprofile"])) < 2e-3 * scale
