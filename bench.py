@@ -200,6 +200,8 @@ def run_reference(args):
     rank, world, _ = env_rank()
     if rank != 0:
         return 0
+    from paper_2411_04703_gb300 import workloads as W
+    full = W.plasma_buncher()            # the workload the default arm measures (its config)
     steps = args.steps
     value, t, sample = oracle_sample(steps, args.warmup)
     line = {
@@ -207,7 +209,8 @@ def run_reference(args):
         "steps": steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t / steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": "plasma buncher 128x128x512 (bounded sample 32x32x128), TSC, PML, moving window",
+        "config": {"workload": full.name, "grid": list(full.grid), "shape": "TSC",
+                   "boundaries": "transverse CPML 10 cells, moving window",
                    "sample": sample},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},

@@ -27,6 +27,9 @@ def test_reference_arm_prints_the_contract_line():
                 "scaling", "vs_baseline", "dtype", "data", "config"):
         assert key in line, key
     assert line["value"] > 0 and line["higher_is_better"] is True and line["steps"] == 1
+    from paper_2411_04703_gb300 import workloads as W
+    assert line["config"]["workload"] == W.plasma_buncher().name      # the default arm's workload
+    assert line["config"]["sample"]
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
     e2e = line["e2e"]
