@@ -668,3 +668,140 @@ def test_tsc_gather_of_a_quadratic_adds_the_shape_variance():
         expect = (X[0] - 8.0) ** 2 + 0.25 + 0.5 * ((X[2] - 8.0) ** 2 + 0.25)
         for c in YEE:
             assert got[c] == pytest.approx(expect, rel=1e-12, abs=1e-12), (c, X)
+
+
+# ------------------------------------------------------------------ lab-frame diagnostics
+# The lab-frame moments transform every RRF event back to the lab (Eq. Lor1-Lor2 inverted) and
+# drift each particle ballistically to the weighted mean lab time (the time skew of Eq. DT).
+# For a ballistic beam every back-transformed event lies on the particle's lab straight line,
+# so the drifted lab positions are the loaded lab positions (lab t = 0) plus one common shift
+# v t_mean when all velocities are equal: the lab bunching at k_r, the lab rms length and the
+# lab emittance (a shear x -> x + (u_x/gamma) t with one gamma) equal those of the input.
+
+GR_LAB, GB_LAB = 5.0, 10.0          # RRF and beam Lorentz factors (Eq. Belon factor ~ 7.96)
+
+
+def _lab_beam(n, lam, rng, gamma=GB_LAB, ux_sigma=0.0, x_sigma=0.0):
+    """Lab beam at t = 0: z on a comb of period lam with two phases (bunching |cos(phi/2)|
+    mixed with a uniform part), transverse x with an x-u_x correlation, one lab gamma."""
+    m = rng.integers(0, 24, n)
+    ph = np.where(rng.random(n) < 0.5, 0.0, 1.1)
+    uni = rng.random(n) < 0.3
+    z = lam * (m + ph / (2 * math.pi)) + np.where(uni, lam * rng.random(n), 0.0)
+    x = rng.normal(0.0, x_sigma, n) if x_sigma else np.zeros(n)
+    ux = (0.4 * x + rng.normal(0.0, ux_sigma, n)) if ux_sigma else np.zeros(n)
+    uz = np.sqrt(gamma * gamma - 1.0 - ux * ux)
+    X = np.stack([x, np.zeros(n), z - z.mean()])
+    U = np.stack([ux, np.zeros(n), uz])
+    return X, U
+
+
+def _bunching(z, k, w=None):
+    w = np.ones_like(z) if w is None else w
+    return abs(np.sum(w * np.exp(-1j * k * z))) / np.sum(w)
+
+
+def _emit(x, ux):
+    cx = np.mean((x - x.mean()) * (ux - ux.mean()))
+    return math.sqrt(np.var(x) * np.var(ux) - cx * cx)
+
+
+def _lab_sim(q=0.0):
+    # a charge-free species moves ballistically (no current, no self field), so the pins hold
+    # after steps as well as at load
+    s = oracle.Sim((4, 4, 512), (1.0, 1.0, 1.0), 0.5, GR_LAB, order=1)
+    sid = s.add_species(q, 1.0)
+    return s, sid
+
+
+@pytest.mark.parametrize("steps", [0, 12])
+def test_lab_moments_recover_the_lab_bunching_length_and_mean_time(steps):
+    rng = np.random.default_rng(21)
+    lam = 1.0
+    X, U = _lab_beam(6000, lam, rng)
+    s, sid = _lab_sim()
+    org = (2.0, 2.0, 256.0)
+    assert s.load(sid, X, U, frame=LAB, origin=org) == X.shape[1]
+    s.step(steps)
+    kr = 2 * math.pi / lam
+    b_in = _bunching(X[2], kr)
+    assert 0.3 < b_in < 0.9
+    m1 = s.moments(sid, frame=1, k=kr)
+    assert m1["bunching"] == pytest.approx(b_in, rel=1e-9)
+    assert m1["rms_z"] == pytest.approx(np.std(X[2]), rel=1e-9)
+    assert m1["mean_gamma"] == pytest.approx(GB_LAB, rel=1e-12)
+    # the RRF image of k_r (Doppler/Lorentz: k' = k_r gamma_R (1 - beta_B beta_R)) gives the same
+    # bunching in the boosted frame, since z' = z / (gamma_R (1 - beta_B beta_R)) per particle
+    bR, bB = math.sqrt(1 - GR_LAB ** -2), math.sqrt(1 - GB_LAB ** -2)
+    m0 = s.moments(sid, frame=0, k=kr * GR_LAB * (1 - bB * bR))
+    assert m0["bunching"] == pytest.approx(b_in, rel=1e-9)
+    # mean lab time of the events: t = gamma_R (t' + beta_R z'), z' = z / (gamma_R (1 - bB bR)) +
+    # beta' t' + origin; the input z has mean 0
+    bp = (bB - bR) / (1 - bB * bR)
+    tp = steps * 0.5
+    zp_mean = org[2] + bp * tp
+    assert m1["mean_t"] == pytest.approx(GR_LAB * (tp + bR * zp_mean), rel=1e-12)
+
+
+def test_lab_moments_wrong_or_missing_drift_would_fail_the_bunching_pin():
+    # The same events drifted with the sign of the drift flipped, or not drifted at all, lose the
+    # lab bunching by far more than the pin's tolerance: the pin above detects both mistakes.
+    rng = np.random.default_rng(21)
+    lam = 1.0
+    X, U = _lab_beam(6000, lam, rng)
+    bR, bB = math.sqrt(1 - GR_LAB ** -2), math.sqrt(1 - GB_LAB ** -2)
+    zp = X[2] / (GR_LAB * (1 - bB * bR))          # Eq. Belon, per particle (monoenergetic)
+    t_ev = GR_LAB * bR * zp                       # lab time of each event at t' = 0
+    z_ev = GR_LAB * zp                            # lab position of each event
+    tm = t_ev.mean()
+    kr = 2 * math.pi / lam
+    b_in = _bunching(X[2], kr)
+    right = z_ev + bB * (tm - t_ev)
+    flipped = z_ev + bB * (t_ev - tm)
+    assert _bunching(right, kr) == pytest.approx(b_in, rel=1e-9)
+    assert abs(_bunching(flipped, kr) - b_in) > 0.05
+    assert abs(_bunching(z_ev, kr) - b_in) > 0.05
+
+
+def test_lab_emittance_is_the_input_emittance_for_one_gamma():
+    rng = np.random.default_rng(22)
+    X, U = _lab_beam(8000, 1.0, rng, ux_sigma=0.05, x_sigma=0.3)
+    # the RRF drift to t' = 0 moves x by up to a few cells: a wide box keeps every particle away
+    # from the periodic wrap
+    s = oracle.Sim((64, 4, 512), (1.0, 1.0, 1.0), 0.5, GR_LAB, order=1)
+    sid = s.add_species(0.0, 1.0)
+    assert s.load(sid, X, U, frame=LAB, origin=(32.0, 2.0, 256.0)) == X.shape[1]
+    eps = _emit(X[0], U[0])
+    assert eps > 0.01
+    for steps in (0, 10):
+        if steps:
+            s.step(steps)
+        m1 = s.moments(sid, frame=1, k=0.0)
+        assert m1["emit_nx"] == pytest.approx(eps, rel=1e-8)
+        assert m1["emit_ny"] == pytest.approx(0.0, abs=1e-12)
+        assert m1["mean_gamma"] == pytest.approx(GB_LAB, rel=1e-12)
+
+
+def test_lab_energy_spread_and_kinetic_energy_of_a_two_energy_beam():
+    rng = np.random.default_rng(23)
+    n = 4000
+    g = np.where(np.arange(n) % 2 == 0, 9.0, 11.0)
+    z = rng.uniform(-3, 3, n)
+    X = np.stack([np.zeros(n), np.zeros(n), z])
+    U = np.stack([np.zeros(n), np.zeros(n), np.sqrt(g * g - 1)])
+    w = np.where(np.arange(n) % 2 == 0, 1.0, 3.0)
+    s = oracle.Sim((4, 4, 512), (1.0, 1.0, 1.0), 0.5, GR_LAB, order=1)
+    sid = s.add_species(0.0, 2.5)
+    s.load(sid, X, U, w, frame=LAB, origin=(2.0, 2.0, 256.0))
+    m1 = s.moments(sid, frame=1)
+    # weights 1 : 3 on gamma 9 : 11 -> mean 10.5, std sqrt(0.25*0.75)*2 = 0.866
+    assert m1["mean_gamma"] == pytest.approx(10.5, rel=1e-12)
+    assert m1["rel_energy_spread"] == pytest.approx(2 * math.sqrt(0.25 * 0.75) / 10.5, rel=1e-10)
+    assert m1["kinetic_energy"] == pytest.approx(2.5 * np.sum(w * (g - 1)), rel=1e-12)
+    assert m1["sum_w"] == pytest.approx(np.sum(w), rel=1e-15)
+    assert m1["charge"] == 0.0
+    # in the boosted frame the same beam has gamma' = gamma_R (gamma - beta_R u_z) per particle
+    m0 = s.moments(sid, frame=0)
+    bR = math.sqrt(1 - GR_LAB ** -2)
+    gp = GR_LAB * (g - bR * np.sqrt(g * g - 1))
+    assert m0["kinetic_energy"] == pytest.approx(2.5 * np.sum(w * (gp - 1)), rel=1e-9)
