@@ -260,10 +260,7 @@ def run_adjoint(args):
     sim.sync()
     torch.cuda.synchronize()
     fwd_ms = e0.elapsed_time(e1)
-    un = w.undulator
-    k_lab = api.resonant_wavenumber(un.lambda_u, un.K, w.beam.gamma)
-    bz = 1.0 - (1.0 + 0.5 * un.K ** 2) / (2.0 * w.beam.gamma ** 2)
-    k_rrf = k_lab * w.gamma_R * (1.0 - bz * math.sqrt(1.0 - 1.0 / w.gamma_R ** 2))
+    k_rrf = api.rrf_resonant_wavenumber(w)
     t0 = time.perf_counter()
     g = sim.backward(ids["beam"], k_rrf)
     torch.cuda.synchronize()

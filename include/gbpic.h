@@ -381,6 +381,18 @@ int pic_backward(pic_ctx *ctx, const pic_adjoint_seed *seed, pic_grads *out);
  * wavelength.  Host-only; no device work. */
 int pic_resolution_factor(const pic_ctx *ctx, double lambda_lab, double *r_rf, int *ok);
 
+/* FEL resonant wavenumber of the bunching diagnostic (Eq. RadLambda, Sec. "Relativistic booster
+ * frame"): the lab wavelength lambda_l = lambda_u (1 + K^2/2) / (2 gamma_B^2) radiated by a beam of
+ * lab Lorentz factor gamma_B in a planar undulator of strength K and lab period lambda_u
+ * (normalised units).  frame PIC_FRAME_LAB: *k = 2 pi / lambda_l.  frame PIC_FRAME_BOOSTED: the
+ * image of that wave pattern, moving with the beam's mean lab velocity beta_z (1 - beta_z =
+ * (1 + K^2/2) / (2 gamma_B^2)), in the frame of Lorentz factor gamma_R: *k = gamma_R (1 - beta_z
+ * beta_R) 2 pi / lambda_l, the inverse of the beam elongation of Eq. Belon at the mean velocity
+ * (formed without cancellation at large gamma).  Host-only, FP64, no context and no device work.
+ * Errors: PIC_ERR_ARG for k NULL, lambda_u <= 0, K < 0, gamma_B < 1, gamma_R < 1, a non-finite
+ * argument or an unknown frame (message in pic_last_error(NULL)). */
+int pic_resonant_wavenumber(double K, double lambda_u, double gamma_B, double gamma_R, int frame, double *k);
+
 /* Release every device allocation of the context.  NULL is accepted. */
 int pic_destroy(pic_ctx *ctx);
 

@@ -129,6 +129,7 @@ def lib(build_if_missing: bool = True):
             "pic_use_graphs": [vp, i],
             "pic_set_pusher": [vp, i],
             "pic_resolution_factor": [vp, d, P(d), P(i)],
+            "pic_resonant_wavenumber": [d, d, d, d, i, P(d)],
             "pic_checkpoint": [vp, i],
             "pic_backward": [vp, P(pic_adjoint_seed), P(pic_grads)],
             "pic_set_tuning": [vp, P(pic_tuning)],
@@ -431,10 +432,16 @@ class Sim:
         return tuple(int(v) for v in out)
 
 
-def resonant_wavenumber(lambda_u: float, K: float, gamma_B: float) -> float:
-    """Lab FEL resonant wavenumber 2 pi / lambda_l with lambda_l = lambda_u (1 + K^2/2)/(2 gamma^2)
-    (Eq. RadLambda), for the bunching diagnostic."""
-    return 2.0 * math.pi * 2.0 * gamma_B ** 2 / (lambda_u * (1.0 + 0.5 * K * K))
+def resonant_wavenumber(lambda_u: float, K: float, gamma_B: float, gamma_R: float = 1.0,
+                        frame: int = PIC_FRAME_LAB) -> float:
+    """FEL resonant wavenumber of Eq. RadLambda (pic_resonant_wavenumber): the lab value, or its
+    image in the frame of Lorentz factor gamma_R (frame=PIC_FRAME_BOOSTED)."""
+    L = lib()
+    k = C.c_double()
+    r = L.pic_resonant_wavenumber(float(K), float(lambda_u), float(gamma_B), float(gamma_R), int(frame), C.byref(k))
+    if r != 0:
+        raise PicError(r, L.pic_last_error(None).decode())
+    return k.value
 
 
 def from_workload(w, device=0, stream=None, tuning=None, beam=True, beam_arrays=None):
@@ -489,12 +496,9 @@ def from_ensemble(e, device=0, stream=None, tuning=None, beam=True):
 
 def rrf_resonant_wavenumber(w) -> float:
     """The boosted-frame image of the lab resonant wavenumber of workload ``w`` (its undulator's
-    K and period, the beam's gamma): k' = gamma_R (1 - beta_z beta_R) k, beta_z the beam's mean
-    longitudinal velocity in the undulator (Eq. RadLambda and the Lorentz transformation of a wave)."""
+    K and period, the beam's gamma, the frame's gamma_R), from pic_resonant_wavenumber."""
     un = w.undulator
-    k_lab = resonant_wavenumber(un.lambda_u, un.K, w.beam.gamma)
-    bz = 1.0 - (1.0 + 0.5 * un.K ** 2) / (2.0 * w.beam.gamma ** 2)
-    return k_lab * w.gamma_R * (1.0 - bz * math.sqrt(1.0 - 1.0 / w.gamma_R ** 2))
+    return resonant_wavenumber(un.lambda_u, un.K, w.beam.gamma, w.gamma_R, PIC_FRAME_BOOSTED)
 
 
 _BUNCHING_FN = None

@@ -1139,6 +1139,31 @@ int pic_resolution_factor(const pic_ctx *c, double lambda_lab, double *r_rf, int
     return PIC_OK;
 }
 
+int pic_resonant_wavenumber(double K, double lambda_u, double gamma_B, double gamma_R, int frame, double *k)
+{
+    if (!k) return fail(nullptr, PIC_ERR_ARG, "pic_resonant_wavenumber: k is NULL");
+    if (!(lambda_u > 0.0) || !(gamma_B >= 1.0) || !(gamma_R >= 1.0) || !(K >= 0.0) || !std::isfinite(K) ||
+        !std::isfinite(lambda_u) || !std::isfinite(gamma_B) || !std::isfinite(gamma_R)) {
+        return fail(nullptr, PIC_ERR_ARG,
+                    "pic_resonant_wavenumber: need lambda_u > 0, K >= 0, gamma_B >= 1, gamma_R >= 1 (finite)");
+    }
+    if (frame != PIC_FRAME_LAB && frame != PIC_FRAME_BOOSTED) {
+        return fail(nullptr, PIC_ERR_ARG, "pic_resonant_wavenumber: frame must be PIC_FRAME_LAB or PIC_FRAME_BOOSTED");
+    }
+    const double a = 1.0 + 0.5 * K * K;
+    // Eq. RadLambda: lambda_l = lambda_u (1 + K^2/2) / (2 gamma_B^2)
+    const double k_lab = 2.0 * M_PI * 2.0 * gamma_B * gamma_B / (lambda_u * a);
+    if (frame == PIC_FRAME_LAB) { *k = k_lab; return PIC_OK; }
+    // a structure moving with the beam's mean lab velocity beta_z (1 - beta_z = a / (2 gamma_B^2))
+    // has k' = gamma_R (1 - beta_z beta_R) k in the frame moving at beta_R; the factor is formed
+    // as (1 - beta_R) + beta_R (1 - beta_z) with 1 - beta_R = 1 / (gamma_R^2 (1 + beta_R))
+    const double bR = std::sqrt(1.0 - 1.0 / (gamma_R * gamma_R));
+    const double one_m_bR = 1.0 / (gamma_R * gamma_R * (1.0 + bR));
+    const double one_m_bz = a / (2.0 * gamma_B * gamma_B);
+    *k = k_lab * gamma_R * (one_m_bR + bR * one_m_bz);
+    return PIC_OK;
+}
+
 int pic_use_graphs(pic_ctx *c, int on)
 {
     int r = check_ctx(c);

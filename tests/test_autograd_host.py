@@ -84,12 +84,10 @@ def test_bunching_loss_default_wavenumber_and_profile_length(monkeypatch):
     K = torch.tensor(w.undulator.K, dtype=torch.float64, requires_grad=True)
     prof = torch.tensor(w.plasma.n_nodes, dtype=torch.float64, requires_grad=True)
     api.bunching_loss(w, K, prof)
-    # the boosted-frame image of the lab resonant wavenumber: k' = gamma_R (1 - beta_z beta_R) k,
-    # with beta_z from the undulator's mean longitudinal velocity
+    # the default k_bunch is the boosted-frame image of the lab resonant wavenumber, from the
+    # library's Eq. RadLambda call at the workload's K, beam gamma and gamma_R
     un, g, gR = w.undulator, w.beam.gamma, w.gamma_R
-    lam = un.lambda_u * (1 + un.K ** 2 / 2) / (2 * g ** 2)
-    bz = 1 - (1 + un.K ** 2 / 2) / (2 * g ** 2)
-    expect = 2 * np.pi / lam * gR * (1 - bz * np.sqrt(1 - 1 / gR ** 2))
+    expect = api.resonant_wavenumber(un.lambda_u, un.K, g, gR, api.PIC_FRAME_BOOSTED)
     assert seen["kb"] == pytest.approx(expect, rel=1e-12)
     with pytest.raises(ValueError):
         api.bunching_loss(w, K, prof[:5])

@@ -35,11 +35,7 @@ def _cuda():
 
 
 def _k_rrf(w):
-    un = w.undulator
-    k_lab = api.resonant_wavenumber(un.lambda_u, un.K, w.beam.gamma)
-    bz = 1.0 - (1.0 + 0.5 * un.K ** 2) / (2.0 * w.beam.gamma ** 2)
-    bR = math.sqrt(1.0 - 1.0 / w.gamma_R ** 2)
-    return k_lab * w.gamma_R * (1.0 - bz * bR)
+    return api.rrf_resonant_wavenumber(w)
 
 
 def _workload(profile_scale=None):

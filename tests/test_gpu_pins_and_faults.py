@@ -234,10 +234,7 @@ def test_refused_allocation_in_create_is_reported_and_released():
 # ------------------------------------------------------------------ autograd wrapper
 
 def _k_rrf(w):
-    un = w.undulator
-    k_lab = api.resonant_wavenumber(un.lambda_u, un.K, w.beam.gamma)
-    bz = 1.0 - (1.0 + 0.5 * un.K ** 2) / (2.0 * w.beam.gamma ** 2)
-    return k_lab * w.gamma_R * (1.0 - bz * math.sqrt(1.0 - 1.0 / w.gamma_R ** 2))
+    return api.rrf_resonant_wavenumber(w)
 
 
 def test_torch_autograd_wrapper_gives_the_adjoint():

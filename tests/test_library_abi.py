@@ -4,6 +4,8 @@ import ctypes
 import os
 import re
 
+import pytest
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
@@ -18,7 +20,8 @@ def test_header_declares_the_boundary():
     for need in ["pic_create", "pic_load_species", "pic_set_external_field", "pic_set_plasma", "pic_step",
                  "pic_get_fields", "pic_get_moments", "pic_destroy", "pic_last_error", "pic_create_batch",
                  "pic_load_species_batch", "pic_set_external_field_batch", "pic_set_plasma_batch",
-                 "pic_get_moments_run", "pic_autotune", "pic_use_graphs", "pic_checkpoint", "pic_backward", "pic_set_pusher", "pic_resolution_factor"]:
+                 "pic_get_moments_run", "pic_autotune", "pic_use_graphs", "pic_checkpoint", "pic_backward", "pic_set_pusher", "pic_resolution_factor",
+                 "pic_resonant_wavenumber"]:
         assert need in names
 
 
@@ -33,7 +36,37 @@ def test_library_exports_every_declared_symbol():
 def test_binding_loads_without_gpu():
     from paper_2411_04703_gb300 import api
     L = api.lib()
-    assert L.pic_last_error(None) is not None or True
+    # before any failed call the context-free message is an empty string, not NULL
+    assert isinstance(L.pic_last_error(None), bytes)
+
+
+# ------------------------------------------------------------------ Eq. RadLambda (host-only call)
+
+def test_resonant_wavenumber_matches_the_oracle(oracle_lib):
+    import math
+
+    import oracle
+    from paper_2411_04703_gb300 import api
+    for lam_u, K, gB, gR in [(0.02, 1.0, 100.0, 10.0), (2.0, 1.5, 2000.0, 2000.0 / math.sqrt(2.125)),
+                             (7.3, 0.0, 300.0, 50.0), (1.0, 2.0, 5.0, 1.0)]:
+        k_lab = api.resonant_wavenumber(lam_u, K, gB)
+        assert k_lab == pytest.approx(2 * math.pi / oracle.resonant_wavelength(lam_u, K, gB), rel=1e-13)
+        # the boosted image is the lab wave pattern moving with the beam's mean velocity, whose
+        # longitudinal Lorentz factor is gamma_B / sqrt(1 + K^2/2): stretched by Eq. Belon's factor.
+        # Both forms of the mean velocity agree to leading order, 1 - beta_z = 1/(2 gamma_z^2); they
+        # differ by the next term, of relative size 1/gamma_z^2 at most
+        gz = gB / math.sqrt(1 + 0.5 * K * K)
+        k_rrf = api.resonant_wavenumber(lam_u, K, gB, gR, api.PIC_FRAME_BOOSTED)
+        assert k_rrf == pytest.approx(k_lab / oracle.beam_elongation(gz, gR), rel=1.0 / gz ** 2)
+
+
+def test_resonant_wavenumber_rejects_bad_arguments():
+    from paper_2411_04703_gb300 import api
+    for args in [(0.0, 1.0, 100.0), (1.0, -1.0, 100.0), (1.0, 1.0, 0.5), (float("nan"), 1.0, 100.0)]:
+        with pytest.raises(api.PicError, match="pic_resonant_wavenumber"):
+            api.resonant_wavenumber(*args)
+    with pytest.raises(api.PicError, match="frame"):
+        api.resonant_wavenumber(1.0, 1.0, 100.0, 10.0, 7)
 
 
 # ------------------------------------------------------------------ argument validation
