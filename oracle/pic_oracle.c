@@ -74,6 +74,7 @@ typedef struct {
     osp sp[O_MAXSP];
     long dropped; /* deposit contributions outside a non-periodic grid (should stay 0) */
     int pusher;   /* 0: Boris, 1: Vay */
+    int threads;  /* > 1: the particle loop runs on that many OpenMP threads (timing only) */
 } osim;
 
 /* ------------------------------------------------------------------ shapes */
@@ -654,10 +655,10 @@ static const double O_STAG[6][3] = {
     {0.5, 0.0, 0.0}, {0.0, 0.5, 0.0}, {0.0, 0.0, 0.5},
     {0.0, 0.5, 0.5}, {0.5, 0.0, 0.5}, {0.5, 0.5, 0.0}};
 
-static void o_add(osim *s, double *f, long i, long j, long k, double v)
+static void o_add(const osim *s, double *f, long *dropped, long i, long j, long k, double v)
 {
     long ix = o_index(s, i, j, k);
-    if (ix < 0) { if (v != 0.0) s->dropped++; return; }
+    if (ix < 0) { if (v != 0.0) (*dropped)++; return; }
     f[ix] += v;
 }
 
@@ -667,7 +668,8 @@ static void o_add(osim *s, double *f, long i, long j, long k, double v)
  *   W_x = DS_x (S0_y S0_z + DS_y S0_z/2 + S0_y DS_z/2 + DS_y DS_z/3)   (cyclic for y, z),
  *   J_x(i+1/2) - J_x(i-1/2) = -q w (dx/dt) W_x(i) / V_cell,
  * accumulated from the low end of the stencil where J = 0. */
-static void o_esirkepov(osim *s, double qw, const double X0[3], const double X1[3])
+static void o_esirkepov(const osim *s, double *const J[3], long *dropped, double qw, const double X0[3],
+                        const double X1[3])
 {
     long lo[3], cnt[3];
     double S0[3][8], DS[3][8];
@@ -694,7 +696,7 @@ static void o_esirkepov(osim *s, double qw, const double X0[3], const double X1[
                 double Wx = DS[0][a] * (S0[1][b] * S0[2][c] + 0.5 * DS[1][b] * S0[2][c] +
                                         0.5 * S0[1][b] * DS[2][c] + DS[1][b] * DS[2][c] / 3.0);
                 acc += Wx;
-                o_add(s, s->F[O_JX], lo[0] + a, lo[1] + b, lo[2] + c, cf[0] * acc);
+                o_add(s, J[0], dropped, lo[0] + a, lo[1] + b, lo[2] + c, cf[0] * acc);
             }
         }
     /* J_y: prefix along y for each (x, z) */
@@ -705,7 +707,7 @@ static void o_esirkepov(osim *s, double qw, const double X0[3], const double X1[
                 double Wy = DS[1][b] * (S0[2][c] * S0[0][a] + 0.5 * DS[2][c] * S0[0][a] +
                                         0.5 * S0[2][c] * DS[0][a] + DS[2][c] * DS[0][a] / 3.0);
                 acc += Wy;
-                o_add(s, s->F[O_JY], lo[0] + a, lo[1] + b, lo[2] + c, cf[1] * acc);
+                o_add(s, J[1], dropped, lo[0] + a, lo[1] + b, lo[2] + c, cf[1] * acc);
             }
         }
     /* J_z: prefix along z for each (x, y) */
@@ -716,39 +718,82 @@ static void o_esirkepov(osim *s, double qw, const double X0[3], const double X1[
                 double Wz = DS[2][c] * (S0[0][a] * S0[1][b] + 0.5 * DS[0][a] * S0[1][b] +
                                         0.5 * S0[0][a] * DS[1][b] + DS[0][a] * DS[1][b] / 3.0);
                 acc += Wz;
-                o_add(s, s->F[O_JZ], lo[0] + a, lo[1] + b, lo[2] + c, cf[2] * acc);
+                o_add(s, J[2], dropped, lo[0] + a, lo[1] + b, lo[2] + c, cf[2] * acc);
             }
         }
 }
 
-/* Gather + push + move + deposit of every live particle of species p (one leap-frog step). */
-static void o_push_species(osim *s, osp *p)
+/* Gather + push + move + deposit of particle i of species p (one leap-frog step); the current
+ * goes to J[3], deposits outside a non-periodic grid are counted in *dropped. */
+static void o_push_one(const osim *s, osp *p, long i, double *const J[3], long *dropped)
 {
     double tp = (double)s->step * s->dt;
     double qm = p->q / p->m;
-    for (long i = 0; i < p->n; i++) {
-        if (!p->alive[i]) continue;
-        double *X = &p->X[3 * i], *U = &p->U[3 * i];
-        if (!p->frozen) {
-            double E[3], B[3], Ee[3], Be[3];
-            for (int c = 0; c < 3; c++) {
-                E[c] = o_gather(s, s->F[O_EX + c], O_STAG[c], X);
-                B[c] = o_gather(s, s->F[O_BX + c], O_STAG[3 + c], X);
-            }
-            o_external(s, (X[2] + (double)s->shifts) * s->d[2], tp, Ee, Be);
-            for (int c = 0; c < 3; c++) { E[c] += Ee[c]; B[c] += Be[c]; }
-            if (s->pusher == 1) oracle_vay(qm, s->dt, E, B, U);
-            else oracle_boris(qm, s->dt, E, B, U);
+    double *X = &p->X[3 * i], *U = &p->U[3 * i];
+    if (!p->frozen) {
+        double E[3], B[3], Ee[3], Be[3];
+        for (int c = 0; c < 3; c++) {
+            E[c] = o_gather(s, s->F[O_EX + c], O_STAG[c], X);
+            B[c] = o_gather(s, s->F[O_BX + c], O_STAG[3 + c], X);
         }
-        double g = sqrt(1.0 + U[0] * U[0] + U[1] * U[1] + U[2] * U[2]);
-        double X1[3];
-        for (int d = 0; d < 3; d++) X1[d] = X[d] + s->dt * U[d] / (g * s->d[d]);
-        double Xw[3] = {X1[0], X1[1], X1[2]};
-        o_wrap_pos(s, Xw);
-        if (!o_inside(s, Xw)) { p->alive[i] = 0; continue; }
-        o_esirkepov(s, p->q * p->W[i], X, X1);
-        memcpy(X, Xw, sizeof Xw);
+        o_external(s, (X[2] + (double)s->shifts) * s->d[2], tp, Ee, Be);
+        for (int c = 0; c < 3; c++) { E[c] += Ee[c]; B[c] += Be[c]; }
+        if (s->pusher == 1) oracle_vay(qm, s->dt, E, B, U);
+        else oracle_boris(qm, s->dt, E, B, U);
     }
+    double g = sqrt(1.0 + U[0] * U[0] + U[1] * U[1] + U[2] * U[2]);
+    double X1[3];
+    for (int d = 0; d < 3; d++) X1[d] = X[d] + s->dt * U[d] / (g * s->d[d]);
+    double Xw[3] = {X1[0], X1[1], X1[2]};
+    o_wrap_pos(s, Xw);
+    if (!o_inside(s, Xw)) { p->alive[i] = 0; return; }
+    o_esirkepov(s, J, dropped, p->q * p->W[i], X, X1);
+    memcpy(X, Xw, sizeof Xw);
+}
+
+/* Every live particle of species p, in index order, depositing into the grid's J. */
+static void o_push_species(osim *s, osp *p)
+{
+    double *const J[3] = {s->F[O_JX], s->F[O_JY], s->F[O_JZ]};
+#ifdef _OPENMP
+    if (s->threads > 1) {
+        /* Timing aid only: the particles are split over threads, each depositing into a private
+         * copy of J that is added to the grid's J afterwards.  The sums then run in another order,
+         * so the results differ from the serial loop at FP64 rounding; the serial loop is the
+         * reference. */
+        long dropped = 0;
+#pragma omp parallel num_threads(s->threads) reduction(+ : dropped)
+        {
+            double *Jt = (double *)calloc(3 * s->ncell, sizeof(double));
+            double *const Jl[3] = {Jt, Jt + s->ncell, Jt + 2 * s->ncell};
+#pragma omp for schedule(static)
+            for (long i = 0; i < p->n; i++)
+                if (p->alive[i]) o_push_one(s, p, i, Jl, &dropped);
+#pragma omp critical
+            for (int c = 0; c < 3; c++)
+                for (long k = 0; k < s->ncell; k++) J[c][k] += Jl[c][k];
+            free(Jt);
+        }
+        s->dropped += dropped;
+        return;
+    }
+#endif
+    for (long i = 0; i < p->n; i++)
+        if (p->alive[i]) o_push_one(s, p, i, J, &s->dropped);
+}
+
+/* Threads of the particle loop (1: the serial reference loop).  Returns the number used: 1
+ * when the library was built without OpenMP. */
+int osim_set_threads(void *h, int n)
+{
+    osim *s = (osim *)h;
+#ifdef _OPENMP
+    s->threads = n > 1 ? n : 1;
+#else
+    (void)n;
+    s->threads = 1;
+#endif
+    return s->threads;
 }
 
 /* ------------------------------------------------------------------ fields */
@@ -933,7 +978,8 @@ void osim_deposit_one(void *h, double qw, const double *X0, const double *X1)
 {
     osim *s = (osim *)h;
     for (int f = O_JX; f <= O_JZ; f++) memset(s->F[f], 0, s->ncell * sizeof(double));
-    o_esirkepov(s, qw, X0, X1);
+    double *const J[3] = {s->F[O_JX], s->F[O_JY], s->F[O_JZ]};
+    o_esirkepov(s, J, &s->dropped, qw, X0, X1);
 }
 
 /* Gather of all six field components at X (unit tests of the gather alone). */
