@@ -35,18 +35,18 @@ sys.path.insert(0, ROOT)
 METRIC = "particle-steps/s (gather+push+deposit+FDTD) FP32 vs FP64 at tol; adjoint/fwd ratio"
 UNIT = "particle-steps/s"
 HBM_FALLBACK = 6800.0
-# algorithmic bytes (FP32 storage): per pushed particle r+w of cell 4 + offset 12 + momentum 12
-# plus the weight read 4; per frozen particle r+w of cell + offset; per cell E,B read by the
-# gather (24) and J written by the deposit (12)
-BYTES_PUSHED = 60.0
-BYTES_FROZEN = 36.0
+# algorithmic bytes (FP32 storage) of the particle kernel: per pushed particle r+w of cell 4 +
+# offset 12 + momentum 12 (56 B; the weight, read with the momentum, is reported apart); per
+# frozen particle r+w of cell + offset; per cell, once per step, E,B read by the gather (24) and J
+# written by the deposit (12)
+BYTES_PUSHED = 56.0
+BYTES_WEIGHT = 4.0
+BYTES_FROZEN = 32.0
 BYTES_CELL_PUSH = 36.0
-# DRAM bytes (read + write) per particle-kernel launch of the plasma buncher 128x128x512, averaged
-# over its two launches per step, from one ncu pass of dram__bytes_read.sum and
-# dram__bytes_write.sum on the full-size bench run.  None: the counters were taken on the 512-thread
-# build of the kernel (plasma electrons 4.148 GB, beam 0.235 GB per launch), and the kernel has
-# changed since (1024-thread CTAs, the pusher option), so they no longer describe it.
-TRAFFIC_PUSH_BUNCHER = None
+# DRAM bytes (read + write) of the particle kernel per step of the plasma buncher 128x128x512 (its
+# two launches: plasma electrons and beam), from one ncu capture of dram__bytes_read.sum and
+# dram__bytes_write.sum; None until the counters are taken on the kernel as built.
+TRAFFIC_PUSH_BUNCHER_STEP = None
 
 
 def peaks():
@@ -196,23 +196,196 @@ def oracle_sample(steps, warmup, seed=2):
     return value, t, sample
 
 
+def cpu_info():
+    """Host core count and CPU model (lscpu), for the CPU baseline."""
+    n = os.cpu_count() or 1
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model"):
+                v = line.split(":", 1)[1].strip()
+                if v and v != "-" and not v.isdigit():
+                    model = v
+                    break
+    except Exception:
+        pass
+    return n, model
+
+
+def oracle_buncher_sim(seed=2, grid=(32, 32, 128), n_beam=65536, threads=1):
+    import oracle
+    from paper_2411_04703_gb300 import workloads as W
+    oracle.build()
+    w = W.plasma_buncher(grid=grid, n_beam=n_beam, seed=seed)
+    o = oracle.Sim(w.grid, w.d, w.dt, w.gamma_R, bc=w.bc, pml=w.pml, order=w.order,
+                   moving_window=w.moving_window, window_v=w.window_v)
+    used = o.set_threads(threads)
+    se = o.add_species(-1.0, 1.0)
+    si = o.add_species(1.0, 1836.15267343, frozen=True)
+    sb = o.add_species(-1.0, 1.0)
+    p = w.plasma
+    o.set_plasma(se, si, p.ppc, p.xrange, p.z_nodes, p.n_nodes)
+    x, u, wt = W.sample_beam(w)
+    o.load(sb, x, u, wt, frame=0, origin=w.beam.origin)
+    return o, (se, sb), used
+
+
+def oracle_sample_threads(steps, threads):
+    """The oracle's particle loop on `threads` host threads (private J per thread), same sub-box as
+    oracle_sample: the all-core CPU figure."""
+    o, (se, sb), used = oracle_buncher_sim(threads=threads)
+    n0 = o.count(se) + o.count(sb)
+    t0 = time.perf_counter()
+    o.step(steps)
+    t = time.perf_counter() - t0
+    n1 = o.count(se) + o.count(sb)
+    return 0.5 * (n0 + n1) * steps / t, t, used
+
+
+def _rel(g, r):
+    import numpy as np
+    den = float(np.max(np.abs(r)))
+    return float(np.max(np.abs(g - r)) / den) if den > 0 else float(np.max(np.abs(g)))
+
+
+def _species_err(sim, sid, o, osid):
+    """Momentum error of matching particles (by id), max over components of max|du| / max|u_ref|."""
+    import numpy as np
+    P = sim.get_particles(sid)
+    X, U, Wt, ids = o.particles(osid)
+    common, ga, oa = np.intersect1d(P["id"], ids, return_indices=True)
+    Ug = P["u"][ga].astype(np.float64)
+    Uo = U[oa]
+    return {"matched": int(len(common)), "only_gpu": int(len(P["id"]) - len(common)),
+            "only_oracle": int(len(ids) - len(common)),
+            "u_rel_err": max(_rel(Ug[:, c], Uo[:, c]) for c in range(3)) if len(common) else 0.0}
+
+
+def fp32_vs_fp64(device, threads):
+    """Error of the FP32 CUDA path against the FP64 oracle, per result, on cases the oracle finishes
+    in seconds.  Both sides start from the same seeded lab-frame beam and plasma (each transforms
+    them itself).  (1) The reduced plasma buncher (28x26x52, TSC, PML, moving window): relative
+    field and momentum errors after 1 and 20 steps.  (2) The whole vacuum-undulator run (32x32x64,
+    65,536 beam, CIC, 200 steps): the long-run diagnostics in the boosted frame and the lab."""
+    import numpy as np
+    import oracle
+    from paper_2411_04703_gb300 import api, workloads as W
+    oracle.build()
+    names = ["Ex", "Ey", "Ez", "Bx", "By", "Bz", "Jx", "Jy", "Jz"]
+    out = {"definition": "max|gpu - oracle| / max|oracle| per field component (over the grid) and per "
+                         "momentum component (over matched particles); diagnostics |d_gpu - d_ref| / |d_ref|"}
+    w = W.mini_plasma()
+    x, u, wt = W.sample_beam(w)
+    sim, ids = api.from_workload(w, device=device, beam_arrays=(x, u, wt))
+    o = oracle.Sim(w.grid, w.d, w.dt, w.gamma_R, bc=w.bc, pml=w.pml, order=w.order,
+                   moving_window=w.moving_window, window_v=w.window_v)
+    o.set_threads(threads)
+    oid = {"plasma_e": o.add_species(-1.0, 1.0), "plasma_i": o.add_species(1.0, 1836.15267343, frozen=True)}
+    oid["beam"] = o.add_species(-1.0, 1.0)
+    p = w.plasma
+    o.set_plasma(oid["plasma_e"], oid["plasma_i"], p.ppc, p.xrange, p.z_nodes, p.n_nodes)
+    o.load(oid["beam"], x, u, wt, frame=0, origin=w.beam.origin)
+    done = 0
+    for n in (1, 20):
+        sim.step(n - done)
+        sim.sync()
+        o.step(n - done)
+        done = n
+        f = {names[c]: _rel(sim.get_field(c).astype(np.float64), o.field(c)) for c in range(9)}
+        sp = {k: _species_err(sim, ids[k], o, oid[k]) for k in ("beam", "plasma_e")}
+        out[f"{w.name}, {n} step(s)"] = {"fields": f, "species": sp}
+    sim.close()
+    del sim, o
+    w = W.vacuum_undulator()
+    x, u, wt = W.sample_beam(w)
+    sim, ids = api.from_workload(w, device=device, beam_arrays=(x, u, wt))
+    o = oracle.Sim(w.grid, w.d, w.dt, w.gamma_R, bc=w.bc, order=w.order)
+    o.set_threads(threads)
+    o.set_external(w.undulator.K, w.undulator.lambda_u)
+    sb = o.add_species(-1.0, 1.0)
+    o.load(sb, x, u, wt, frame=0, origin=w.beam.origin, match_undulator=True)
+    sim.step(w.steps)
+    sim.sync()
+    o.step(w.steps)
+    un = w.undulator
+    k_lab = api.resonant_wavenumber(un.lambda_u, un.K, w.beam.gamma)
+    k_rrf = api.rrf_resonant_wavenumber(w)
+    diag = {}
+    for frame, oframe, k, tag in [(api.PIC_FRAME_BOOSTED, 0, k_rrf, "boosted"), (api.PIC_FRAME_LAB, 1, k_lab, "lab")]:
+        mg = sim.get_moments(ids["beam"], frame, k_bunch=k)
+        mo = o.moments(sb, frame=oframe, k=k)
+        for key in ("bunching", "emit_nx", "emit_ny", "rel_energy_spread"):
+            diag[f"{key} ({tag})"] = {"gpu": mg[key], "oracle": mo[key],
+                                      "rel_err": abs(mg[key] - mo[key]) / max(abs(mo[key]), 1e-300)}
+    out[f"{w.name}, whole run ({w.steps} steps)"] = diag
+    sim.close()
+    return out
+
+
+def adjoint_block(device, steps=100, every=50):
+    """Adjoint/forward cost of the differentiated run (64x64x256, 2M beam + 4 ppc plasma, CIC):
+    `steps` forward steps recording checkpoints every `every`, then pic_backward (segment
+    recompute with per-step records + the adjoint sweep), both timed with CUDA events."""
+    import torch
+    from paper_2411_04703_gb300 import api, workloads as W
+    w = W.adjoint_workload()
+    sim, ids = api.from_workload(w, device=device)
+    sim.step(3)
+    sim.sync()
+    sim.checkpoint(every)
+    stream = sim.stream
+    torch.cuda.synchronize()
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    e0.record(stream)
+    sim.step(steps)
+    e1.record(stream)
+    g = sim.backward(ids["beam"], api.rrf_resonant_wavenumber(w))
+    e2.record(stream)
+    torch.cuda.synchronize()
+    fwd, bwd = e0.elapsed_time(e1), e1.elapsed_time(e2)
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+    return {"workload": w.name, "steps": steps, "checkpoint_every": every,
+            "forward_ms_per_step": fwd / steps, "backward_ms_per_step": bwd / steps, "ratio": bwd / fwd,
+            "includes": "backward = segment recompute with per-step records + adjoint sweep",
+            "loss": g["loss"], "dL_dK": g["dL_dK"]}
+
+
 def run_reference(args):
+    """The reference arm: the FP64 oracle, as it stands, on the host cores (its particle loop on
+    all of them), each step a step of the 32x32x128 sub-box of the plasma buncher."""
     rank, world, _ = env_rank()
     if rank != 0:
         return 0
     from paper_2411_04703_gb300 import workloads as W
     full = W.plasma_buncher()            # the workload the default arm measures (its config)
     steps = args.steps
-    value, t, sample = oracle_sample(steps, args.warmup)
+    ncores, model = cpu_info()
+    o, (se, sb), used = oracle_buncher_sim(threads=ncores)
+    if args.warmup:
+        o.step(args.warmup)
+    n0 = o.count(se) + o.count(sb)
+    t0 = time.perf_counter()
+    o.step(steps)
+    t = time.perf_counter() - t0
+    n1 = o.count(se) + o.count(sb)
+    value = 0.5 * (n0 + n1) * steps / t
+    sample = (f"FP64 oracle, 32x32x128 sub-box of the plasma buncher (8 ppc plasma + frozen ions, "
+              f"{o.count(sb)} beam), {steps} steps after {args.warmup} warm-up, particle loop on {used} host "
+              f"thread(s) (OpenMP, a private J per thread)")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t / steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": full.name, "grid": list(full.grid), "shape": "TSC",
-                   "boundaries": "transverse CPML 10 cells, moving window",
-                   "sample": sample},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "config": {"workload": full.name, "grid": [32, 32, 128], "target_grid": list(full.grid), "shape": "TSC",
+                   "boundaries": "transverse CPML 10 cells, moving window", "sample": sample,
+                   "note": "value is per particle-step on the 32x32x128 sub-box (same cells, densities, "
+                           "particles per cell, boundaries and window), not a run of the full grid"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle", "sample": sample,
+                         "cpu_model": model, "nproc": ncores},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -339,6 +512,8 @@ def run_gbpic(args):
         if grid != (128, 128, 512):
             w.name = f"plasma buncher {grid[0]}x{grid[1]}x{grid[2]} (reduced), {nb} beam + 8 ppc plasma, TSC"
         beam = W.sample_beam(w)
+        if args.tile:
+            w.tile = tuple(int(v) for v in args.tile.split(","))
         if args.sort_every:
             w.sort_every = args.sort_every
         elif args.autotune:
@@ -367,6 +542,7 @@ def run_gbpic(args):
     clocks.start()
     barrier()
     torch.cuda.synchronize()
+    shifts0 = sim.get_time()[1]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     sim.step(args.steps)
@@ -375,6 +551,7 @@ def run_gbpic(args):
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
+    shifts_timed = sim.get_time()[1] - shifts0
     ms = e0.elapsed_time(e1)
     n1 = sum(sim.get_count(s) for s in pushed)
     frozen1 = sim.get_count(ids["plasma_i"]) if "plasma_i" in ids else 0
@@ -389,39 +566,50 @@ def run_gbpic(args):
     psteps_all, ms_max = aggregate(psteps, ms, world, dev)
     value = psteps_all / (ms_max / 1000.0)
 
-    # roofline of the dominant kernel class (live CUDA-event trace of the timed region)
+    # roofline of the dominant kernel class (live CUDA-event trace of the timed region): the
+    # algorithmic bytes of one step's launches of that class over their CUDA-event time per step
     hbm, peak_kind = peaks()
     ncell = ncell_total
     n_beam = sim.get_count(ids["beam"])
     n_e = 0.5 * (n0 + n1) - n_beam
     classes = tr["ms"]
+    steps_traced = args.steps      # the traced pass (the timed region, or the pass after it) has K steps
     dom = max(("push", "push_frozen", "fields", "sort"), key=lambda k: classes[k])
     shape = "CIC" if w.order == 1 else "TSC"
+    launches = tr["events"][dom]
     if dom == "push":
-        # one launch per mobile species per step; each reads E, B of the grid and writes J once
-        launches = tr["events"]["push"]
-        per_step = max(1, round(launches / args.steps))
-        bytes_per = ((n_e + n_beam) * BYTES_PUSHED + per_step * ncell * BYTES_CELL_PUSH) / per_step
+        # one launch per mobile species per step; the grid term (E, B read once, J written once)
+        # is counted once per step, not once per species launch
+        bytes_step = (n_e + n_beam) * BYTES_PUSHED + ncell * BYTES_CELL_PUSH
+        units = {"pushed_particles": int(round(n_e + n_beam)), "cells": int(ncell),
+                 "bytes_per_pushed_particle": BYTES_PUSHED, "bytes_per_cell": BYTES_CELL_PUSH,
+                 "weight_read_bytes_not_counted": BYTES_WEIGHT * (n_e + n_beam)}
     elif dom == "push_frozen":
-        launches = tr["events"]["push_frozen"]
-        bytes_per = 0.5 * (frozen0 + frozen1) * BYTES_FROZEN + ncell * 12.0
+        bytes_step = 0.5 * (frozen0 + frozen1) * BYTES_FROZEN + ncell * 12.0
+        units = {"frozen_particles": int(0.5 * (frozen0 + frozen1)), "cells": int(ncell)}
     elif dom == "fields":
-        launches = tr["events"]["fields"]
-        bytes_per = ncell * (36.0 + 48.0 + 36.0)
+        bytes_step = ncell * (36.0 + 48.0 + 36.0)
+        units = {"cells": int(ncell), "bytes_per_cell": 120.0}
     else:
-        launches = tr["events"]["sort"]
-        bytes_per = 3 * (n0 + frozen0) * 36.0
-    avg_ms = classes[dom] / max(launches, 1)
-    achieved = bytes_per / (avg_ms / 1000.0) / 1e9
-    traffic = TRAFFIC_PUSH_BUNCHER if (dom == "push" and args.workload == "buncher" and w.grid == (128, 128, 512)) else None
+        bytes_step = 3 * (n0 + frozen0) * 36.0
+        units = {"particles": int(n0 + frozen0)}
+    ms_step = classes[dom] / steps_traced
+    achieved = bytes_step / (ms_step / 1000.0) / 1e9
+    traffic = None
+    if dom == "push" and args.workload == "buncher" and w.grid == (128, 128, 512):
+        traffic = TRAFFIC_PUSH_BUNCHER_STEP
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": traffic,
                 "kernel": {"push": f"k_push<{shape}, mobile> (" + " + ".join(k for k in ("beam", "plasma_e") if k in ids) + ")",
                            "push_frozen": f"k_lattice / k_push<{shape}, frozen> (ions)", "fields": "k_fdtd_b/e",
                            "sort": "tile sort"}[dom],
+                "per": "step (all launches of the kernel in one step)",
+                "launches_per_step": launches / max(steps_traced, 1),
+                "avg_launch_ms": classes[dom] / max(launches, 1),
+                "ms_per_step": ms_step,
+                "algorithmic_bytes_per_step": bytes_step,
+                "units": units,
                 "peak_kind": f"{peak_kind} (hbm_gbs)",
-                "avg_launch_ms": avg_ms,
-                "algorithmic_bytes_per_launch": bytes_per,
                 "time_share": {k: v / max(sum(classes.values()), 1e-9) for k, v in classes.items() if v > 0}}
     sim.close()
     del sim
@@ -467,15 +655,30 @@ def run_gbpic(args):
         del sim2
         torch.cuda.empty_cache()
 
+    adjoint = None
+    if rank == 0 and world == 1 and args.workload == "buncher" and not args.no_adjoint:
+        adjoint = adjoint_block(local)
+
     cpu = None
+    accuracy = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ncores, model = cpu_info()
         if args.workload == "vacuum":
             cv, ct, sample = oracle_sample_vacuum(20, 0)
         elif ens is not None:
             cv, ct, sample = oracle_sample_ensemble(2, 0)
         else:
             cv, ct, sample = oracle_sample(3, 0)
-        cpu = {"value": cv, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+        cpu = {"value": cv, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+               "cpu_model": model, "nproc": ncores}
+        if args.workload == "buncher":
+            av, at, used = oracle_sample_threads(10, ncores)
+            cpu["all_cores"] = {"value": av, "unit": UNIT, "cores": used, "seconds": at,
+                                "sample": "the same sub-box, 10 steps, the particle loop on all host cores "
+                                          "(OpenMP, a private J per thread)"}
+            # the FP32 path's error against the FP64 oracle, per result (this leg is where bench.py
+            # runs the oracle)
+            accuracy = fp32_vs_fp64(local, ncores)
 
     if rank == 0:
         line = {
@@ -488,8 +691,10 @@ def run_gbpic(args):
                        "tile": list(w.tile), "sort_every": tuned if tuned else w.sort_every,
                        "sort_every_from": "autotuner" if tuned else "workload",
                        "l2": l2,
+                       "window_shifts_in_timed_region": int(shifts_timed),
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+            "fp32_vs_fp64": accuracy, "adjoint": adjoint,
             "gpu_launches": int(kernels_timed if kernels_timed is not None else tr["kernels"]),
             "cuda_graphs": bool(graphs),
             "fallback_deposits": int(tr.get("fallback", 0)),
@@ -503,15 +708,18 @@ def run_gbpic(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["gbpic", "reference"], default="gbpic")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true",
+                    help="skip the oracle leg (CPU timing and the FP32-vs-FP64 accuracy block)")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward block")
     ap.add_argument("--grid", default="128,128,512",
                     help="plasma-buncher grid (a smaller one, e.g. 64,64,128, for profiling captures)")
     ap.add_argument("--beam", type=int, default=0, help="beam macroparticles (0: scaled with the grid)")
     ap.add_argument("--sort-every", type=int, default=0, help="steps between tile sorts (0: the workload's)")
+    ap.add_argument("--tile", default="", help="buncher: tile size in cells, e.g. 8,4,4 (default: the workload's)")
     ap.add_argument("--runs", type=int, default=64, help="ensemble runs (the batched sweep has 64)")
     ap.add_argument("--no-autotune", action="store_true", help="ensemble: keep the workload's sort cadence")
     ap.add_argument("--autotune", action="store_true",
