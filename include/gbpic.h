@@ -315,19 +315,26 @@ int pic_trace_read(pic_ctx *ctx, pic_trace *out);
 /* Allocation-free counting sort of caller-owned arrays, for callers that cannot let a library
  * allocate device memory (an application that reserves its whole device budget in its own
  * pool at start-up and forbids allocations afterwards, or code running where the CUDA
- * allocator must not be entered).  The paper has no counterpart: it is a variant of the tile
- * sort that pic_step runs internally.  cells: device int32[n], packed cell indices
- * i | j << 10 | k << 20 (-1 or a cell outside the grid = dummy, dropped); grid, tile: host int[3] (grid <= 1024 x 1024 x
- * 2048, 1 <= tile <= grid); order: device int32[n], receives at sorted position q the index of
- * the input element placed there (live elements only, ascending tile-major key: tiles x-fastest,
- * cells in a tile x-fastest; order among equal keys unspecified); key_start: device
- * int32[n_keys + 1] with n_keys = (tiles per dim product) * tile cells, receives the exclusive
- * start of each key (key_start[n_keys] = number of live elements); stream: cudaStream_t or NULL.
+ * allocator must not be entered).  The paper has no counterpart: it is a tile counting sort like
+ * the one pic_step runs internally, but with its own key (below; pic_step's internal key orders
+ * the cells of a tile differently and adds the offset's octant).  cells: device int32[n], packed
+ * cell indices i | j << 10 | k << 20 (-1 or a cell outside the grid = dummy, dropped); grid,
+ * tile: host int[3] (grid <= 1024 x 1024 x 2048, 1 <= tile <= grid); order: device int32[n],
+ * receives at sorted position q the index of the input element placed there (live elements
+ * only, ascending key; order among equal keys unspecified).  The key of cell (i, j, k) with
+ * nt_d = ceil(grid_d / tile_d) tiles per dim is
+ *   key = ((k / T_z) nt_y + j / T_y) nt_x + i / T_x) * (T_x T_y T_z)
+ *         + ((k % T_z) T_y + j % T_y) T_x + i % T_x,
+ * i.e. tiles x-fastest, then the cells of a tile x-fastest.  key_start: device int32[n_keys + 1]
+ * with n_keys = nt_x nt_y nt_z T_x T_y T_z, receives the exclusive start of each key
+ * (key_start[n_keys] = number of live elements); stream: cudaStream_t or NULL.
  * Limits: n <= PIC_NOALLOC_MAX_N, n_keys <= PIC_NOALLOC_MAX_KEYS; larger sizes return
  * PIC_ERR_ARG with a message in pic_last_error(NULL).  Scratch comes from a fixed device array
  * inside the library (about 4 MB per GPU that loads the library, held until the process
  * exits); the first call on each device looks up its address (with that device current), so
- * make the first call before any stream capture.  It calls no cudaMalloc/cudaFree.  All calls
+ * make the first call before any stream capture.  The address found then is kept for the life of
+ * the process: it belongs to the device's primary context, so do not call this entry point after
+ * a cudaDeviceReset of that device or with another (non-primary) context current.  It calls no cudaMalloc/cudaFree.  All calls
  * share that scratch: calls whose work overlaps on the GPU race and give wrong results.
  * Asynchronous on `stream`. */
 #define PIC_NOALLOC_MAX_N (1 << 20)

@@ -166,12 +166,14 @@ extern "C" int pic_tile_sort_noalloc(const int32_t *cells, int64_t n, const int 
         t.nt[d] = (grid[d] + tile[d] - 1) / tile[d];
         ntiles *= t.nt[d];
     }
-    t.tile_cells = tile[0] * tile[1] * tile[2];
-    const int64_t n_keys = ntiles * t.tile_cells;
-    t.n_keys = (int)std::min<int64_t>(n_keys, kNaMaxKeys);
-    if (n_keys > kNaMaxKeys)
+    // sizes in 64-bit: a tile as large as the grid's limits has more cells than an int holds
+    const int64_t tile_cells = (int64_t)tile[0] * tile[1] * tile[2];
+    const int64_t n_keys = ntiles * tile_cells;
+    if (n_keys <= 0 || n_keys > kNaMaxKeys)
         return na_fail(PIC_ERR_ARG, "pic_tile_sort_noalloc: " + std::to_string(n_keys) + " keys exceed the maximum " +
                                         std::to_string(kNaMaxKeys));
+    t.tile_cells = (int)tile_cells;
+    t.n_keys = (int)n_keys;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return na_fail(PIC_ERR_CUDA, "pic_tile_sort_noalloc: no current device");
     int *scratch = nullptr;

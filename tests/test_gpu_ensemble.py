@@ -118,11 +118,16 @@ def test_ensemble_whole_run_tracks_oracle_per_run():
         sb = o.add_species(-1.0, 1.0, capacity=x.shape[1])
         o.load(sb, x, u, wt, frame=oracle.LAB, origin=w.beam.origin, match_undulator=True)
         o.step(w.steps)
+        # bunching at the run's own resonant wavenumber (its K) in each frame
+        un = w.undulator
+        kb = {api.PIC_FRAME_BOOSTED: api.resonant_wavenumber(un.lambda_u, un.K, w.beam.gamma, w.gamma_R,
+                                                             api.PIC_FRAME_BOOSTED),
+              api.PIC_FRAME_LAB: api.resonant_wavenumber(un.lambda_u, un.K, w.beam.gamma)}
         for frame, oframe in ((api.PIC_FRAME_BOOSTED, 0), (api.PIC_FRAME_LAB, 1)):
-            mg = sim.get_moments_run(ids["beam"], r, frame, k_bunch=1.0)
-            mo = o.moments(sb, frame=oframe, k=1.0)
+            mg = sim.get_moments_run(ids["beam"], r, frame, k_bunch=kb[frame])
+            mo = o.moments(sb, frame=oframe, k=kb[frame])
             assert mg["count"] == mo["count"]
-            for key in ("emit_nx", "emit_ny", "rel_energy_spread", "mean_gamma", "rms_z", "mean_z"):
+            for key in ("emit_nx", "emit_ny", "rel_energy_spread", "mean_gamma", "rms_z", "mean_z", "bunching"):
                 assert mg[key] == pytest.approx(mo[key], rel=1e-3), (r, frame, key)
         assert sim.get_moments_run(ids["plasma_e"], r)["count"] == o.count(se)
 

@@ -57,3 +57,40 @@ def test_vacuum_undulator_200_steps_diagnostics_track_oracle():
     assert mo_b["count"] == w.beam.n
     # the fields the beam radiated agree too (whole-grid energy)
     assert sim.get_moments(ids["beam"])["field_energy"] == pytest.approx(o.moments(s)["field_energy"], rel=TOL_DIAG)
+
+
+def test_plasma_buncher_300_steps_diagnostics_track_oracle():
+    # The plasma-buncher physics (boost 20, lab gamma 400 beam in a cold lab-static plasma with
+    # frozen neutralising ions, TSC, transverse CPML, moving window with plasma injection) on the
+    # oracle-sized grid 28 x 26 x 52 (5 um longitudinal cells: the window shifts ~50 times in 300
+    # steps).  Both sides load the same seeded lab beam and fill the same plasma lattice; after 300
+    # steps the beam's bunching (at the plasma wavenumber of the normalised units, k = 1, and at
+    # twice it), emittances and energy spread agree to 1e-3 in both frames, and the plasma
+    # electron count is exact.
+    import os
+    w = W.mini_plasma(steps=300)
+    x, u, wt = W.sample_beam(w)
+    sim, ids = api.from_workload(w, beam_arrays=(x, u, wt))
+    o = oracle.Sim(w.grid, w.d, w.dt, w.gamma_R, bc=w.bc, pml=w.pml, order=w.order,
+                   moving_window=w.moving_window, window_v=w.window_v)
+    o.set_threads(os.cpu_count() or 1)
+    se = o.add_species(-1.0, 1.0)
+    si = o.add_species(1.0, 1836.15267343, frozen=True)
+    sb = o.add_species(-1.0, 1.0, capacity=x.shape[1])
+    p = w.plasma
+    o.set_plasma(se, si, p.ppc, p.xrange, p.z_nodes, p.n_nodes)
+    o.load(sb, x, u, wt, frame=oracle.LAB, origin=w.beam.origin)
+    sim.step(w.steps)
+    sim.sync()
+    o.step(w.steps)
+    assert sim.get_time() == o.time()
+    assert sim.get_time()[1] >= 40          # the window moved through the plasma
+    assert sim.get_count(ids["plasma_e"]) == o.count(se)
+    for frame, oframe in ((api.PIC_FRAME_BOOSTED, 0), (api.PIC_FRAME_LAB, 1)):
+        for k in (1.0, 2.0):
+            mg = sim.get_moments(ids["beam"], frame, k_bunch=k)
+            mo = o.moments(sb, frame=oframe, k=k)
+            assert mg["count"] == mo["count"]
+            for key in ("bunching", "emit_nx", "emit_ny", "rel_energy_spread"):
+                assert mg[key] == pytest.approx(mo[key], rel=TOL_DIAG), (frame, k, key, mg[key], mo[key])
+    sim.close()

@@ -153,6 +153,50 @@ def test_whole_run_tracks_oracle(case):
                 assert mg[key] == pytest.approx(mo[key], rel=1e-3), (frame, key)
 
 
+PML_CASES = ["plasma_tsc_pml_window", "long_undulator_tsc_pml_ramp"]
+
+
+@pytest.mark.parametrize("case", PML_CASES)
+def test_cpml_layers_track_oracle_over_steps(case):
+    # Random fields everywhere, the absorbing layers included, and auxiliary CPML state zero on
+    # both sides: after the first step the layers' psi is nonzero, so steps 2 and 3 exercise the
+    # b psi recursion term.  All nodes of E and B, layers included, are compared after 3 steps at
+    # the per-step tolerance (three steps of FP32 rounding stay well inside it), and after 20 steps
+    # within 1e-4 (FP32 drift of the fields and particles over 20 steps).
+    w = CASES[case]()
+    sim, ids = api.from_workload(w)
+    random_fields(sim, w, seed=101)
+    o, oid = parity.oracle_from_gpu(w, sim, ids)
+    sim.step(3)
+    sim.sync()
+    o.step(3)
+    f = parity.compare_fields(sim, o)
+    for k in ["Ex", "Ey", "Ez", "Bx", "By", "Bz"]:
+        assert f[k] < TOL_STEP, (3, k, f)
+    # the layers' own nodes: the first/last pml cells of each absorbing dim
+    n = w.pml
+    for c in range(6):
+        g = sim.get_field(c).astype(np.float64)
+        r = o.field(c)
+        for dd, axis in ((0, 2), (1, 1), (2, 0)):
+            if w.bc[dd][0] != W.PML:
+                continue
+            sl_lo = [slice(None)] * 3
+            sl_hi = [slice(None)] * 3
+            sl_lo[axis] = slice(0, n)
+            sl_hi[axis] = slice(w.grid[dd] - n, w.grid[dd])
+            for sl in (tuple(sl_lo), tuple(sl_hi)):
+                den = np.max(np.abs(r))
+                assert np.max(np.abs(g[sl] - r[sl])) < TOL_STEP * den, (c, dd)
+                assert np.max(np.abs(r[sl])) > 1e-3 * den      # the layers hold field
+    sim.step(17)
+    sim.sync()
+    o.step(17)
+    f = parity.compare_fields(sim, o)
+    for k in ["Ex", "Ey", "Ez", "Bx", "By", "Bz"]:
+        assert f[k] < 1e-4, (20, k, f)
+
+
 def test_moments_from_identical_state_match_fp64():
     w = W.mini_vacuum(order=2)
     sim, ids = api.from_workload(w)

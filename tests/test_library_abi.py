@@ -165,6 +165,9 @@ def test_noalloc_sort_rejects_out_of_range_sizes_before_any_device_work():
         ((fake, (1 << 20) + 1, g, t, fake, fake), "exceeds the maximum"),
         ((fake, 10, g, (ctypes.c_int * 3)(8, 128, 8), fake, fake), "out of range"),
         ((fake, 10, (ctypes.c_int * 3)(1024, 1024, 8), (ctypes.c_int * 3)(1, 1, 1), fake, fake), "keys exceed"),
+        # one tile as large as the grid limits: 2^31 cells, more than an int holds
+        ((fake, 10, (ctypes.c_int * 3)(1024, 1024, 2048), (ctypes.c_int * 3)(1024, 1024, 2048), fake, fake),
+         "keys exceed"),
     ]
     for (cells, n, grid, tile, order, key_start), words in cases:
         r = S(cells, n, grid, tile, order, key_start, None)

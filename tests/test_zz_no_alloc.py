@@ -86,6 +86,72 @@ def test_noalloc_sort_matches_context_sort_on_two_calls():
         sim.close()
 
 
+def _call(fn, packed, n, grid, tile, n_keys):
+    import torch
+    order = torch.full((max(n, 1),), -7, dtype=torch.int32, device="cuda")
+    key_start = torch.full((n_keys + 1,), -7, dtype=torch.int32, device="cuda")
+    g3, t3 = (C.c_int * 3)(*grid), (C.c_int * 3)(*tile)
+    r = fn(packed.data_ptr(), n, g3, t3, order.data_ptr(), key_start.data_ptr(),
+           torch.cuda.current_stream().cuda_stream)
+    assert r == 0, api.lib().pic_last_error(None)
+    torch.cuda.synchronize()
+    return order.cpu().numpy(), key_start.cpu().numpy()
+
+
+def test_noalloc_sort_drops_dummies_and_cells_outside_the_grid():
+    # -1 and packed cells beyond the grid in each dim are dropped: key_start ends at the live
+    # count and order holds exactly the live input indices, grouped by key as the documented
+    # key says (numpy bincount / cumsum of the same keys)
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    fn = _noalloc_fn()
+    grid, tile = (20, 18, 44), (8, 4, 8)
+    rng = np.random.default_rng(31)
+    n = 30000
+    c = np.stack([rng.integers(0, g, n) for g in grid], 1)
+    packed = c[:, 0] | (c[:, 1] << 10) | (c[:, 2] << 20)
+    kind = rng.integers(0, 8, n)
+    packed = np.where(kind == 0, -1, packed)
+    packed = np.where(kind == 1, (grid[0] + rng.integers(0, 1024 - grid[0], n)) | (c[:, 1] << 10) | (c[:, 2] << 20), packed)
+    packed = np.where(kind == 2, c[:, 0] | ((grid[1] + rng.integers(0, 1024 - grid[1], n)) << 10) | (c[:, 2] << 20), packed)
+    packed = np.where(kind == 3, c[:, 0] | (c[:, 1] << 10) | ((grid[2] + rng.integers(0, 64, n)) << 20), packed)
+    live = kind >= 4
+    nt = [(g + t - 1) // t for g, t in zip(grid, tile)]
+    n_keys = nt[0] * nt[1] * nt[2] * tile[0] * tile[1] * tile[2]
+    for call in range(2):           # the second call finds the first call's scratch
+        o, ks = _call(fn, torch.tensor(packed, dtype=torch.int32, device="cuda"), n, grid, tile, n_keys)
+        keys = _keys(c[live], grid, tile)
+        expect = np.concatenate([[0], np.cumsum(np.bincount(keys, minlength=n_keys))])
+        assert np.array_equal(ks, expect), call
+        assert ks[-1] == int(live.sum())
+        got = o[:ks[-1]]
+        assert sorted(got.tolist()) == np.flatnonzero(live).tolist()
+        assert np.array_equal(_keys(c[got], grid, tile), np.sort(keys))
+
+
+def test_noalloc_sort_at_the_largest_key_count():
+    # n_keys = PIC_NOALLOC_MAX_KEYS = 2^22 (256 x 128 x 128 cells, one cell per tile): the scan of
+    # the 2^22 + 1 counters takes three levels, with its block sums at the scratch's bound
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    fn = _noalloc_fn()
+    grid, tile = (256, 128, 128), (1, 1, 1)
+    n_keys = 256 * 128 * 128
+    assert n_keys == 1 << 22
+    rng = np.random.default_rng(32)
+    n = 1 << 20
+    c = np.stack([rng.integers(0, g, n) for g in grid], 1)
+    packed = torch.tensor(c[:, 0] | (c[:, 1] << 10) | (c[:, 2] << 20), dtype=torch.int32, device="cuda")
+    o, ks = _call(fn, packed, n, grid, tile, n_keys)
+    keys = _keys(c, grid, tile)
+    expect = np.concatenate([[0], np.cumsum(np.bincount(keys, minlength=n_keys))])
+    assert np.array_equal(ks, expect)
+    assert np.array_equal(np.sort(o), np.arange(n))
+    assert np.all(np.diff(keys[o]) >= 0)
+
+
 def test_noalloc_sort_rejects_sizes_beyond_its_maximum():
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
