@@ -52,7 +52,7 @@ enum { PIC_FRAME_LAB = 0, PIC_FRAME_BOOSTED = 1 };
 enum {
     PIC_EX = 0, PIC_EY, PIC_EZ, PIC_BX, PIC_BY, PIC_BZ, PIC_JX, PIC_JY, PIC_JZ, PIC_RHO
 };
-enum { PIC_EXT_NONE = 0, PIC_EXT_PLANAR_UNDULATOR = 1 };
+enum { PIC_EXT_NONE = 0, PIC_EXT_PLANAR_UNDULATOR = 1, PIC_EXT_PLANAR_UNDULATOR_3D = 2 };
 enum { PIC_PUSHER_BORIS = 0, PIC_PUSHER_VAY = 1 };
 
 typedef struct pic_ctx pic_ctx;
@@ -162,7 +162,14 @@ int pic_load_species_batch(pic_ctx *ctx, const pic_species *sp, const int64_t *n
  * z_start = -inf: f = 1 everywhere.  In the RRF the element moves at -c beta_R (Eq. Vprime):
  * the particle at RRF z', t' sees lab z = gamma_R (z' + beta_R t') and Eq. M1-M4 give
  * B'_y = gamma_R B_y, E'_x = -beta_R B'_y.  Evaluated analytically at each particle, added to
- * the gathered self fields.  lambda_u, z_start, ramp_len: lab, normalised. */
+ * the gathered self fields.  lambda_u, z_start, ramp_len: lab, normalised.
+ * PIC_EXT_PLANAR_UNDULATOR_3D: the same element with the transverse dependence of a planar
+ * undulator's vacuum field (poles above and below in y), B_y = B0 f(z) cosh(k_u y) cos(k_u z +
+ * phase), B_z = -B0 f(z) sinh(k_u y) sin(k_u z + phase) (divergence- and curl-free where f = 1),
+ * y measured from the undulator axis, which is the grid's y mid-plane (y = ny dy / 2).  The
+ * longitudinal component is unchanged by the boost (Eq. M1-M4: B'_z = B_z); B'_y and E'_x as
+ * above.  A matched load (match_undulator) then uses A_x = (B0/k_u) cosh(k_u y) sin(k_u z +
+ * phase).  The adjoint (pic_checkpoint) supports PIC_EXT_PLANAR_UNDULATOR only. */
 typedef struct {
     int type;
     double K, lambda_u, phase, z_start, ramp_len;

@@ -79,8 +79,8 @@ def lib():
                 "osim_set_field": (None, [vp, i, pd]),
                 "osim_get_field": (None, [vp, i, pd]),
                 "osim_set_external": (None, [vp, i, d, d, d, d, d]),
-                "osim_external_at": (None, [vp, d, d, pd, pd]),
-                "osim_undulator_Ax": (d, [vp, d]),
+                "osim_external_at": (None, [vp, d, d, d, pd, pd]),
+                "osim_undulator_Ax": (d, [vp, d, d]),
                 "osim_set_plasma": (None, [vp, i, i, pi, pi, i, pd, pd, i]),
                 "osim_step": (None, [vp, l]),
                 "osim_fdtd": (None, [vp]),
@@ -278,13 +278,14 @@ class Sim:
         self.L.osim_set_external(self.h, int(kind), float(K), float(lambda_u), float(phase),
                                  float(z_start), float(ramp))
 
-    def external_at(self, zp, tp):
+    def external_at(self, zp, tp, y=0.0):
+        """RRF external field at RRF z' (absolute), time t' and y from the undulator axis."""
         E, B = np.zeros(3), np.zeros(3)
-        self.L.osim_external_at(self.h, float(zp), float(tp), _pd(E), _pd(B))
+        self.L.osim_external_at(self.h, float(y), float(zp), float(tp), _pd(E), _pd(B))
         return E, B
 
-    def undulator_Ax(self, zlab):
-        return self.L.osim_undulator_Ax(self.h, float(zlab))
+    def undulator_Ax(self, zlab, y=0.0):
+        return self.L.osim_undulator_Ax(self.h, float(y), float(zlab))
 
     def set_plasma(self, sp_e, sp_i, ppc, xrange, z_nodes, n_nodes, fill=True):
         ppc = np.ascontiguousarray(ppc, np.int32)

@@ -269,10 +269,9 @@ void oracle_field_transform(const double E[3], const double B[3], double beta,
     }
 }
 
-/* Planar-undulator lab field B_y = B0 f(z) cos(k_u z + phi0); f is a linear entrance
- * ramp ("gentle slope", Sec. "Electron propagation"), 0 before z_start, 1 after
- * z_start + ramp (ramp <= 0: field everywhere). */
-static double o_undulator_lab_By(const osim *s, double zlab)
+/* Entrance ramp f(z) of the undulator: linear ("gentle slope", Sec. "Electron propagation"),
+ * 0 before z_start, 1 after z_start + ramp (ramp < 0: field everywhere; ramp = 0: a step). */
+static double o_ramp(const osim *s, double zlab)
 {
     double f = 1.0;
     if (s->ramp > 0.0) {
@@ -281,20 +280,42 @@ static double o_undulator_lab_By(const osim *s, double zlab)
     } else if (s->ramp == 0.0 && isfinite(s->z_start)) {
         f = zlab >= s->z_start ? 1.0 : 0.0;
     }
-    return s->B0 * f * cos(s->ku * zlab + s->phase0);
+    return f;
 }
 
-/* External field at RRF absolute position z' (normalised length) and time t':
- * the static lab element sits at lab z = gR (z' + bR t') (it moves at -c bR in the
- * RRF, Eq. Vprime; inverse of Eq. Lor1-Lor2) and is transformed with Eq. M1-M4. */
-static void o_external(const osim *s, double zp, double tp, double E[3], double B[3])
+/* Planar-undulator lab field at lab (y, z): type 1, the ideal on-axis form B_y = B0 f(z)
+ * cos(k_u z + phi0); type 2, the vacuum field of a planar undulator with poles above and below
+ * in y: B_y = B0 f cosh(k_u y) cos(k_u z + phi0), B_z = -B0 f sinh(k_u y) sin(k_u z + phi0)
+ * (div B = curl B = 0 where f = 1), y measured from the undulator axis. */
+static void o_undulator_lab_B(const osim *s, double y, double zlab, double Bl[3])
+{
+    double a = s->B0 * o_ramp(s, zlab), ph = s->ku * zlab + s->phase0;
+    Bl[0] = 0.0;
+    if (s->ext == 2) {
+        Bl[1] = a * cosh(s->ku * y) * cos(ph);
+        Bl[2] = -a * sinh(s->ku * y) * sin(ph);
+    } else {
+        Bl[1] = a * cos(ph);
+        Bl[2] = 0.0;
+    }
+}
+
+/* External field at RRF absolute position (y, z') (normalised length; y from the undulator
+ * axis, which the transverse boost leaves unchanged) and time t': the static lab element sits
+ * at lab z = gR (z' + bR t') (it moves at -c bR in the RRF, Eq. Vprime; inverse of Eq.
+ * Lor1-Lor2) and is transformed with Eq. M1-M4. */
+static void o_external(const osim *s, double y, double zp, double tp, double E[3], double B[3])
 {
     E[0] = E[1] = E[2] = B[0] = B[1] = B[2] = 0.0;
     if (!s->ext) return;
     double zlab = s->gR * (zp + s->bR * tp);
-    double El[3] = {0, 0, 0}, Bl[3] = {0, o_undulator_lab_By(s, zlab), 0};
+    double El[3] = {0, 0, 0}, Bl[3];
+    o_undulator_lab_B(s, y, zlab, Bl);
     oracle_field_transform(El, Bl, s->bR, E, B);
 }
+
+/* The undulator axis: the grid's y mid-plane. */
+static double o_axis_y(const osim *s) { return 0.5 * s->n[1] * s->d[1]; }
 
 void osim_set_external(void *h, int type, double K, double lambda_u, double phase,
                        double z_start, double ramp)
@@ -312,19 +333,21 @@ void osim_set_external(void *h, int type, double K, double lambda_u, double phas
 
 void osim_set_pusher(void *h, int pusher) { ((osim *)h)->pusher = pusher; }
 
-void osim_external_at(void *h, double zp, double tp, double *E, double *B)
+void osim_external_at(void *h, double y, double zp, double tp, double *E, double *B)
 {
-    o_external((osim *)h, zp, tp, E, B);
+    o_external((osim *)h, y, zp, tp, E, B);
 }
 
-/* Undulator vector potential a(z') at t' = 0 without ramp: A_x = (B0/k_u) sin(k_u z + phi0),
- * a Lorentz-invariant transverse component; dA_x/dz_lab = B_y. */
-static double o_undulator_Ax(const osim *s, double zlab)
+/* Undulator vector potential at lab (y, z) without ramp: A_x = (B0/k_u) sin(k_u z + phi0)
+ * (type 1), times cosh(k_u y) for the type-2 field, a Lorentz-invariant transverse component
+ * with B_y = dA_x/dz_lab and B_z = -dA_x/dy. */
+static double o_undulator_Ax(const osim *s, double y, double zlab)
 {
-    return s->B0 / s->ku * sin(s->ku * zlab + s->phase0);
+    double a = s->B0 / s->ku * sin(s->ku * zlab + s->phase0);
+    return s->ext == 2 ? a * cosh(s->ku * y) : a;
 }
 
-double osim_undulator_Ax(void *h, double zlab) { return o_undulator_Ax((osim *)h, zlab); }
+double osim_undulator_Ax(void *h, double y, double zlab) { return o_undulator_Ax((osim *)h, y, zlab); }
 
 /* ------------------------------------------------------------------ loading */
 
@@ -382,7 +405,8 @@ long osim_load(void *h, int spi, long n, const double *x, const double *u, const
         if (frame == 0 && match && s->ext) {
             double g = sqrt(1.0 + ui[0] * ui[0] + ui[1] * ui[1] + ui[2] * ui[2]);
             double zlab = xi[2] + s->gR * origin[2] * s->d[2];
-            ui[0] += -(p->q / p->m) * o_undulator_Ax(s, zlab);
+            double yax = xi[1] + origin[1] * s->d[1] - o_axis_y(s);
+            ui[0] += -(p->q / p->m) * o_undulator_Ax(s, yax, zlab);
             ui[2] = sqrt(g * g - 1.0 - ui[0] * ui[0] - ui[1] * ui[1]);
         }
         if (frame == 0) oracle_lab_to_boosted(s->gR, xi, ui, xp, up);
@@ -736,7 +760,7 @@ static void o_push_one(const osim *s, osp *p, long i, double *const J[3], long *
             E[c] = o_gather(s, s->F[O_EX + c], O_STAG[c], X);
             B[c] = o_gather(s, s->F[O_BX + c], O_STAG[3 + c], X);
         }
-        o_external(s, (X[2] + (double)s->shifts) * s->d[2], tp, Ee, Be);
+        o_external(s, X[1] * s->d[1] - o_axis_y(s), (X[2] + (double)s->shifts) * s->d[2], tp, Ee, Be);
         for (int c = 0; c < 3; c++) { E[c] += Ee[c]; B[c] += Be[c]; }
         if (s->pusher == 1) oracle_vay(qm, s->dt, E, B, U);
         else oracle_boris(qm, s->dt, E, B, U);

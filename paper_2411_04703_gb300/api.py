@@ -21,7 +21,7 @@ PIC_OK = 0
 PIC_BC_PERIODIC, PIC_BC_PML, PIC_BC_OPEN = 0, 1, 2
 PIC_FRAME_LAB, PIC_FRAME_BOOSTED = 0, 1
 PIC_EX, PIC_EY, PIC_EZ, PIC_BX, PIC_BY, PIC_BZ, PIC_JX, PIC_JY, PIC_JZ, PIC_RHO = range(10)
-PIC_EXT_NONE, PIC_EXT_PLANAR_UNDULATOR = 0, 1
+PIC_EXT_NONE, PIC_EXT_PLANAR_UNDULATOR, PIC_EXT_PLANAR_UNDULATOR_3D = 0, 1, 2
 ERRORS = {-1: "PIC_ERR_ARG", -2: "PIC_ERR_CUDA", -3: "PIC_ERR_ALLOC", -4: "PIC_ERR_STATE",
           -5: "PIC_ERR_DEVICE", -6: "PIC_ERR_CAPACITY"}
 MOMENT_NAMES = [
@@ -455,7 +455,7 @@ def from_workload(w, device=0, stream=None, tuning=None, beam=True, beam_arrays=
     ids = {}
     if w.undulator is not None:
         un = w.undulator
-        sim.set_external_field(un.K, un.lambda_u, un.phase, un.z_start, un.ramp)
+        sim.set_external_field(un.K, un.lambda_u, un.phase, un.z_start, un.ramp, kind=un.kind)
     if w.plasma is not None:
         p = w.plasma
         ids["plasma_e"], ids["plasma_i"] = sim.set_plasma(p.ppc, p.xrange, p.z_nodes, p.n_nodes)
@@ -526,7 +526,7 @@ def _bunching_fn():
             sim, ids = from_workload(wk, device=device)
             try:
                 un = wk.undulator
-                sim.set_external_field(float(K), un.lambda_u, un.phase, un.z_start, un.ramp)
+                sim.set_external_field(float(K), un.lambda_u, un.phase, un.z_start, un.ramp, kind=un.kind)
                 sim.checkpoint(every)
                 sim.step(wk.steps)
                 g = sim.backward(ids[species], k_bunch)

@@ -285,6 +285,9 @@ ExtDev ext_step(const pic_ctx *c)
     x.theta = (float)std::fmod(kp * ((double)c->shifts * c->d[2] + c->bR * tp) + c->phase0, two_pi);
     x.phase_tab = c->phase_tab;
     x.amp_tab = c->amp_tab;
+    x.kuy = (float)(c->ku * c->d[1]);
+    x.y0 = (float)(0.5 * c->n[1]);
+    x.igR = (float)(1.0 / c->gR);
     x.clock = c->dclock;
     {
         const double kp = c->ku * c->gR;
@@ -689,7 +692,8 @@ int pic_set_external_field(pic_ctx *c, const pic_external *f)
         c->ext_type = 0;
         return PIC_OK;
     }
-    if (f->type != PIC_EXT_PLANAR_UNDULATOR) return fail(c, PIC_ERR_ARG, "unknown external field type");
+    if (f->type != PIC_EXT_PLANAR_UNDULATOR && f->type != PIC_EXT_PLANAR_UNDULATOR_3D)
+        return fail(c, PIC_ERR_ARG, "unknown external field type");
     if (!(f->lambda_u > 0)) return fail(c, PIC_ERR_ARG, "lambda_u must be > 0");
     drop_graph(c);   // captured launches hold the field's constants
     c->ext_type = f->type;
@@ -1468,6 +1472,8 @@ int pic_checkpoint(pic_ctx *c, int every_k)
         if (c->bc[d][0] != PIC_BC_PERIODIC) return fail(c, PIC_ERR_ARG, "the adjoint needs a periodic grid");
     if (c->ext_type && std::isfinite(c->z_start) && c->ramp >= 0.0)
         return fail(c, PIC_ERR_ARG, "the adjoint needs an undulator without entrance ramp");
+    if (c->ext_type == PIC_EXT_PLANAR_UNDULATOR_3D)
+        return fail(c, PIC_ERR_ARG, "the adjoint is built for the 1-D planar undulator field");
     drop_graph(c);
     c->ad_on = 1;
     c->ad_every = every_k;

@@ -73,6 +73,9 @@ struct ExtDev {
     int ramp_mode;        // 0: f = 1; 1: linear ramp; 2: step
     float ramp_a, ramp_b; // ramp argument r = ramp_a (k + off_z) + ramp_b
     const float *amp_tab; // ensembles: gamma_R B0 of the run that owns row k; NULL: B0g everywhere
+    float kuy;            // 3-D field: k_u dy, the phase of cosh / sinh per cell along y
+    float y0;             // 3-D field: undulator axis (grid y coordinate of the mid-plane)
+    float igR;            // 1 / gamma_R (B'_z = B_z = B'_y amplitude / gamma_R)
     // the step's phase and ramp offset from the device step counter (so that a captured CUDA
     // graph replays correctly): theta = (th_a n + th_b) mod 2 pi, ramp_b = rb_a n + rb_b
     const long long *clock;

@@ -57,6 +57,8 @@ struct LoadP {
     double gR, bR, igR2;
     int frame, match;
     double qm, Aamp, ku, phase0;   // undulator vector potential A_x = Aamp sin(k_u z + phase0)
+    int cosh_y;                    // 3-D field: A_x also carries cosh(k_u y), y from the axis ay
+    double ay;
     long long n, stride;           // particles of this launch; component stride of x and u
     int id_base;
     int zb;                        // first row of the run the particles are loaded into
@@ -75,7 +77,8 @@ __global__ void k_load(SpeciesDev sp, LoadP p, const double *x, const double *u,
             // matched entry: lab energy kept, transverse canonical momentum u_x + (q/m) A_x = 0
             const double g = sqrt(1.0 + ui[0] * ui[0] + ui[1] * ui[1] + ui[2] * ui[2]);
             const double zlab = xi[2] + p.gR * p.origin[2] * p.d[2];
-            ui[0] += -p.qm * p.Aamp * sin(p.ku * zlab + p.phase0);
+            const double ch = p.cosh_y ? cosh(p.ku * (xi[1] + p.origin[1] * p.d[1] - p.ay)) : 1.0;
+            ui[0] += -p.qm * p.Aamp * ch * sin(p.ku * zlab + p.phase0);
             ui[2] = sqrt(g * g - 1.0 - ui[0] * ui[0] - ui[1] * ui[1]);
         }
         double xp[3], up[3];
@@ -444,7 +447,9 @@ cudaError_t launch_load(pic_ctx *c, int si, int64_t n, const double *dx, const d
     p.bR = c->bR;
     p.igR2 = 1.0 / (c->gR * c->gR);
     p.frame = frame;
-    p.match = match && c->ext_type == PIC_EXT_PLANAR_UNDULATOR;
+    p.match = match && (c->ext_type == PIC_EXT_PLANAR_UNDULATOR || c->ext_type == PIC_EXT_PLANAR_UNDULATOR_3D);
+    p.cosh_y = c->ext_type == PIC_EXT_PLANAR_UNDULATOR_3D;
+    p.ay = 0.5 * c->n[1] * c->d[1];
     p.qm = s.q / s.m;
     const double B0 = c->B0_run.empty() ? c->B0 : c->B0_run[run];
     p.Aamp = c->ku > 0 ? B0 / c->ku : 0.0;

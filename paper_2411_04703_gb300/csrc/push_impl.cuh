@@ -368,15 +368,21 @@ __device__ __forceinline__ void push_u(const Acc &acc, const float o[3], const i
     B[0] = gather<N>(acc, 3, su[0], ss[1], ss[2], wu[0], ws[1], ws[2]);
     B[1] = gather<N>(acc, 4, ss[0], su[1], ss[2], ws[0], wu[1], ws[2]);
     B[2] = gather<N>(acc, 5, ss[0], ss[1], su[2], ws[0], ws[1], wu[2]);
-    if (ext.type == PIC_EXT_PLANAR_UNDULATOR) {
+    if (ext.type == PIC_EXT_PLANAR_UNDULATOR || ext.type == PIC_EXT_PLANAR_UNDULATOR_3D) {
         float f = 1.f;
         if (ext.ramp_mode) {
             const float r = fmaf(ext.ramp_a, (float)c[2] + o[2], ext.ramp_b);
             f = ext.ramp_mode == 1 ? fminf(fmaxf(r, 0.f), 1.f) : (r >= 0.f ? 1.f : 0.f);
         }
         const float ph = ext.phase_tab[c[2]] + fmaf(ext.kdz, o[2], ext.theta);
-        const float amp = ext.amp_tab ? __ldg(ext.amp_tab + c[2]) : ext.B0g;
-        const float By = amp * f * cosf(ph);
+        const float amp = (ext.amp_tab ? __ldg(ext.amp_tab + c[2]) : ext.B0g) * f;
+        float By = amp * cosf(ph);
+        if (ext.type == PIC_EXT_PLANAR_UNDULATOR_3D) {
+            // k_u y from the axis; B'_z = B_z is the lab amplitude (B'_y's over gamma_R)
+            const float ky = ((float)c[1] - ext.y0 + o[1]) * ext.kuy;
+            B[2] -= amp * ext.igR * sinhf(ky) * sinf(ph);
+            By *= coshf(ky);
+        }
         B[1] += By;
         E[0] -= ext.beta_R * By;
     }

@@ -62,6 +62,7 @@ class Undulator:
     z_start: float = -math.inf  # lab z of the entrance (normalised); -inf: field everywhere
     ramp: float = -1.0          # lab length of the linear entrance ramp; < 0: none
     match: bool = True          # load the beam with matched transverse canonical momentum
+    kind: int = 1               # 1: ideal on-axis planar field; 2: with its cosh/sinh y-dependence
 
 
 @dataclasses.dataclass

@@ -42,7 +42,7 @@ def oracle_from_gpu(w, sim, ids, fields=True):
         o.set_state(oid[name], X, P["u"].astype(np.float64), P["w"].astype(np.float64), P["id"])
     if w.undulator is not None:
         un = w.undulator
-        o.set_external(un.K, un.lambda_u, un.phase, un.z_start, un.ramp)
+        o.set_external(un.K, un.lambda_u, un.phase, un.z_start, un.ramp, kind=un.kind)
     step, shifts, m_last = sim.get_time()
     if w.plasma is not None:
         p = w.plasma
@@ -132,7 +132,7 @@ def oracle_from_gpu_run(e, sim, ids, run, fields=True):
         o.set_state(oid[name], X, P["u"].astype(np.float64), P["w"].astype(np.float64), P["id"])
     if w.undulator is not None:
         un = w.undulator
-        o.set_external(un.K, un.lambda_u, un.phase, un.z_start, un.ramp)
+        o.set_external(un.K, un.lambda_u, un.phase, un.z_start, un.ramp, kind=un.kind)
     step, shifts, m_last = sim.get_time()
     if w.plasma is not None:
         p = w.plasma

@@ -13,7 +13,7 @@ def test_bunching_loss_plumbs_the_adjoint(monkeypatch):
     calls = {}
 
     class StandIn:
-        def set_external_field(self, K, lambda_u, *rest):
+        def set_external_field(self, K, lambda_u, *rest, **kw):
             calls["K"] = K
 
         def checkpoint(self, k):
@@ -63,7 +63,7 @@ def test_bunching_loss_default_wavenumber_and_profile_length(monkeypatch):
     seen = {}
 
     class StandIn:
-        def set_external_field(self, *a):
+        def set_external_field(self, *a, **kw):
             pass
 
         def checkpoint(self, k):

@@ -34,12 +34,21 @@ def random_fields(sim, w, seed, amp=1e-3):
         sim.set_field(c, (amp * rng.standard_normal((w.grid[2], w.grid[1], w.grid[0]))).astype(np.float32))
 
 
-def test_lab_to_boosted_load_matches_oracle():
+def _und3d(w):
+    # the planar undulator with its cosh/sinh transverse dependence (PIC_EXT_PLANAR_UNDULATOR_3D)
+    w.undulator.kind = 2
+    return w
+
+
+@pytest.mark.parametrize("kind", [1, 2])
+def test_lab_to_boosted_load_matches_oracle(kind):
+    # the matched load uses A_x of the field kind (times cosh(k_u y) off axis for kind 2)
     w = W.mini_vacuum(order=1)
+    w.undulator.kind = kind
     x, u, wt = W.sample_beam(w)
     sim, ids = api.from_workload(w, beam_arrays=(x, u, wt))
     o = oracle.Sim(w.grid, w.d, w.dt, w.gamma_R, bc=w.bc, order=w.order)
-    o.set_external(w.undulator.K, w.undulator.lambda_u)
+    o.set_external(w.undulator.K, w.undulator.lambda_u, kind=kind)
     s = o.add_species(-1.0, 1.0, capacity=x.shape[1])
     o.load(s, x, u, wt, frame=oracle.LAB, origin=w.beam.origin, match_undulator=True)
     r = parity.compare_species(w, sim, ids["beam"], o, s)
@@ -54,6 +63,8 @@ CASES = {
     "vacuum_tsc": lambda: W.mini_vacuum(order=2),
     "plasma_tsc_pml_window": lambda: W.mini_plasma(),
     "long_undulator_tsc_pml_ramp": lambda: W.mini_long_undulator(),
+    "vacuum_tsc_undulator_3d": lambda: _und3d(W.mini_vacuum(order=2)),
+    "long_undulator_3d_pml_ramp": lambda: _und3d(W.mini_long_undulator()),
 }
 
 

@@ -805,3 +805,96 @@ def test_lab_energy_spread_and_kinetic_energy_of_a_two_energy_beam():
     bR = math.sqrt(1 - GR_LAB ** -2)
     gp = GR_LAB * (g - bR * np.sqrt(g * g - 1))
     assert m0["kinetic_energy"] == pytest.approx(2.5 * np.sum(w * (gp - 1)), rel=1e-9)
+
+
+# ------------------------------------------------------------------ 3-D planar undulator field
+
+def _field3d(gR=1.0, K=1.2, lam=5.0, ny=16, dy=0.5):
+    s = oracle.Sim((4, ny, 8), (1.0, dy, 1.0), 0.1, gR)
+    s.set_external(K=K, lambda_u=lam, kind=2)
+    return s
+
+
+def test_3d_undulator_lab_field_is_divergence_and_curl_free():
+    # gamma_R = 1: the RRF is the lab.  The cosh/sinh field satisfies div B = 0 and
+    # (curl B)_x = dB_z/dy - dB_y/dz = 0 (a vacuum magnetostatic field); central differences of
+    # step h leave O(h^2) ~ 1e-10 of the field.
+    s = _field3d()
+    ku = 2 * math.pi / 5.0
+    B0 = 1.2 * ku
+    h = 1e-5
+    rng = np.random.default_rng(41)
+    for _ in range(20):
+        y, z = rng.uniform(-1.5, 1.5), rng.uniform(-7, 7)
+        f = lambda yy, zz: s.external_at(zz, 0.0, y=yy)[1]
+        dBy_dy = (f(y + h, z)[1] - f(y - h, z)[1]) / (2 * h)
+        dBz_dz = (f(y, z + h)[2] - f(y, z - h)[2]) / (2 * h)
+        dBz_dy = (f(y + h, z)[2] - f(y - h, z)[2]) / (2 * h)
+        dBy_dz = (f(y, z + h)[1] - f(y, z - h)[1]) / (2 * h)
+        assert abs(dBy_dy + dBz_dz) < 1e-8 * B0 * ku
+        assert abs(dBz_dy - dBy_dz) < 1e-8 * B0 * ku
+        assert abs(f(y, z)[0]) == 0.0
+        # grows off axis: |B_y| = B0 cosh(k_u y) |cos(k_u z)|
+        assert abs(f(y, z)[1]) == pytest.approx(B0 * math.cosh(ku * y) * abs(math.cos(ku * z)), rel=1e-12, abs=1e-14)
+
+
+def test_3d_undulator_reduces_to_the_ideal_field_on_axis():
+    for gR in (1.0, 20.0):
+        s1 = oracle.Sim((4, 16, 8), (1.0, 0.5, 1.0), 0.1, gR)
+        s1.set_external(K=1.2, lambda_u=5.0, kind=1)
+        s2 = _field3d(gR=gR)
+        for zp, tp in [(0.1, 0.0), (0.37, 2.0), (-1.0, 11.0)]:
+            E1, B1 = s1.external_at(zp, tp, y=0.0)
+            E2, B2 = s2.external_at(zp, tp, y=0.0)
+            np.testing.assert_allclose(E2, E1, rtol=0, atol=1e-15)
+            np.testing.assert_allclose(B2, B1, rtol=0, atol=1e-15)
+
+
+def test_3d_undulator_rrf_field_keeps_the_lorentz_invariants():
+    # the lab field is purely magnetic: in the RRF E'.B' = 0 and B'^2 - E'^2 = B_lab^2 at the
+    # same event (lab z = gamma_R (z' + beta_R t'), y unchanged); the longitudinal B'_z = B_z
+    gR = 20.0
+    lab = _field3d(gR=1.0)
+    rrf = _field3d(gR=gR)
+    bR = rrf.beta_R
+    rng = np.random.default_rng(42)
+    for _ in range(10):
+        y, zp, tp = rng.uniform(-1, 1), rng.uniform(-0.3, 0.3), rng.uniform(0, 3)
+        E, B = rrf.external_at(zp, tp, y=y)
+        _, Bl = lab.external_at(gR * (zp + bR * tp), 0.0, y=y)
+        scale = float(Bl @ Bl) * gR ** 2 + 1e-300
+        assert abs(E @ B) < 1e-12 * scale
+        assert (B @ B - E @ E) == pytest.approx(Bl @ Bl, rel=1e-9, abs=1e-12 * scale)
+        assert B[2] == pytest.approx(Bl[2], rel=1e-12, abs=1e-15)
+
+
+def test_3d_undulator_canonical_momentum_off_axis():
+    # the field depends on (y, z) only, so u_x + (q/m) A_x(y, z) with A_x = (B0/k_u) cosh(k_u y)
+    # sin(k_u z) is conserved (gamma_R = 1, a test electron off axis); the matched load starts it
+    # at zero, and y oscillates slowly (the natural focusing of the cosh field)
+    K, gB, lam = 1.0, 20.0, 2 * math.pi
+    nz, ny = 64, 64
+    dz, dy = 2 * math.pi / nz, 0.05
+    dt = 0.05 * dz
+    s = oracle.Sim((4, ny, nz), (1.0, dy, dz), dt, 1.0)
+    sid = s.add_species(-1.0, 1.0)
+    s.set_external(K=K, lambda_u=lam, kind=2)
+    y_off = 0.4                              # from the axis at ny dy / 2
+    x = np.array([[0.0], [0.0], [0.0]])
+    u = np.array([[0.0], [0.0], [math.sqrt(gB * gB - 1)]])
+    s.load(sid, x, u, w=np.zeros(1), frame=LAB, origin=(2.0, ny / 2 + y_off / dy, 10.0), match_undulator=True)
+    X, U, _, _ = s.particles(sid)
+    yax = X[0, 1] * dy - 0.5 * ny * dy
+    assert (-1.0) * s.undulator_Ax(X[0, 2] * dz, y=yax) + U[0, 0] == pytest.approx(0.0, abs=1e-12)
+    P0 = None
+    for n in range(400):
+        s.step(1)
+        X1, U1, _, _ = s.particles(sid)
+        yax = X[0, 1] * dy - 0.5 * ny * dy
+        P = 0.5 * (U[0, 0] + U1[0, 0]) + (-1.0) * s.undulator_Ax(X[0, 2] * dz, y=yax)
+        if P0 is None:
+            P0 = P
+        assert abs(P - P0) < 1e-4 * K, (n, P, P0)
+        X, U = X1, U1
+    # the off-axis electron was pushed towards the axis (y decreased) by the cosh focusing
+    assert X[0, 1] * dy - 0.5 * ny * dy < y_off
