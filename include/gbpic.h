@@ -238,14 +238,30 @@ int pic_set_pusher(pic_ctx *ctx, int pusher);
  * capturing fails the context falls back to launching. */
 int pic_use_graphs(pic_ctx *ctx, int on);
 
-/* Autotuner of the tile-sort cadence (the tile itself is the compiled 8x8x8 region).  Runs trials of whole sort periods (>= 32 steps each) with sort_every = 1, 2, 3, 4, 6,
+/* Autotuner of the tile-sort cadence at the context's current tile size (pic_autotune_tiles
+ * below also chooses the tile).  Runs trials of whole sort periods (>= 32 steps each) with
+ * sort_every = 1, 2, 3, 4, 6,
  * 8, 12, 16, 24, 32 (up to max_sort_every), each starting with a sort, in two passes (ascending,
  * then descending), times them with CUDA events on the context stream and keeps the fastest per
  * step (a rarer sort must win by 2 %).  The trial steps are real steps: the simulation advances
- * by their total (about 500 steps for max_sort_every = 16).  A
- * fast drift (cells per step) favours frequent sorts, a slow one rare sorts; the tile stays the
- * compiled 8x8x8 region.  *sort_every_out (may be NULL) receives the choice.  Synchronous. */
+ * by their total (about 500 steps for max_sort_every = 16).  A fast drift (cells per step)
+ * favours frequent sorts, a slow one rare sorts.  *sort_every_out (may be NULL) receives the
+ * choice.  Synchronous. */
 int pic_autotune(pic_ctx *ctx, int max_sort_every, int *sort_every_out);
+
+/* Autotuner of the tile size and the sort cadence together.  tiles: host int[n_tiles][3],
+ * candidate tile sizes (the first is the reference, e.g. the current 8 x 8 x 8); each must pass
+ * pic_set_tuning's checks (2..16 cells per dim, the region within shared memory, for an ensemble
+ * a z size dividing the rows of a run), else PIC_ERR_ARG.  Every candidate runs whole periods of
+ * the current cadence (>= 32 steps, the first step sorting on the new tiles), in two passes
+ * (ascending, then descending); the fastest per step is kept (a candidate must beat the best
+ * before it in the list by 2 %), then pic_autotune picks the cadence for it.  The trials
+ * advance the run.  Changing the tile reallocates the species' tile tables through the context's
+ * allocator; the tile sizes 8 x 8 x 8 use the kernel's compiled region, others its runtime-sized
+ * one.  tile_out (host int[3]) and sort_every_out receive the choice (either may be NULL).
+ * PIC_ERR_STATE while adjoint checkpoints are recorded. */
+int pic_autotune_tiles(pic_ctx *ctx, const int *tiles, int n_tiles, int max_sort_every, int *tile_out,
+                       int *sort_every_out);
 
 /* Wait for the context stream; returns PIC_ERR_DEVICE if a kernel raised the error word. */
 int pic_sync(pic_ctx *ctx);

@@ -126,6 +126,7 @@ def lib(build_if_missing: bool = True):
             "pic_set_plasma_batch": [vp, P(pic_plasma), P(d), P(i), P(i)],
             "pic_get_moments_run": [vp, i, i, i, d, P(pic_moments)],
             "pic_autotune": [vp, i, P(i)],
+            "pic_autotune_tiles": [vp, P(i), i, i, P(i), P(i)],
             "pic_use_graphs": [vp, i],
             "pic_set_pusher": [vp, i],
             "pic_resolution_factor": [vp, d, P(d), P(i)],
@@ -370,6 +371,14 @@ class Sim:
         out = C.c_int()
         self._check(self.L.pic_autotune(self.h, int(max_sort_every), C.byref(out)))
         return out.value
+
+    def autotune_tiles(self, tiles=((8, 8, 8), (8, 8, 4), (8, 4, 4), (4, 4, 4)), max_sort_every=16):
+        """Pick the tile size (from `tiles`, the first the reference) and then the sort cadence by
+        timed trials (advances the simulation); returns (tile, sort_every)."""
+        flat = (C.c_int * (3 * len(tiles)))(*[int(v) for t in tiles for v in t])
+        tout, sout = (C.c_int * 3)(), C.c_int()
+        self._check(self.L.pic_autotune_tiles(self.h, flat, len(tiles), int(max_sort_every), tout, C.byref(sout)))
+        return tuple(int(v) for v in tout), sout.value
 
     def sync(self):
         self._check(self.L.pic_sync(self.h))

@@ -177,6 +177,52 @@ int alloc_tile_scratch(pic_ctx *c)
 
 double shifts_due(const pic_ctx *c, int64_t n) { return std::floor(c->vw * (double)n * c->dt / c->d[2]); }
 
+// A tile size the particle kernel can run: 2..16 cells per dim, the tile's shared-memory region
+// (tile + drift margin + stencil halo) within the shared memory of one CTA, and for an ensemble a
+// z size that divides the rows of a run (tiles never straddle runs).
+int check_tile(pic_ctx *c, const int T[3], int margin)
+{
+    for (int d = 0; d < 3; d++)
+        if (T[d] < 2 || T[d] > 16) return fail(c, PIC_ERR_ARG, "tile sizes must be 2..16");
+    if (margin < 0 || margin > 2) return fail(c, PIC_ERR_ARG, "margin must be 0..2");
+    int R3 = 1;
+    for (int d = 0; d < 3; d++) R3 *= T[d] + 2 * margin + margin_lo(c) + margin_hi(c);
+    if ((size_t)R3 * 12 * sizeof(float) + 40 * 1024 > 224 * 1024)
+        return fail(c, PIC_ERR_ARG, "tile region exceeds shared memory");
+    if (c->runs > 1 && c->nzr % T[2] != 0)
+        return fail(c, PIC_ERR_ARG, "ensemble: the tile's z size must divide the rows of a run");
+    return PIC_OK;
+}
+
+// Changes the tile size of a context that holds species: the per-species tile tables (sort keys,
+// work items, sparse-tile lists) are reallocated for the new tiling and the next step sorts.
+int retile(pic_ctx *c, const int T[3])
+{
+    drop_graph(c);
+    for (int d = 0; d < 3; d++) c->T[d] = T[d];
+    set_tiles(c);
+    int r = alloc_tile_scratch(c);
+    if (r) return r;
+    for (int si = 0; si < c->nsp; si++) {
+        Species &s = c->sp[si];
+        if (s.lattice) continue;
+        dfree(c, s.items);
+        dfree(c, s.cell_start);
+        dfree(c, s.chunk_start);
+        dfree(c, s.sparse_start);
+        dfree(c, s.sparse_tiles);
+        s.items = nullptr;
+        s.cell_start = s.chunk_start = s.sparse_start = s.sparse_tiles = nullptr;
+        s.max_items = c->ntiles + s.cap / kChunkMin + 2;
+        if ((r = alloc_zero(c, &s.items, s.max_items)) || (r = alloc_zero(c, &s.cell_start, c->n_keys + 1)) ||
+            (r = alloc_zero(c, &s.chunk_start, c->ntiles + 1)) || (r = alloc_zero(c, &s.sparse_start, c->ntiles + 1)) ||
+            (r = alloc_zero(c, &s.sparse_tiles, c->ntiles)))
+            return r;
+    }
+    c->sort_base = c->step;   // the stored order is of the old tiles: sort before the next push
+    return PIC_OK;
+}
+
 // Tracing: a pair of events around a launch group of class cls.
 cudaEvent_t take_event(pic_ctx *c)
 {
@@ -576,16 +622,8 @@ int pic_set_tuning(pic_ctx *c, const pic_tuning *t)
     if (r) return r;
     if (!t) return fail(c, PIC_ERR_ARG, "tuning is NULL");
     if (c->nsp > 0) return fail(c, PIC_ERR_STATE, "set tuning before creating species");
-    for (int d = 0; d < 3; d++)
-        if (t->tile[d] < 2 || t->tile[d] > 16) return fail(c, PIC_ERR_ARG, "tile sizes must be 2..16");
     if (t->sort_every < 1) return fail(c, PIC_ERR_ARG, "sort_every must be >= 1");
-    if (t->margin < 0 || t->margin > 2) return fail(c, PIC_ERR_ARG, "margin must be 0..2");
-    int R3 = 1;
-    for (int d = 0; d < 3; d++) R3 *= t->tile[d] + 2 * t->margin + margin_lo(c) + margin_hi(c);
-    if ((size_t)R3 * 12 * sizeof(float) + 40 * 1024 > 224 * 1024)
-        return fail(c, PIC_ERR_ARG, "tile region exceeds shared memory");
-    if (c->runs > 1 && c->nzr % t->tile[2] != 0)
-        return fail(c, PIC_ERR_ARG, "ensemble: the tile's z size must divide the rows of a run");
+    if ((r = check_tile(c, t->tile, t->margin))) return r;
     for (int d = 0; d < 3; d++) c->T[d] = t->tile[d];
     drop_graph(c);
     c->sort_every = t->sort_every;
@@ -1165,6 +1203,59 @@ int pic_resonant_wavenumber(double K, double lambda_u, double gamma_B, double ga
     const double one_m_bR = 1.0 / (gamma_R * gamma_R * (1.0 + bR));
     const double one_m_bz = a / (2.0 * gamma_B * gamma_B);
     *k = k_lab * gamma_R * (one_m_bR + bR * one_m_bz);
+    return PIC_OK;
+}
+
+int pic_autotune_tiles(pic_ctx *c, const int *tiles, int n_tiles, int max_sort_every, int *tile_out,
+                       int *sort_every_out)
+{
+    int r = check_ctx(c);
+    if (r) return r;
+    if (!tiles || n_tiles < 1) return fail(c, PIC_ERR_ARG, "no tile candidates");
+    if (max_sort_every < 1) return fail(c, PIC_ERR_ARG, "max_sort_every must be >= 1");
+    if (c->ad_on) return fail(c, PIC_ERR_STATE, "the tile cannot change while adjoint checkpoints are recorded");
+    for (int q = 0; q < n_tiles; q++)
+        if ((r = check_tile(c, tiles + 3 * q, c->M))) return r;
+    cudaEvent_t a = nullptr, b = nullptr;
+    CK(cudaEventCreate(&a));
+    if (cudaEventCreate(&b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        return fail(c, PIC_ERR_CUDA, "cudaEventCreate failed");
+    }
+    // every candidate, in two passes (ascending then descending), over whole periods of the
+    // current sort cadence (>= 32 steps), each trial starting with a sort on the new tiles
+    const int se = c->sort_every;
+    const int64_t steps = ((std::max(32, se) + se - 1) / se) * (int64_t)se;
+    std::vector<double> tot(n_tiles, 0.0);
+    for (int pass = 0; pass < 2 && !r; pass++) {
+        for (int q0 = 0; q0 < n_tiles && !r; q0++) {
+            const int q = pass == 0 ? q0 : n_tiles - 1 - q0;
+            if ((r = retile(c, tiles + 3 * q))) break;
+            cudaEventRecord(a, c->stream);
+            r = pic_step(c, steps);
+            cudaEventRecord(b, c->stream);
+            if (r) break;
+            float ms = 0;
+            if (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+                r = fail_cuda(c, cudaGetLastError(), "autotune timing");
+                break;
+            }
+            tot[q] += ms / (double)steps;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (r) return r;
+    // the first candidate is the reference: another must beat the best so far by 2 %
+    int best = 0;
+    for (int q = 1; q < n_tiles; q++)
+        if (tot[q] < 0.98 * tot[best]) best = q;
+    if ((r = retile(c, tiles + 3 * best))) return r;
+    int se_best = c->sort_every;
+    if ((r = pic_autotune(c, max_sort_every, &se_best))) return r;
+    if (tile_out)
+        for (int d = 0; d < 3; d++) tile_out[d] = c->T[d];
+    if (sort_every_out) *sort_every_out = se_best;
     return PIC_OK;
 }
 

@@ -20,18 +20,21 @@ __device__ __forceinline__ float ld(const float *F, const GridDev &g, int i, int
     return __ldg(F + ((long long)k * g.n[1] + j) * g.n[0] + i);
 }
 
-// psi = b psi + (b - 1) dF; returns dF + psi (the CPML-stretched derivative).
-__device__ __forceinline__ float cpml(float *psi, long long ix, float b, float dF)
+// CPML-stretched derivative dF + psi' with psi' = b psi + (b - 1) dF (psi the value loaded
+// before; b >= 1: outside the layers, no auxiliary term).  The new psi' is returned in psi.
+__device__ __forceinline__ float cpml_d(float b, float &psi, float dF)
 {
     if (b >= 1.f) return dF;
-    const float p = fmaf(b, psi[ix], (b - 1.f) * dF);
-    psi[ix] = p;
-    return dF + p;
+    psi = fmaf(b, psi, (b - 1.f) * dF);
+    return dF + psi;
 }
 
 // B -= dtt curl E (half step).  B_x at (i, j+1/2, k+1/2), B_y at (i+1/2, j, k+1/2),
-// B_z at (i+1/2, j+1/2, k): forward differences of E.
-__global__ void k_fdtd_b(FieldsDev f, GridDev g, PmlDev pml, float dtt)
+// B_z at (i+1/2, j+1/2, k): forward differences of E.  Every load of the cell (E and its
+// neighbours, B, the layers' psi) is issued before the first store, so one round trip to memory
+// covers the cell.
+__global__ void __launch_bounds__(256) k_fdtd_b(const float *__restrict__ E, float *__restrict__ B,
+                                                float *__restrict__ psiB, GridDev g, PmlDev pml, float dtt)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -40,32 +43,46 @@ __global__ void k_fdtd_b(FieldsDev f, GridDev g, PmlDev pml, float dtt)
     const int zb = zblock(k, g.nzr);
     const long long N = g.ncell;
     const long long ix = ((long long)k * g.n[1] + j) * g.n[0] + i;
-    const float *Ex = f.E, *Ey = f.E + N, *Ez = f.E + 2 * N;
+    const float *Ex = E, *Ey = E + N, *Ez = E + 2 * N;
     const float ex = Ex[ix], ey = Ey[ix], ez = Ez[ix];
+    const float ez_y = ld(Ez, g, i, j + 1, k, zb), ey_z = ld(Ey, g, i, j, k + 1, zb);
+    const float ex_z = ld(Ex, g, i, j, k + 1, zb), ez_x = ld(Ez, g, i + 1, j, k, zb);
+    const float ey_x = ld(Ey, g, i + 1, j, k, zb), ex_y = ld(Ex, g, i, j + 1, k, zb);
+    const float b0 = B[ix], b1 = B[N + ix], b2 = B[2 * N + ix];
     const float idx = 1.f / g.d[0], idy = 1.f / g.d[1], idz = 1.f / g.d[2];
-    float dEz_dy = (ld(Ez, g, i, j + 1, k, zb) - ez) * idy;
-    float dEy_dz = (ld(Ey, g, i, j, k + 1, zb) - ey) * idz;
-    float dEx_dz = (ld(Ex, g, i, j, k + 1, zb) - ex) * idz;
-    float dEz_dx = (ld(Ez, g, i + 1, j, k, zb) - ez) * idx;
-    float dEy_dx = (ld(Ey, g, i + 1, j, k, zb) - ey) * idx;
-    float dEx_dy = (ld(Ex, g, i, j + 1, k, zb) - ex) * idy;
+    float dEz_dy = (ez_y - ez) * idy;
+    float dEy_dz = (ey_z - ey) * idz;
+    float dEx_dz = (ex_z - ex) * idz;
+    float dEz_dx = (ez_x - ez) * idx;
+    float dEy_dx = (ey_x - ey) * idx;
+    float dEx_dy = (ex_y - ex) * idy;
     if (pml.on) {
         const float bx = pml.bB[0][i], by = pml.bB[1][j], bz = pml.bB[2][k];
-        dEz_dy = cpml(pml.psiB + 0 * N, ix, by, dEz_dy);
-        dEy_dz = cpml(pml.psiB + 1 * N, ix, bz, dEy_dz);
-        dEx_dz = cpml(pml.psiB + 2 * N, ix, bz, dEx_dz);
-        dEz_dx = cpml(pml.psiB + 3 * N, ix, bx, dEz_dx);
-        dEy_dx = cpml(pml.psiB + 4 * N, ix, bx, dEy_dx);
-        dEx_dy = cpml(pml.psiB + 5 * N, ix, by, dEx_dy);
+        if (bx < 1.f || by < 1.f || bz < 1.f) {
+            float p[6];
+#pragma unroll
+            for (int q = 0; q < 6; q++) p[q] = psiB[q * N + ix];
+            dEz_dy = cpml_d(by, p[0], dEz_dy);
+            dEy_dz = cpml_d(bz, p[1], dEy_dz);
+            dEx_dz = cpml_d(bz, p[2], dEx_dz);
+            dEz_dx = cpml_d(bx, p[3], dEz_dx);
+            dEy_dx = cpml_d(bx, p[4], dEy_dx);
+            dEx_dy = cpml_d(by, p[5], dEx_dy);
+            if (by < 1.f) { psiB[0 * N + ix] = p[0]; psiB[5 * N + ix] = p[5]; }
+            if (bz < 1.f) { psiB[1 * N + ix] = p[1]; psiB[2 * N + ix] = p[2]; }
+            if (bx < 1.f) { psiB[3 * N + ix] = p[3]; psiB[4 * N + ix] = p[4]; }
+        }
     }
-    f.B[ix] -= dtt * (dEz_dy - dEy_dz);
-    f.B[N + ix] -= dtt * (dEx_dz - dEz_dx);
-    f.B[2 * N + ix] -= dtt * (dEy_dx - dEx_dy);
+    B[ix] = b0 - dtt * (dEz_dy - dEy_dz);
+    B[N + ix] = b1 - dtt * (dEx_dz - dEz_dx);
+    B[2 * N + ix] = b2 - dtt * (dEy_dx - dEx_dy);
 }
 
 // E += dt (curl B - J).  E_x at (i+1/2, j, k), E_y at (i, j+1/2, k), E_z at (i, j, k+1/2):
-// backward differences of B.
-__global__ void k_fdtd_e(FieldsDev f, GridDev g, PmlDev pml)
+// backward differences of B.  Loads first, as in k_fdtd_b.
+__global__ void __launch_bounds__(256) k_fdtd_e(float *__restrict__ E, const float *__restrict__ B,
+                                                const float *__restrict__ J, float *__restrict__ psiE, GridDev g,
+                                                PmlDev pml)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -74,28 +91,41 @@ __global__ void k_fdtd_e(FieldsDev f, GridDev g, PmlDev pml)
     const int zb = zblock(k, g.nzr);
     const long long N = g.ncell;
     const long long ix = ((long long)k * g.n[1] + j) * g.n[0] + i;
-    const float *Bx = f.B, *By = f.B + N, *Bz = f.B + 2 * N;
+    const float *Bx = B, *By = B + N, *Bz = B + 2 * N;
     const float bxv = Bx[ix], byv = By[ix], bzv = Bz[ix];
+    const float bz_y = ld(Bz, g, i, j - 1, k, zb), by_z = ld(By, g, i, j, k - 1, zb);
+    const float bx_z = ld(Bx, g, i, j, k - 1, zb), bz_x = ld(Bz, g, i - 1, j, k, zb);
+    const float by_x = ld(By, g, i - 1, j, k, zb), bx_y = ld(Bx, g, i, j - 1, k, zb);
+    const float e0 = E[ix], e1 = E[N + ix], e2 = E[2 * N + ix];
+    const float j0 = J[ix], j1 = J[N + ix], j2 = J[2 * N + ix];
     const float idx = 1.f / g.d[0], idy = 1.f / g.d[1], idz = 1.f / g.d[2];
-    float dBz_dy = (bzv - ld(Bz, g, i, j - 1, k, zb)) * idy;
-    float dBy_dz = (byv - ld(By, g, i, j, k - 1, zb)) * idz;
-    float dBx_dz = (bxv - ld(Bx, g, i, j, k - 1, zb)) * idz;
-    float dBz_dx = (bzv - ld(Bz, g, i - 1, j, k, zb)) * idx;
-    float dBy_dx = (byv - ld(By, g, i - 1, j, k, zb)) * idx;
-    float dBx_dy = (bxv - ld(Bx, g, i, j - 1, k, zb)) * idy;
+    float dBz_dy = (bzv - bz_y) * idy;
+    float dBy_dz = (byv - by_z) * idz;
+    float dBx_dz = (bxv - bx_z) * idz;
+    float dBz_dx = (bzv - bz_x) * idx;
+    float dBy_dx = (byv - by_x) * idx;
+    float dBx_dy = (bxv - bx_y) * idy;
     if (pml.on) {
         const float bx = pml.bE[0][i], by = pml.bE[1][j], bz = pml.bE[2][k];
-        dBz_dy = cpml(pml.psiE + 0 * N, ix, by, dBz_dy);
-        dBy_dz = cpml(pml.psiE + 1 * N, ix, bz, dBy_dz);
-        dBx_dz = cpml(pml.psiE + 2 * N, ix, bz, dBx_dz);
-        dBz_dx = cpml(pml.psiE + 3 * N, ix, bx, dBz_dx);
-        dBy_dx = cpml(pml.psiE + 4 * N, ix, bx, dBy_dx);
-        dBx_dy = cpml(pml.psiE + 5 * N, ix, by, dBx_dy);
+        if (bx < 1.f || by < 1.f || bz < 1.f) {
+            float p[6];
+#pragma unroll
+            for (int q = 0; q < 6; q++) p[q] = psiE[q * N + ix];
+            dBz_dy = cpml_d(by, p[0], dBz_dy);
+            dBy_dz = cpml_d(bz, p[1], dBy_dz);
+            dBx_dz = cpml_d(bz, p[2], dBx_dz);
+            dBz_dx = cpml_d(bx, p[3], dBz_dx);
+            dBy_dx = cpml_d(bx, p[4], dBy_dx);
+            dBx_dy = cpml_d(by, p[5], dBx_dy);
+            if (by < 1.f) { psiE[0 * N + ix] = p[0]; psiE[5 * N + ix] = p[5]; }
+            if (bz < 1.f) { psiE[1 * N + ix] = p[1]; psiE[2 * N + ix] = p[2]; }
+            if (bx < 1.f) { psiE[3 * N + ix] = p[3]; psiE[4 * N + ix] = p[4]; }
+        }
     }
     const float dt = g.dt;
-    f.E[ix] += dt * (dBz_dy - dBy_dz - f.J[ix]);
-    f.E[N + ix] += dt * (dBx_dz - dBz_dx - f.J[N + ix]);
-    f.E[2 * N + ix] += dt * (dBy_dx - dBx_dy - f.J[2 * N + ix]);
+    E[ix] = e0 + dt * (dBz_dy - dBy_dz - j0);
+    E[N + ix] = e1 + dt * (dBx_dz - dBz_dx - j1);
+    E[2 * N + ix] = e2 + dt * (dBy_dx - dBx_dy - j2);
 }
 
 // Moving window: every array moves down one z plane, the front plane becomes zero.  One
@@ -134,7 +164,8 @@ __global__ void k_sumsq(const float *a, long long n, double *partial)
 cudaError_t launch_fdtd_b(pic_ctx *c, float dtt)
 {
     dim3 blk(32, 8, 1), grd((c->n[0] + 31) / 32, (c->n[1] + 7) / 8, c->n[2]);
-    k_fdtd_b<<<grd, blk, 0, c->stream>>>(FieldsDev{c->E, c->B, c->J}, grid_dev(c), pml_dev(c), dtt);
+    const PmlDev pml = pml_dev(c);
+    k_fdtd_b<<<grd, blk, 0, c->stream>>>(c->E, c->B, pml.psiB, grid_dev(c), pml, dtt);
     c->kernels++;
     return cudaGetLastError();
 }
@@ -142,7 +173,8 @@ cudaError_t launch_fdtd_b(pic_ctx *c, float dtt)
 cudaError_t launch_fdtd_e(pic_ctx *c)
 {
     dim3 blk(32, 8, 1), grd((c->n[0] + 31) / 32, (c->n[1] + 7) / 8, c->n[2]);
-    k_fdtd_e<<<grd, blk, 0, c->stream>>>(FieldsDev{c->E, c->B, c->J}, grid_dev(c), pml_dev(c));
+    const PmlDev pml = pml_dev(c);
+    k_fdtd_e<<<grd, blk, 0, c->stream>>>(c->E, c->B, c->J, pml.psiE, grid_dev(c), pml);
     c->kernels++;
     return cudaGetLastError();
 }

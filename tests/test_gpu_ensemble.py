@@ -153,3 +153,29 @@ def test_autotuner_picks_a_cadence_and_keeps_physics():
             assert ma["count"] == mb["count"]
             for key in ("mean_gamma", "rel_energy_spread", "emit_nx", "emit_ny", "rms_z", "field_energy"):
                 assert ma[key] == pytest.approx(mb[key], rel=1e-3), (r, frame, key)
+
+
+def test_tile_autotuner_picks_a_tile_and_cadence_and_keeps_physics():
+    # the tile is tuned together with the cadence: the first candidate is the compiled 8^3
+    # region, the others the runtime-sized region; the run then tracks a twin that kept the
+    # default tuning for as many steps (per-run diagnostics within 1e-3)
+    e = W.mini_ensemble()
+    sim, ids = api.from_ensemble(e)
+    twin, tids = api.from_ensemble(e)
+    cands = ((8, 8, 8), (8, 8, 4), (4, 4, 4))
+    tile, se = sim.autotune_tiles(cands, max_sort_every=8)
+    assert tile in cands and se in (1, 2, 3, 4, 6, 8)
+    n = sim.get_time()[0]
+    assert n >= 2 * len(cands) * 32
+    twin.step(n)
+    sim.sync()
+    twin.sync()
+    for r in range(e.runs):
+        for frame in (api.PIC_FRAME_BOOSTED, api.PIC_FRAME_LAB):
+            ma = sim.get_moments_run(ids["beam"], r, frame, k_bunch=1.0)
+            mb = twin.get_moments_run(tids["beam"], r, frame, k_bunch=1.0)
+            assert ma["count"] == mb["count"]
+            for key in ("mean_gamma", "rel_energy_spread", "emit_nx", "emit_ny", "rms_z", "field_energy"):
+                assert ma[key] == pytest.approx(mb[key], rel=1e-3), (r, frame, key)
+    with pytest.raises(api.PicError, match="tile"):
+        sim.autotune_tiles(((8, 8, 8), (32, 8, 8)))

@@ -90,6 +90,27 @@ def test_one_step_from_identical_state(case):
         assert f[k] < TOL_STEP, (k, f)
 
 
+@pytest.mark.parametrize("tile", [(8, 4, 4), (4, 4, 4), (8, 8, 4)])
+@pytest.mark.parametrize("case", ["vacuum_cic", "plasma_tsc_pml_window"])
+def test_one_step_on_other_tiles_from_identical_state(case, tile):
+    # tiles other than 8^3 run the particle kernel's runtime-sized region (what the tile
+    # autotuner can choose): the same per-step bar against the oracle
+    w = CASES[case]()
+    sim, ids = api.from_workload(w, tuning={"tile": tile, "sort_every": 4, "margin": 1})
+    random_fields(sim, w, seed=17)
+    sim.sort()
+    o, oid = parity.oracle_from_gpu(w, sim, ids)
+    sim.step(1)
+    sim.sync()
+    o.step(1)
+    for name in ids:
+        r = parity.compare_species(w, sim, ids[name], o, oid[name])
+        assert r["only_gpu"] == 0 and r["only_oracle"] == 0 and r["cell_mismatch"] == 0, (name, r)
+        assert r["u_rel_err"] < TOL_STEP, (name, r)
+    f = parity.compare_fields(sim, o)
+    assert max(f.values()) < TOL_STEP, f
+
+
 @pytest.mark.parametrize("case", ["vacuum_tsc", "plasma_tsc_pml_window"])
 def test_one_step_vay_pusher_from_identical_state(case):
     w = CASES[case]()
