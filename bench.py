@@ -507,10 +507,14 @@ def run_gbpic(args):
         l2 = "inputs larger than L2 (particle state ~8 GB, fields 0.4 GB)"
     else:
         grid = tuple(int(v) for v in args.grid.split(","))
-        nb = args.beam or int(round(4194304 * (grid[0] * grid[1] * grid[2]) / (128 * 128 * 512)))
-        w = W.plasma_buncher(grid=grid, n_beam=nb, seed=2 + rank)
-        if grid != (128, 128, 512):
-            w.name = f"plasma buncher {grid[0]}x{grid[1]}x{grid[2]} (reduced), {nb} beam + 8 ppc plasma, TSC"
+        if args.workload == "buncher2d":
+            # the paper's 2-D geometry (x-z, ny = 1): 1024 x 2048 cells, 4 ppc, 1M beam
+            w = W.plasma_buncher_2d(seed=6 + rank)
+        else:
+            nb = args.beam or int(round(4194304 * (grid[0] * grid[1] * grid[2]) / (128 * 128 * 512)))
+            w = W.plasma_buncher(grid=grid, n_beam=nb, seed=2 + rank)
+            if grid != (128, 128, 512):
+                w.name = f"plasma buncher {grid[0]}x{grid[1]}x{grid[2]} (reduced), {nb} beam + 8 ppc plasma, TSC"
         beam = W.sample_beam(w)
         if args.tile:
             w.tile = tuple(int(v) for v in args.tile.split(","))
@@ -524,8 +528,9 @@ def run_gbpic(args):
             torch.cuda.empty_cache()
         sim, ids = api.from_workload(w, device=local, beam_arrays=beam)
         ncell_total = w.ncell
-        boundaries = "transverse CPML 10 cells, moving window"
-        l2 = "inputs larger than L2 (particle state ~9 GB, fields 0.3 GB)"
+        boundaries = "transverse CPML 10 cells, moving window" + (" (2-D: x PML, y uniform)" if args.workload == "buncher2d" else "")
+        l2 = ("inputs larger than L2 (particle state ~0.6 GB, fields 0.05 GB)" if args.workload == "buncher2d"
+              else "inputs larger than L2 (particle state ~9 GB, fields 0.3 GB)")
     # periodic workloads replay their steps as CUDA graphs (tracing would turn that off): their
     # kernel-class composition comes from a traced pass after the timed region
     graphs = args.workload in ("vacuum", "ensemble")
@@ -725,7 +730,7 @@ def main():
     ap.add_argument("--autotune", action="store_true",
                     help="buncher: pick the sort cadence with the autotuner (its slow drift makes the "
                          "cadence matter little; the default keeps 8)")
-    ap.add_argument("--workload", choices=["buncher", "ensemble", "vacuum", "adjoint"], default="buncher",
+    ap.add_argument("--workload", choices=["buncher", "buncher2d", "ensemble", "vacuum", "adjoint"], default="buncher",
                     help="buncher: the plasma buncher 128x128x512 (default); ensemble: the batched sweep "
                          "of 64 runs of 64x64x128 in one context")
     args = ap.parse_args()

@@ -54,6 +54,7 @@ enum {
 };
 enum { PIC_EXT_NONE = 0, PIC_EXT_PLANAR_UNDULATOR = 1, PIC_EXT_PLANAR_UNDULATOR_3D = 2 };
 enum { PIC_PUSHER_BORIS = 0, PIC_PUSHER_VAY = 1 };
+enum { PIC_GATHER_MOMENTUM = 0, PIC_GATHER_ENERGY = 1 };
 
 typedef struct pic_ctx pic_ctx;
 
@@ -90,7 +91,12 @@ typedef struct {
  * boundaries bc, particle shape order 1 (CIC) or 2 (TSC).  Fields start at zero.  dt must
  * satisfy the Yee Courant limit dt < 1/sqrt(sum 1/dx_i^2).  On success *out owns all device
  * state (allocated through dev); on failure *out is NULL and the status says why
- * (pic_last_error(NULL) gives the message of a failed create). */
+ * (pic_last_error(NULL) gives the message of a failed create).
+ * A 2-D geometry (the x-z plane of the paper's runs, everything uniform along y) is a grid with
+ * ny = 1 and a periodic y: the particle shape then sums to one on the single y node, the
+ * Esirkepov current's y component becomes the out-of-plane current q w v_y (shape of the
+ * average x-z position), and the curl's y derivatives vanish.  Any periodic dim may be shorter
+ * than the stencil; its indices wrap modulo its size. */
 int pic_create(pic_ctx **out, pic_grid grid, const double dx[3], double dt, double gamma_boost,
                const pic_boundaries *bc, int shape_order, const pic_device *dev);
 
@@ -108,7 +114,7 @@ int pic_create_batch(pic_ctx **out, int runs, pic_grid grid, const double dx[3],
                      double gamma_boost, const pic_boundaries *bc, int shape_order,
                      const pic_device *dev);
 
-/* Tile size for the per-tile sort and the particle kernel (cells, each 2..16), number of
+/* Tile size for the per-tile sort and the particle kernel (cells, each 1..16), number of
  * steps between sorts (>= 1), and the margin (cells, 0..2) a particle may drift outside its
  * tile between sorts before it takes the slower global-memory path.  Defaults 8x8x8, 8, 1. */
 typedef struct {
@@ -233,6 +239,16 @@ int pic_step(pic_ctx *ctx, int64_t n);
  * lab-static plasma inside the undulator, seen from the RRF).  The adjoint needs Boris. */
 int pic_set_pusher(pic_ctx *ctx, int pusher);
 
+/* Field gather of every mobile species.  PIC_GATHER_MOMENTUM (default): each component is
+ * interpolated with the deposit's shape at its Yee point (the reading of the paper's scheme).
+ * PIC_GATHER_ENERGY: one order lower along the dims where the component is staggered (CIC -> nearest
+ * grid point, TSC -> CIC there), the transpose of the Esirkepov deposit: the x-shape of J_x is
+ * the lower-order shape at the half-integer nodes, so for a gradient field E = -grad_h phi the
+ * gathered E_x is exactly -d/dx of phi interpolated with the full shape, and B = curl_h A
+ * gathers to the curl of the gathered A.  The adjoint needs PIC_GATHER_MOMENTUM.  PIC_ERR_ARG
+ * for an unknown scheme; PIC_ERR_STATE while adjoint checkpoints are recorded. */
+int pic_set_gather(pic_ctx *ctx, int gather);
+
 /* Replay of captured step sequences in pic_step (on = 1, the default) or one launch per kernel
  * (on = 0).  The capture is redone when species, the external field or the tuning change; if
  * capturing fails the context falls back to launching. */
@@ -251,7 +267,7 @@ int pic_autotune(pic_ctx *ctx, int max_sort_every, int *sort_every_out);
 
 /* Autotuner of the tile size and the sort cadence together.  tiles: host int[n_tiles][3],
  * candidate tile sizes (the first is the reference, e.g. the current 8 x 8 x 8); each must pass
- * pic_set_tuning's checks (2..16 cells per dim, the region within shared memory, for an ensemble
+ * pic_set_tuning's checks (1..16 cells per dim, the region within shared memory, for an ensemble
  * a z size dividing the rows of a run), else PIC_ERR_ARG.  Every candidate runs whole periods of
  * the current cadence (>= 32 steps, the first step sorting on the new tiles), in two passes
  * (ascending, then descending); the fastest per step is kept (a candidate must beat the best

@@ -94,6 +94,7 @@ def lib():
                 "oracle_vay": (None, [d, d, pd, pd, pd]),
                 "osim_set_pusher": (None, [vp, i]),
                 "osim_set_threads": (i, [vp, i]),
+                "osim_set_gather": (None, [vp, i]),
                 "oracle_field_transform": (None, [pd, pd, d, pd, pd]),
                 "oracle_lab_to_boosted": (None, [d, pd, pd, pd, pd]),
                 "oracle_boosted_to_lab": (None, [d, pd, d, pd, pd, pd, pd]),
@@ -302,6 +303,10 @@ class Sim:
         """Threads of the particle loop (timing only; 1, the default, is the serial reference
         loop).  Returns the number used (1 without OpenMP)."""
         return self.L.osim_set_threads(self.h, int(n))
+
+    def set_gather(self, gather):
+        """0: momentum-conserving gather (default), 1: energy-conserving."""
+        self.L.osim_set_gather(self.h, int(gather))
 
     def set_pusher(self, pusher):
         """0: Boris (default), 1: Vay."""

@@ -74,6 +74,7 @@ typedef struct {
     osp sp[O_MAXSP];
     long dropped; /* deposit contributions outside a non-periodic grid (should stay 0) */
     int pusher;   /* 0: Boris, 1: Vay */
+    int gather;   /* 0: momentum-conserving (order everywhere), 1: energy-conserving */
     int threads;  /* > 1: the particle loop runs on that many OpenMP threads (timing only) */
 } osim;
 
@@ -84,6 +85,7 @@ typedef struct {
 static double o_shape(int order, double dd)
 {
     double a = fabs(dd);
+    if (order == 0) return (dd >= -0.5 && dd < 0.5) ? 1.0 : 0.0;   /* nearest grid point */
     if (order == 1) return a < 1.0 ? 1.0 - a : 0.0;
     if (a <= 0.5) return 0.75 - a * a;
     if (a < 1.5) return 0.5 * (1.5 - a) * (1.5 - a);
@@ -332,6 +334,7 @@ void osim_set_external(void *h, int type, double K, double lambda_u, double phas
 }
 
 void osim_set_pusher(void *h, int pusher) { ((osim *)h)->pusher = pusher; }
+void osim_set_gather(void *h, int gather) { ((osim *)h)->gather = gather; }
 
 void osim_external_at(void *h, double y, double zp, double tp, double *E, double *B)
 {
@@ -652,17 +655,22 @@ void oracle_vay(double qm, double dt, const double E[3], const double B[3], doub
 }
 
 /* Interpolate grid component f, whose nodes sit at index + stag (cells), to X with the
- * particle shape (same weighting as the deposit). */
+ * particle shape.  Momentum-conserving gather: the deposit's order in every dim.  Energy-
+ * conserving gather: one order lower along the dims where the component is staggered (the
+ * x-shape of the Esirkepov current J_x is the lower-order shape at the half-integer nodes, so
+ * E_x gathered this way is the transpose of the deposit; for a gradient field E = -grad_h phi it
+ * gives exactly -d/dx of phi interpolated with the full-order shape). */
 static double o_gather(const osim *s, const double *f, const double stag[3], const double X[3])
 {
-    double h = 0.5 * (s->order + 1);
     long lo[3], cnt[3];
     double wv[3][6];
     for (int d = 0; d < 3; d++) {
+        int ord = (s->gather == 1 && stag[d] != 0.0) ? s->order - 1 : s->order;
+        double h = 0.5 * (ord + 1);
         lo[d] = (long)floor(X[d] - stag[d] - h);
         long hi = (long)floor(X[d] - stag[d] + h);
         cnt[d] = hi - lo[d] + 1;
-        for (long a = 0; a < cnt[d]; a++) wv[d][a] = o_shape(s->order, (double)(lo[d] + a) + stag[d] - X[d]);
+        for (long a = 0; a < cnt[d]; a++) wv[d][a] = o_shape(ord, (double)(lo[d] + a) + stag[d] - X[d]);
     }
     double sum = 0.0;
     for (long c = 0; c < cnt[2]; c++)

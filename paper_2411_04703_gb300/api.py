@@ -22,6 +22,7 @@ PIC_BC_PERIODIC, PIC_BC_PML, PIC_BC_OPEN = 0, 1, 2
 PIC_FRAME_LAB, PIC_FRAME_BOOSTED = 0, 1
 PIC_EX, PIC_EY, PIC_EZ, PIC_BX, PIC_BY, PIC_BZ, PIC_JX, PIC_JY, PIC_JZ, PIC_RHO = range(10)
 PIC_EXT_NONE, PIC_EXT_PLANAR_UNDULATOR, PIC_EXT_PLANAR_UNDULATOR_3D = 0, 1, 2
+PIC_GATHER_MOMENTUM, PIC_GATHER_ENERGY = 0, 1
 ERRORS = {-1: "PIC_ERR_ARG", -2: "PIC_ERR_CUDA", -3: "PIC_ERR_ALLOC", -4: "PIC_ERR_STATE",
           -5: "PIC_ERR_DEVICE", -6: "PIC_ERR_CAPACITY"}
 MOMENT_NAMES = [
@@ -129,6 +130,7 @@ def lib(build_if_missing: bool = True):
             "pic_autotune_tiles": [vp, P(i), i, i, P(i), P(i)],
             "pic_use_graphs": [vp, i],
             "pic_set_pusher": [vp, i],
+            "pic_set_gather": [vp, i],
             "pic_resolution_factor": [vp, d, P(d), P(i)],
             "pic_resonant_wavenumber": [d, d, d, d, i, P(d)],
             "pic_checkpoint": [vp, i],
@@ -357,6 +359,10 @@ class Sim:
         r, ok = C.c_double(), C.c_int()
         self._check(self.L.pic_resolution_factor(self.h, float(lambda_lab), C.byref(r), C.byref(ok)))
         return r.value, bool(ok.value)
+
+    def set_gather(self, gather):
+        """PIC_GATHER_MOMENTUM (0, default) or PIC_GATHER_ENERGY (1)."""
+        self._check(self.L.pic_set_gather(self.h, int(gather)))
 
     def set_pusher(self, pusher):
         """PIC_PUSHER_BORIS (0, default) or PIC_PUSHER_VAY (1)."""

@@ -183,7 +183,7 @@ double shifts_due(const pic_ctx *c, int64_t n) { return std::floor(c->vw * (doub
 int check_tile(pic_ctx *c, const int T[3], int margin)
 {
     for (int d = 0; d < 3; d++)
-        if (T[d] < 2 || T[d] > 16) return fail(c, PIC_ERR_ARG, "tile sizes must be 2..16");
+        if (T[d] < 1 || T[d] > 16) return fail(c, PIC_ERR_ARG, "tile sizes must be 1..16");
     if (margin < 0 || margin > 2) return fail(c, PIC_ERR_ARG, "margin must be 0..2");
     int R3 = 1;
     for (int d = 0; d < 3; d++) R3 *= T[d] + 2 * margin + margin_lo(c) + margin_hi(c);
@@ -1172,6 +1172,18 @@ int pic_set_pusher(pic_ctx *c, int pusher)
     return PIC_OK;
 }
 
+int pic_set_gather(pic_ctx *c, int gather)
+{
+    int r = check_ctx(c);
+    if (r) return r;
+    if (gather != PIC_GATHER_MOMENTUM && gather != PIC_GATHER_ENERGY) return fail(c, PIC_ERR_ARG, "unknown gather scheme");
+    if (c->ad_on && gather != PIC_GATHER_MOMENTUM)
+        return fail(c, PIC_ERR_STATE, "the adjoint reverses the momentum-conserving gather");
+    drop_graph(c);   // captured launches hold the kernel variant
+    c->gather = gather;
+    return PIC_OK;
+}
+
 int pic_resolution_factor(const pic_ctx *c, double lambda_lab, double *r_rf, int *ok)
 {
     if (!c || !r_rf) return PIC_ERR_ARG;
@@ -1565,6 +1577,8 @@ int pic_checkpoint(pic_ctx *c, int every_k)
         return fail(c, PIC_ERR_ARG, "the adjoint needs an undulator without entrance ramp");
     if (c->ext_type == PIC_EXT_PLANAR_UNDULATOR_3D)
         return fail(c, PIC_ERR_ARG, "the adjoint is built for the 1-D planar undulator field");
+    if (c->gather != PIC_GATHER_MOMENTUM)
+        return fail(c, PIC_ERR_ARG, "the adjoint reverses the momentum-conserving gather");
     drop_graph(c);
     c->ad_on = 1;
     c->ad_every = every_k;

@@ -43,6 +43,16 @@ struct CellCode {
 __host__ __device__ __forceinline__ int zblock(int k, int nzr) { return (k / nzr) * nzr; }
 __host__ __device__ __forceinline__ int zwrap(int k, int b, int nzr) { return k < b ? k + nzr : (k >= b + nzr ? k - nzr : k); }
 
+// Index p of a periodic dim of n cells brought into [0, n): one step for the usual offsets of a
+// stencil, a remainder when the dim is shorter than the stencil (n = 1: a 2-D geometry).
+__host__ __device__ __forceinline__ int pwrap(int p, int n)
+{
+    if (p < 0) p += n;
+    else if (p >= n) p -= n;
+    if (p < 0 || p >= n) p = ((p % n) + n) % n;
+    return p;
+}
+
 struct GridDev {
     int n[3];
     int periodic[3];
@@ -258,6 +268,7 @@ struct pic_ctx {
     // CUDA graph of whole sort periods (no moving window, no injection, tracing off)
     int use_graphs = 1;
     int pusher = 0;               // PIC_PUSHER_*
+    int gather = 0;               // PIC_GATHER_*
     cudaGraphExec_t graph = nullptr;
     int64_t graph_steps = 0;      // steps one replay advances
     int64_t graph_kernels = 0;    // kernels one replay runs

@@ -25,7 +25,7 @@ namespace {
 
 constexpr int kAdjThreads = 256;
 
-__device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+__device__ __forceinline__ int wrapi(int i, int n) { return pwrap(i, n); }
 
 __device__ __forceinline__ long long nidx(const GridDev &g, int i, int j, int k)
 {

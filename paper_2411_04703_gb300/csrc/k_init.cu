@@ -232,8 +232,14 @@ __global__ void k_lattice_profile(PlaceP g, int d, int lo, int hi, int ppc, int 
             int ci;
             if (!place1(g, d, cell + (a + 0.5) / ppc, o, ci)) continue;
             double x = (double)i - ((double)ci + (double)o);
-            if (g.periodic[d]) x -= g.n[d] * rint(x / g.n[d]);
-            acc += shape_weight(order, x);
+            if (!g.periodic[d]) {
+                acc += shape_weight(order, x);
+                continue;
+            }
+            // every periodic image within the shape's reach (more than one when the dim has
+            // fewer cells than the stencil, e.g. n = 1 in a 2-D geometry)
+            x -= g.n[d] * rint(x / g.n[d]);
+            for (int m = -2; m <= 2; m++) acc += shape_weight(order, x + (double)m * g.n[d]);
         }
     out[i] = (float)acc;
 }

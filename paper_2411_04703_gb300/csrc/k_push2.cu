@@ -10,6 +10,8 @@ cudaError_t launch_push2_mobile_fixed(pic_ctx *c, int si, const ExtDev &ext);
 cudaError_t launch_push2_frozen_fixed(pic_ctx *c, int si, const ExtDev &ext);
 cudaError_t launch_push2_mobile_dyn(pic_ctx *c, int si, const ExtDev &ext);
 cudaError_t launch_push2_frozen_dyn(pic_ctx *c, int si, const ExtDev &ext);
+cudaError_t launch_push2_mobile_fixed_ec(pic_ctx *c, int si, const ExtDev &ext);
+cudaError_t launch_push2_mobile_dyn_ec(pic_ctx *c, int si, const ExtDev &ext);
 
 namespace {
 
@@ -38,12 +40,12 @@ __global__ void k_rho(SpeciesDev sp, GridDev g, float qv, float *rho)
                     bool ok = true;
                     for (int d = 0; d < 2; d++) {
                         if (q[d] < 0 || q[d] >= g.n[d]) {
-                            if (g.periodic[d]) q[d] = q[d] < 0 ? q[d] + g.n[d] : q[d] - g.n[d];
+                            if (g.periodic[d]) q[d] = pwrap(q[d], g.n[d]);
                             else ok = false;
                         }
                     }
                     if (q[2] < zb || q[2] >= zb + g.nzr) {
-                        if (g.periodic[2]) q[2] = zwrap(q[2], zb, g.nzr);
+                        if (g.periodic[2]) q[2] = zb + pwrap(q[2] - zb, g.nzr);
                         else ok = false;
                     }
                     if (ok)
@@ -96,8 +98,13 @@ cudaError_t launch_push(pic_ctx *c, int si, const ExtDev &ext)
 {
     if (c->order == 1) return launch_push_order1(c, si, ext);
     const bool fr = c->sp[si].frozen != 0;
-    if (push::default_region(c)) return fr ? launch_push2_frozen_fixed(c, si, ext) : launch_push2_mobile_fixed(c, si, ext);
-    return fr ? launch_push2_frozen_dyn(c, si, ext) : launch_push2_mobile_dyn(c, si, ext);
+    const bool ec = c->gather == PIC_GATHER_ENERGY;
+    if (push::default_region(c)) {
+        if (fr) return launch_push2_frozen_fixed(c, si, ext);
+        return ec ? launch_push2_mobile_fixed_ec(c, si, ext) : launch_push2_mobile_fixed(c, si, ext);
+    }
+    if (fr) return launch_push2_frozen_dyn(c, si, ext);
+    return ec ? launch_push2_mobile_dyn_ec(c, si, ext) : launch_push2_mobile_dyn(c, si, ext);
 }
 
 // Adds the charge density of species s to rho.

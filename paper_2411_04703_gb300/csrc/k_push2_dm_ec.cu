@@ -1,0 +1,8 @@
+// Second-order (TSC) particle kernel, mobile species, runtime-sized region, energy-conserving gather (see push_impl.cuh).
+#include "push_impl.cuh"
+
+namespace gbpic {
+
+cudaError_t launch_push2_mobile_dyn_ec(pic_ctx *c, int si, const ExtDev &ext) { return push::launch_variant<2, false, false, 1>(c, si, ext); }
+
+}  // namespace gbpic

@@ -65,6 +65,16 @@ template <int RX, int RY, int RZ> struct RegFix {
 // thus keeps full FP32 relative precision in its current.
 template <int ORDER> struct Shape;
 
+// Order 0 (nearest grid point), used only by the energy-conserving gather of the first-order
+// shape along a staggered dim: the half-integer node nearest to the offset o in [0, 1) is c + 1/2
+// (c - 1/2 when o = 0, the half-open convention of the shape).
+template <> struct Shape<0> {
+    static constexpr int N = 1;
+    __device__ __forceinline__ static void stag(float o, int &s, float w[1]) {
+        s = o > 0.f ? 0 : -1; w[0] = 1.f;
+    }
+};
+
 template <> struct Shape<1> {
     static constexpr int N = 2;   // gather nodes per dim
     static constexpr int L = 3;   // general Esirkepov window per dim
@@ -215,12 +225,12 @@ struct GlobAcc {
         for (int d = 0; d < 2; d++) {
             if (p[d] < 0 || p[d] >= g.n[d]) {
                 if (!g.periodic[d]) return -1;
-                p[d] = p[d] < 0 ? p[d] + g.n[d] : p[d] - g.n[d];
+                p[d] = pwrap(p[d], g.n[d]);
             }
         }
         if (p[2] < zb || p[2] >= zb + g.nzr) {
             if (!g.periodic[2]) return -1;
-            p[2] = zwrap(p[2], zb, g.nzr);
+            p[2] = zb + pwrap(p[2] - zb, g.nzr);
         }
         return ((long long)p[2] * g.n[1] + p[1]) * g.n[0] + p[0];
     }
@@ -238,24 +248,31 @@ struct GlobAcc {
     }
 };
 
-template <int N, class Acc>
-__device__ __forceinline__ float gather(const Acc &a, int comp, int sx, int sy, int sz,
-                                        const float *wx, const float *wy, const float *wz)
+template <int NX, int NY, int NZ, class Acc>
+__device__ __forceinline__ float gather3(const Acc &a, int comp, int sx, int sy, int sz,
+                                         const float *wx, const float *wy, const float *wz)
 {
     float s = 0.f;
 #pragma unroll
-    for (int k = 0; k < N; k++) {
+    for (int k = 0; k < NZ; k++) {
         float sk = 0.f;
 #pragma unroll
-        for (int j = 0; j < N; j++) {
+        for (int j = 0; j < NY; j++) {
             float sj = 0.f;
 #pragma unroll
-            for (int i = 0; i < N; i++) sj = fmaf(wx[i], a.f(comp, sx + i, sy + j, sz + k), sj);
+            for (int i = 0; i < NX; i++) sj = fmaf(wx[i], a.f(comp, sx + i, sy + j, sz + k), sj);
             sk = fmaf(wy[j], sj, sk);
         }
         s = fmaf(wz[k], sk, s);
     }
     return s;
+}
+
+template <int N, class Acc>
+__device__ __forceinline__ float gather(const Acc &a, int comp, int sx, int sy, int sz,
+                                        const float *wx, const float *wy, const float *wz)
+{
+    return gather3<N, N, N>(a, comp, sx, sy, sz, wx, wy, wz);
 }
 
 // ------------------------------------------------------------------ Esirkepov
@@ -351,23 +368,27 @@ __device__ __forceinline__ void deposit_simple(const Acc &acc, const float o[3],
 }
 
 // Gather, external field and Boris rotation of one particle: u^{n-1/2} -> u^{n+1/2} in mo.
-template <int ORDER, class Acc>
+// GATHER 0: momentum-conserving (the deposit's shape at each component's Yee point); GATHER 1:
+// energy-conserving (one order lower along the component's staggered dims: the transpose of the
+// Esirkepov deposit, whose J_x has the lower-order shape at the half-integer x nodes).
+template <int ORDER, class Acc, int GATHER = 0>
 __device__ __forceinline__ void push_u(const Acc &acc, const float o[3], const int c[3], float4 &mo,
                                        const SpeciesDev &sp, const ExtDev &ext)
 {
     using S = Shape<ORDER>;
-    constexpr int N = S::N;
+    using SS = Shape<GATHER ? ORDER - 1 : ORDER>;   // shape along staggered dims
+    constexpr int N = S::N, NS = SS::N;
     int su[3], ss[3];
-    float wu[3][N], ws[3][N];
+    float wu[3][N], ws[3][NS];
 #pragma unroll
-    for (int dd = 0; dd < 3; dd++) { S::unst(o[dd], su[dd], wu[dd]); S::stag(o[dd], ss[dd], ws[dd]); }
+    for (int dd = 0; dd < 3; dd++) { S::unst(o[dd], su[dd], wu[dd]); SS::stag(o[dd], ss[dd], ws[dd]); }
     float E[3], B[3];
-    E[0] = gather<N>(acc, 0, ss[0], su[1], su[2], ws[0], wu[1], wu[2]);
-    E[1] = gather<N>(acc, 1, su[0], ss[1], su[2], wu[0], ws[1], wu[2]);
-    E[2] = gather<N>(acc, 2, su[0], su[1], ss[2], wu[0], wu[1], ws[2]);
-    B[0] = gather<N>(acc, 3, su[0], ss[1], ss[2], wu[0], ws[1], ws[2]);
-    B[1] = gather<N>(acc, 4, ss[0], su[1], ss[2], ws[0], wu[1], ws[2]);
-    B[2] = gather<N>(acc, 5, ss[0], ss[1], su[2], ws[0], ws[1], wu[2]);
+    E[0] = gather3<NS, N, N>(acc, 0, ss[0], su[1], su[2], ws[0], wu[1], wu[2]);
+    E[1] = gather3<N, NS, N>(acc, 1, su[0], ss[1], su[2], wu[0], ws[1], wu[2]);
+    E[2] = gather3<N, N, NS>(acc, 2, su[0], su[1], ss[2], wu[0], wu[1], ws[2]);
+    B[0] = gather3<N, NS, NS>(acc, 3, su[0], ss[1], ss[2], wu[0], ws[1], ws[2]);
+    B[1] = gather3<NS, N, NS>(acc, 4, ss[0], su[1], ss[2], ws[0], wu[1], ws[2]);
+    B[2] = gather3<NS, NS, N>(acc, 5, ss[0], ss[1], su[2], ws[0], ws[1], wu[2]);
     if (ext.type == PIC_EXT_PLANAR_UNDULATOR || ext.type == PIC_EXT_PLANAR_UNDULATOR_3D) {
         float f = 1.f;
         if (ext.ramp_mode) {
@@ -431,12 +452,12 @@ __device__ __forceinline__ void push_u(const Acc &acc, const float o[3], const i
 // Gather, external field, Boris push (unless FROZEN) and move of one particle.  On return d
 // holds the push displacement (cells), s the cell shift, o1 the new offsets and c the new cell.
 // Returns false when the particle left through a non-periodic face (it becomes a dummy).
-template <int ORDER, bool FROZEN, class Acc>
+template <int ORDER, bool FROZEN, class Acc, int GATHER = 0>
 __device__ __forceinline__ bool push_move(const Acc &acc, const float o[3], int c[3], float4 &mo,
                                           const SpeciesDev &sp, const GridDev &g, const ExtDev &ext,
                                           int *err, float d[3], int s[3], float o1[3], int zb)
 {
-    if (!FROZEN) push_u<ORDER>(acc, o, c, mo, sp, ext);
+    if (!FROZEN) push_u<ORDER, Acc, GATHER>(acc, o, c, mo, sp, ext);
     const float u[3] = {mo.x, mo.y, mo.z};
     const float ig = rsqrtf(1.f + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
     if (!(ig > 0.f)) { atomicOr(err, ERR_NAN); return false; }
@@ -468,7 +489,7 @@ __device__ __forceinline__ bool stays_all(const float o[3], const float d[3], co
 }
 
 // Whole step of one particle on the global-memory path.
-template <int ORDER, bool FROZEN>
+template <int ORDER, bool FROZEN, int GATHER = 0>
 __device__ __forceinline__ void step_global(const SpeciesDev &sp, const GridDev &g, const FieldsDev &f,
                                             const ExtDev &ext, int *err, int p)
 {
@@ -482,7 +503,7 @@ __device__ __forceinline__ void step_global(const SpeciesDev &sp, const GridDev 
     GlobAcc acc{f.E, f.B, f.J, g, {c[0], c[1], c[2]}, err, zb};
     float d[3], o1[3];
     int s[3];
-    if (push_move<ORDER, FROZEN>(acc, o, c, mo, sp, g, ext, err, d, s, o1, zb)) {
+    if (push_move<ORDER, FROZEN, GlobAcc, GATHER>(acc, o, c, mo, sp, g, ext, err, d, s, o1, zb)) {
         const float fac[3] = {sp.cf[0] * mo.w, sp.cf[1] * mo.w, sp.cf[2] * mo.w};
         deposit_general<ORDER>(acc, o, d, s, fac);
         P = make_float4(o1[0], o1[1], o1[2], __int_as_float(g.cc.pack(c[0], c[1], c[2])));
@@ -527,19 +548,19 @@ __device__ __forceinline__ long long wrap_node(const GridDev &g, int x, int y, i
     for (int d = 0; d < 2; d++) {
         if (p[d] < 0 || p[d] >= g.n[d]) {
             if (!g.periodic[d]) return -1;
-            p[d] = p[d] < 0 ? p[d] + g.n[d] : p[d] - g.n[d];
+            p[d] = pwrap(p[d], g.n[d]);
         }
     }
     if (p[2] < zb || p[2] >= zb + g.nzr) {
         if (!g.periodic[2]) return -1;
-        p[2] = zwrap(p[2], zb, g.nzr);
+        p[2] = zb + pwrap(p[2] - zb, g.nzr);
     }
     return ((long long)p[2] * g.n[1] + p[1]) * g.n[0] + p[0];
 }
 
 // One CTA of kPushThreads per SM: the shared region of a tile holds most of the SM's shared
 // memory, and 1024 threads at 64 registers (a few spills) hide more latency than 512 at 122.
-template <int ORDER, bool FROZEN, class Reg>
+template <int ORDER, bool FROZEN, class Reg, int GATHER>
 __global__ void __launch_bounds__(kPushThreads, 1)
 k_push(SpeciesDev sp, GridDev g, TileDev t, FieldsDev f, ExtDev ext0, int *work, int *work_sparse, int *err, Reg reg)
 {
@@ -570,7 +591,7 @@ k_push(SpeciesDev sp, GridDev g, TileDev t, FieldsDev f, ExtDev ext0, int *work,
             const int p_begin = n_sorted + (item - n_tile_items) * chunk;
             const int p_end = min(p_begin + chunk, n_total);
             for (int p = p_begin + threadIdx.x; p < p_end; p += blockDim.x)
-                step_global<ORDER, FROZEN>(sp, g, f, ext, err, p);
+                step_global<ORDER, FROZEN, GATHER>(sp, g, f, ext, err, p);
             continue;
         }
 
@@ -648,7 +669,7 @@ k_push(SpeciesDev sp, GridDev g, TileDev t, FieldsDev f, ExtDev ext0, int *work,
                 fast = fast && r >= -t.M && r < t.T[dd] + t.M;
             }
             if (!fast) {
-                step_global<ORDER, FROZEN>(sp, g, f, ext, err, p);
+                step_global<ORDER, FROZEN, GATHER>(sp, g, f, ext, err, p);
                 break;
             }
             float4 mo = sp.mom[p];
@@ -657,7 +678,7 @@ k_push(SpeciesDev sp, GridDev g, TileDev t, FieldsDev f, ExtDev ext0, int *work,
             SmemAcc<Reg> acc{reg, sF, sJlo, sJhi, s_js, base};
             float d[3], o1[3];
             int s[3];
-            if (push_move<ORDER, FROZEN>(acc, o, c, mo, sp, g, ext, err, d, s, o1, zb)) {
+            if (push_move<ORDER, FROZEN, SmemAcc<Reg>, GATHER>(acc, o, c, mo, sp, g, ext, err, d, s, o1, zb)) {
                 const float fac[3] = {sp.cf[0] * mo.w, sp.cf[1] * mo.w, sp.cf[2] * mo.w};
 #pragma unroll
                 for (int k = 0; k < 3; k++) dm[k] = __float_as_uint(fabsf(d[k]));
@@ -750,7 +771,7 @@ k_push(SpeciesDev sp, GridDev g, TileDev t, FieldsDev f, ExtDev ext0, int *work,
         if (it >= n_sparse) break;
         const int tile = t.sparse_tiles[it];
         const int pe = t.cell_start[(tile + 1) * kpt];
-        for (int p = t.cell_start[tile * kpt] + lane; p < pe; p += 32) step_global<ORDER, FROZEN>(sp, g, f, ext, err, p);
+        for (int p = t.cell_start[tile * kpt] + lane; p < pe; p += 32) step_global<ORDER, FROZEN, GATHER>(sp, g, f, ext, err, p);
     }
 }
 
@@ -766,14 +787,14 @@ static __global__ void k_dlim_update(float *dlim, unsigned *dmax, float l0, floa
     dmax[k] = 0u;
 }
 
-template <int ORDER, bool FROZEN, class Reg>
+template <int ORDER, bool FROZEN, int GATHER, class Reg>
 cudaError_t launch_t(pic_ctx *c, int si, const ExtDev &ext, Reg reg, int R3)
 {
     const Species &s = c->sp[si];
     TileDev t = tile_dev(c, s);
     const size_t smem = (size_t)(FROZEN ? 0 : 6) * R3 * sizeof(float) + (size_t)3 * R3 * 2 * sizeof(int) +
                         (size_t)kQueue * 8 * sizeof(float);
-    auto kern = k_push<ORDER, FROZEN, Reg>;
+    auto kern = k_push<ORDER, FROZEN, Reg, GATHER>;
     // attribute and occupancy once per kernel and region size (nothing but launches is then issued
     // while a step sequence is captured into a CUDA graph).  The cache is shared by every context
     // of the process: host threads driving contexts at once take it under a lock, and the shared-
@@ -824,21 +845,21 @@ inline bool default_region(const pic_ctx *c)
 }
 
 // One kernel variant: shape order, frozen or mobile species, compile-time (FIXED) or runtime
-// region.  The second-order variants each sit in a translation unit of their own, so that the
-// build compiles them in parallel.
-template <int ORDER, bool FROZEN, bool FIXED>
+// region, gather scheme (mobile species).  The second-order variants each sit in a translation
+// unit of their own, so that the build compiles them in parallel.
+template <int ORDER, bool FROZEN, bool FIXED, int GATHER = 0>
 cudaError_t launch_variant(pic_ctx *c, int si, const ExtDev &ext)
 {
     if constexpr (FIXED) {
         constexpr int R = 8 + 2 * 1 + (ORDER == 1 ? 3 : 5);
         RegFix<R, R, R> reg;
         constexpr int R3 = plane_pitch(R, R) * R;
-        return launch_t<ORDER, FROZEN>(c, si, ext, reg, R3);
+        return launch_t<ORDER, FROZEN, GATHER>(c, si, ext, reg, R3);
     } else {
         const TileDev t = tile_dev(c, c->sp[si]);
         const int P2 = plane_pitch(t.R[0], t.R[1]);
         RegDyn reg{t.R[0], t.R[1], P2, P2 * t.R[2]};
-        return launch_t<ORDER, FROZEN>(c, si, ext, reg, reg.R3);
+        return launch_t<ORDER, FROZEN, GATHER>(c, si, ext, reg, reg.R3);
     }
 }
 
@@ -846,9 +867,13 @@ template <int ORDER>
 cudaError_t launch_order(pic_ctx *c, int si, const ExtDev &ext)
 {
     const bool fr = c->sp[si].frozen != 0;
-    if (default_region(c))
-        return fr ? launch_variant<ORDER, true, true>(c, si, ext) : launch_variant<ORDER, false, true>(c, si, ext);
-    return fr ? launch_variant<ORDER, true, false>(c, si, ext) : launch_variant<ORDER, false, false>(c, si, ext);
+    const bool ec = c->gather == PIC_GATHER_ENERGY;
+    if (default_region(c)) {
+        if (fr) return launch_variant<ORDER, true, true>(c, si, ext);
+        return ec ? launch_variant<ORDER, false, true, 1>(c, si, ext) : launch_variant<ORDER, false, true>(c, si, ext);
+    }
+    if (fr) return launch_variant<ORDER, true, false>(c, si, ext);
+    return ec ? launch_variant<ORDER, false, false, 1>(c, si, ext) : launch_variant<ORDER, false, false>(c, si, ext);
 }
 
 }  // namespace push

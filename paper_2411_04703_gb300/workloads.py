@@ -211,6 +211,32 @@ def mini_plasma(seed=12, grid=(28, 26, 52), n_beam=4000, steps=20):
     return w
 
 
+def plasma_buncher_2d(grid=(1024, 1, 2048), n_beam=1048576, steps=5000, seed=6, pml=10, ppc=(2, 1, 2),
+                      name="plasma buncher 2-D 1024x2048 (x-z), 1M beam + 4 ppc plasma, TSC") -> Workload:
+    """The plasma buncher in the paper's 2-D geometry (x-z plane, uniform along y: ny = 1 with a
+    periodic y), 4 particles per cell as in the paper's 2-D plasma runs (Table I), transverse
+    PML in x, moving window along z."""
+    w = plasma_buncher(grid=grid, n_beam=n_beam, steps=steps, seed=seed, pml=pml, ppc=ppc, name=name)
+    w.bc = ((PML, PML), (PERIODIC, PERIODIC), (OPEN, OPEN))
+    lo, hi = 2, 3
+    w.plasma = dataclasses.replace(w.plasma, xrange=(lo, grid[0] - hi, 0, 1))
+    w.beam.origin = (grid[0] / 2, 0.5, 0.75 * grid[2])
+    w.tile = (8, 1, 8)
+    return w
+
+
+def mini_plasma_2d(seed=16, grid=(28, 1, 52), n_beam=3000, steps=20):
+    """The oracle-sized 2-D plasma buncher (x-z, ny = 1): 5 um longitudinal cells (the window
+    shifts every ~6 steps), 2x1x2 particles per cell, a short beam."""
+    w = mini_plasma(seed=seed, grid=grid, n_beam=n_beam, steps=steps)
+    w.name = f"mini plasma buncher 2-D {grid[0]}x{grid[2]}"
+    w.bc = ((PML, PML), (PERIODIC, PERIODIC), (OPEN, OPEN))
+    w.plasma = dataclasses.replace(w.plasma, ppc=(2, 1, 2), xrange=(2, grid[0] - 3, 0, 1))
+    w.beam.origin = (grid[0] / 2, 0.5, 0.6 * grid[2])
+    w.tile = (8, 1, 8)
+    return w
+
+
 def mini_long_undulator(seed=13):
     w = long_undulator(grid=(24, 20, 48), n_beam=4000, steps=20, seed=seed, pml=4,
                        name="mini long undulator 24x20x48")

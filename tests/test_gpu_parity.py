@@ -65,6 +65,7 @@ CASES = {
     "long_undulator_tsc_pml_ramp": lambda: W.mini_long_undulator(),
     "vacuum_tsc_undulator_3d": lambda: _und3d(W.mini_vacuum(order=2)),
     "long_undulator_3d_pml_ramp": lambda: _und3d(W.mini_long_undulator()),
+    "plasma_2d_tsc_pml_window": lambda: W.mini_plasma_2d(),
 }
 
 
@@ -109,6 +110,34 @@ def test_one_step_on_other_tiles_from_identical_state(case, tile):
         assert r["u_rel_err"] < TOL_STEP, (name, r)
     f = parity.compare_fields(sim, o)
     assert max(f.values()) < TOL_STEP, f
+
+
+@pytest.mark.parametrize("case", ["vacuum_cic", "vacuum_tsc", "plasma_tsc_pml_window", "plasma_2d_tsc_pml_window"])
+def test_one_step_energy_conserving_gather_from_identical_state(case):
+    # the energy-conserving gather (one order lower along each component's staggered dims)
+    w = CASES[case]()
+    sim, ids = api.from_workload(w)
+    sim.set_gather(api.PIC_GATHER_ENERGY)
+    random_fields(sim, w, seed=43)
+    o, oid = parity.oracle_from_gpu(w, sim, ids)
+    o.set_gather(1)
+    sim.step(1)
+    sim.sync()
+    o.step(1)
+    for name in ids:
+        r = parity.compare_species(w, sim, ids[name], o, oid[name])
+        assert r["only_gpu"] == 0 and r["only_oracle"] == 0 and r["cell_mismatch"] == 0, (name, r)
+        assert r["u_rel_err"] < TOL_STEP, (name, r)
+    f = parity.compare_fields(sim, o)
+    assert max(f.values()) < TOL_STEP, f
+    # and it is not the momentum-conserving result (the random fields vary on the grid scale)
+    sim2, ids2 = api.from_workload(w)
+    random_fields(sim2, w, seed=43)
+    sim2.step(1)
+    sim2.sync()
+    key = "beam" if "beam" in ids else "plasma_e"
+    du = np.max(np.abs(sim.get_particles(ids[key])["u"] - sim2.get_particles(ids2[key])["u"]))
+    assert du > 0.0
 
 
 @pytest.mark.parametrize("case", ["vacuum_tsc", "plasma_tsc_pml_window"])

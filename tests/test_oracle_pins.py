@@ -898,3 +898,153 @@ def test_3d_undulator_canonical_momentum_off_axis():
         X, U = X1, U1
     # the off-axis electron was pushed towards the axis (y decreased) by the cosh focusing
     assert X[0, 1] * dy - 0.5 * ny * dy < y_off
+
+
+# ------------------------------------------------------------------ 2-D geometry (ny = 1)
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_two_d_grid_equals_a_y_uniform_three_d_run(order):
+    # The paper's runs are 2-D (x-z).  A grid with ny = 1 and periodic y is that geometry: it must
+    # reproduce a 3-D run (ny = 4, periodic) whose particles are copies of the 2-D ones at
+    # y = y0 + m (m = 0..3, one copy per y cell, each of the 2-D weight: the same density) and
+    # whose fields are uniform in y.  The copies' shapes sum to one on every y node (partition of
+    # unity), so the 3-D fields stay uniform in y and equal the 2-D fields, and every copy's
+    # momentum equals its 2-D particle's.
+    nx, nz, ny3 = 12, 14, 4
+    d = (0.6, 0.5, 0.8)
+    dt = 0.5 / math.sqrt(sum(1 / v ** 2 for v in d))
+    rng = np.random.default_rng(60 + order)
+    n = 200
+    X = np.stack([rng.uniform(0, nx, n), rng.uniform(0, 1, n), rng.uniform(0, nz, n)], 1)
+    U = rng.normal(size=(n, 3)) * 0.5
+    W = rng.uniform(0.5, 1.5, n) * 0.05
+    F = [0.01 * rng.standard_normal((nz, nx)) for _ in range(6)]
+    s2 = oracle.Sim((nx, 1, nz), d, dt, 2.0, order=order)
+    s3 = oracle.Sim((nx, ny3, nz), d, dt, 2.0, order=order)
+    a = s2.add_species(-1.0, 1.0)
+    b = s3.add_species(-1.0, 1.0)
+    s2.set_state(a, X, U, W, np.arange(n))
+    X3 = np.concatenate([X + np.array([0.0, m, 0.0]) for m in range(ny3)])
+    s3.set_state(b, X3, np.tile(U, (ny3, 1)), np.tile(W, ny3), np.arange(ny3 * n))
+    for c in range(6):
+        s2.set_field(c, F[c][:, None, :])
+        s3.set_field(c, np.repeat(F[c][:, None, :], ny3, axis=1))
+    for _ in range(5):
+        s2.step(1)
+        s3.step(1)
+    for c in range(9):
+        f2 = s2.field(c)[:, 0, :]
+        f3 = s3.field(c)
+        scale = np.max(np.abs(f2)) + 1e-300
+        for m in range(ny3):
+            np.testing.assert_allclose(f3[:, m, :], f2, rtol=0, atol=1e-12 * scale)
+    X2o, U2o, _, id2 = s2.particles(a)
+    X3o, U3o, _, id3 = s3.particles(b)
+    for m in range(ny3):
+        sl = (id3 >= m * n) & (id3 < (m + 1) * n)
+        o3 = np.argsort(id3[sl])
+        np.testing.assert_allclose(U3o[sl][o3], U2o[np.argsort(id2)], rtol=0, atol=1e-12)
+        np.testing.assert_allclose(X3o[sl][o3][:, [0, 2]], X2o[np.argsort(id2)][:, [0, 2]], rtol=0, atol=1e-12)
+
+
+def test_two_d_out_of_plane_current_is_q_w_v_y():
+    # In 2-D the Esirkepov y current of one particle moving by (dx, dy, dz) in a step is the
+    # out-of-plane current q w (dy/dt) times the x-z shape averaged the Esirkepov way; summed over
+    # the plane it is exactly q w dy / (dt V) (total-current identity), whatever the in-plane move.
+    d = (0.6, 0.5, 0.8)
+    dt = 0.4
+    for order in (1, 2):
+        s = oracle.Sim((10, 1, 10), d, dt, 1.0 + 1e-12, order=order)
+        s.add_species(-1.0, 1.0)
+        X0 = np.array([4.3, 0.2, 5.1])
+        for dX in ([0.3, 0.4, -0.2], [0.0, -0.7, 0.45], [0.6, 0.1, 0.0]):
+            X1 = X0 + np.array(dX)
+            s.deposit_one(-0.7, X0, X1)
+            V = d[0] * d[1] * d[2]
+            Jy = s.field(JY)
+            assert np.sum(Jy) == pytest.approx(-0.7 * dX[1] * d[1] / (dt * V), rel=1e-12, abs=1e-14)
+            assert np.sum(s.field(JX)) == pytest.approx(-0.7 * dX[0] * d[0] / (dt * V), rel=1e-12, abs=1e-14)
+
+
+# ------------------------------------------------------------------ energy-conserving gather
+
+def _bspline(order, x):
+    a = np.abs(x)
+    if order == 1:
+        return np.where(a < 1.0, 1.0 - a, 0.0)
+    return np.where(a <= 0.5, 0.75 - a * a, np.where(a < 1.5, 0.5 * (1.5 - a) ** 2, 0.0))
+
+
+def _interp_nodes(phi, X, order):
+    # Phi(X) = sum_ijk phi_ijk S(X - i) S(Y - j) S(Z - k) on a periodic grid (phi[k, j, i])
+    nz, ny, nx = phi.shape
+    out = 0.0
+    base = [int(np.floor(v)) for v in X]
+    for dk in range(-2, 4):
+        for dj in range(-2, 4):
+            for di in range(-2, 4):
+                i, j, k = base[0] + di, base[1] + dj, base[2] + dk
+                w = _bspline(order, X[0] - i) * _bspline(order, X[1] - j) * _bspline(order, X[2] - k)
+                if w != 0.0:
+                    out += w * phi[k % nz, j % ny, i % nx]
+    return out
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_energy_conserving_gather_of_a_gradient_is_the_derivative_of_the_interpolated_potential(order):
+    # E = -grad_h phi on the Yee grid (E_x at i+1/2 from phi(i+1) - phi(i), ...).  The energy-
+    # conserving gather (one order lower along the staggered dim) gives exactly -dPhi/dx of phi
+    # interpolated with the full-order shape; the momentum-conserving gather does not.
+    grid, d = (8, 7, 9), (0.6, 0.5, 0.8)
+    rng = np.random.default_rng(70 + order)
+    phi = rng.standard_normal((grid[2], grid[1], grid[0]))
+    Ex = -(np.roll(phi, -1, 2) - phi) / d[0]
+    Ey = -(np.roll(phi, -1, 1) - phi) / d[1]
+    Ez = -(np.roll(phi, -1, 0) - phi) / d[2]
+    s = oracle.Sim(grid, d, 0.1, 1.0 + 1e-12, order=order)
+    for c, f in enumerate((Ex, Ey, Ez)):
+        s.set_field(c, f)
+    h = 1e-6
+    worst_mc = 0.0
+    for _ in range(12):
+        X = rng.uniform(0, 1, 3) * np.array(grid)
+        grad = []
+        for dd in range(3):
+            e = np.zeros(3)
+            e[dd] = h
+            grad.append((_interp_nodes(phi, X + e, order) - _interp_nodes(phi, X - e, order)) / (2 * h * d[dd]))
+        s.set_gather(1)
+        E = s.gather_at(X)[:3]
+        np.testing.assert_allclose(E, -np.array(grad), rtol=0, atol=1e-6 * (1 + np.max(np.abs(grad))))
+        s.set_gather(0)
+        worst_mc = max(worst_mc, float(np.max(np.abs(s.gather_at(X)[:3] + np.array(grad)))))
+    assert worst_mc > 1e-3       # the momentum-conserving gather is not this transpose
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_energy_conserving_gather_of_a_curl_is_the_curl_of_the_gathered_potential(order):
+    # A on the E positions, B = curl_h A on the B positions: the energy-conserving gather of B
+    # equals the curl (in particle position) of the energy-conserving gather of A, so the B
+    # components use the shapes consistent with the E components
+    grid, d = (8, 7, 9), (0.6, 0.5, 0.8)
+    rng = np.random.default_rng(80 + order)
+    Ax, Ay, Az = (rng.standard_normal((grid[2], grid[1], grid[0])) for _ in range(3))
+    fwd = lambda f, ax, dd: (np.roll(f, -1, ax) - f) / dd
+    Bx = fwd(Az, 1, d[1]) - fwd(Ay, 0, d[2])
+    By = fwd(Ax, 0, d[2]) - fwd(Az, 2, d[0])
+    Bz = fwd(Ay, 2, d[0]) - fwd(Ax, 1, d[1])
+    s = oracle.Sim(grid, d, 0.1, 1.0 + 1e-12, order=order)
+    for c, f in enumerate((Ax, Ay, Az, Bx, By, Bz)):
+        s.set_field(c, f)
+    s.set_gather(1)
+    h = 1e-6
+    for _ in range(12):
+        X = rng.uniform(0, 1, 3) * np.array(grid)
+        g = s.gather_at(X)
+        dA = np.zeros((3, 3))          # dA[c, dd] = d A_c / d x_dd (physical units)
+        for dd in range(3):
+            e = np.zeros(3)
+            e[dd] = h
+            dA[:, dd] = (s.gather_at(X + e)[:3] - s.gather_at(X - e)[:3]) / (2 * h * d[dd])
+        curl = np.array([dA[2, 1] - dA[1, 2], dA[0, 2] - dA[2, 0], dA[1, 0] - dA[0, 1]])
+        np.testing.assert_allclose(g[3:], curl, rtol=0, atol=1e-6 * (1 + np.max(np.abs(curl))))
