@@ -249,6 +249,22 @@ int pic_set_pusher(pic_ctx *ctx, int pusher);
  * for an unknown scheme; PIC_ERR_STATE while adjoint checkpoints are recorded. */
 int pic_set_gather(pic_ctx *ctx, int gather);
 
+/* Artificial neutralising ions (Sec. "Electron propagation in vacuum and under external field":
+ * a background of ions compensating the beam's charge, damped linearly over T_ion so that the
+ * beam's fields build up without the kick of a sudden charge).  From the current step, a static
+ * charge density -rho_s (rho_s: species species_id's density now, with the deposit's shape)
+ * fades to zero linearly over T_ion (normalised time).  Reading (the paper does not say how
+ * Gauss's law survives the fading): in a charge-conserving scheme a charge fades only through a
+ * current, so the ions carry J_z with div J = -d rho_ion/dt, J_z(i, j, k + 1/2) = -(dz/T_ion)
+ * sum_{k' <= k} rho_s(i, j, k'), the prefix along z from the low face (the current leaves through
+ * the high z face).  On a periodic z the column mean of rho_s cannot leave the box and stays as a
+ * uniform neutralising background.  Fields must start at zero (the total charge is zero then);
+ * the ions move down with a moving window.  Gauss's law div E = rho_particles + rho_ion(t) then
+ * holds to rounding at every node through the ramp.  T_ion <= 0 removes the ions.  Replay of
+ * captured steps (pic_use_graphs) is off while they exist.  PIC_ERR_ARG for an unknown species;
+ * PIC_ERR_STATE while adjoint checkpoints are recorded. */
+int pic_set_ion_ramp(pic_ctx *ctx, int species_id, double T_ion);
+
 /* Replay of captured step sequences in pic_step (on = 1, the default) or one launch per kernel
  * (on = 0).  The capture is redone when species, the external field or the tuning change; if
  * capturing fails the context falls back to launching. */

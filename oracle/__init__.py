@@ -95,6 +95,7 @@ def lib():
                 "osim_set_pusher": (None, [vp, i]),
                 "osim_set_threads": (i, [vp, i]),
                 "osim_set_gather": (None, [vp, i]),
+                "osim_set_ion_ramp": (None, [vp, i, d]),
                 "oracle_field_transform": (None, [pd, pd, d, pd, pd]),
                 "oracle_lab_to_boosted": (None, [d, pd, pd, pd, pd]),
                 "oracle_boosted_to_lab": (None, [d, pd, d, pd, pd, pd, pd]),
@@ -303,6 +304,10 @@ class Sim:
         """Threads of the particle loop (timing only; 1, the default, is the serial reference
         loop).  Returns the number used (1 without OpenMP)."""
         return self.L.osim_set_threads(self.h, int(n))
+
+    def set_ion_ramp(self, sid, T):
+        """Artificial ions compensating species sid now, faded linearly over T (T <= 0: none)."""
+        self.L.osim_set_ion_ramp(self.h, int(sid), float(T))
 
     def set_gather(self, gather):
         """0: momentum-conserving gather (default), 1: energy-conserving."""

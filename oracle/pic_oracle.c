@@ -75,6 +75,9 @@ typedef struct {
     long dropped; /* deposit contributions outside a non-periodic grid (should stay 0) */
     int pusher;   /* 0: Boris, 1: Vay */
     int gather;   /* 0: momentum-conserving (order everywhere), 1: energy-conserving */
+    /* artificial neutralising ions fading over [ion_t0, ion_t0 + ion_T]: their current density
+     * is ion_G / ion_T (z component, at the E_z points) while they fade */
+    double *ion_G, ion_t0, ion_T;
     int threads;  /* > 1: the particle loop runs on that many OpenMP threads (timing only) */
 } osim;
 
@@ -193,6 +196,7 @@ void osim_destroy(void *h)
         free(p->X); free(p->U); free(p->W); free(p->id); free(p->alive);
     }
     free(s->zprof); free(s->nprof_v);
+    free(s->ion_G);
     free(s);
 }
 
@@ -925,6 +929,15 @@ static void o_window_shift(osim *s)
             if (!o_inside(s, &p->X[3 * i])) p->alive[i] = 0;
         }
     }
+    if (s->ion_G) {
+        /* the artificial ions move with the window: the z prefix of the shifted density is the old
+         * prefix one plane up minus the dropped plane's part; no ions enter at the front */
+        for (long c = 0; c < plane; c++) {
+            double g0 = s->ion_G[c];
+            for (long k = 0; k + 1 < nz; k++) s->ion_G[k * plane + c] = s->ion_G[(k + 1) * plane + c] - g0;
+            if (nz > 1) s->ion_G[(nz - 1) * plane + c] = s->ion_G[(nz - 2) * plane + c];
+        }
+    }
     s->shifts++;
 }
 
@@ -938,10 +951,23 @@ static long o_shifts_due(const osim *s, long n)
  * then fields to n+1; then the window and the plasma are brought to time n+1 (window shifts
  * due by then, lattice planes that crossed the front threshold injected), so that the state
  * at every time n has floor(v_w n dt / dz) shifts and its full plasma lattice. */
+/* Current of the fading artificial ions during step n (t_n to t_n + dt): the part of the ramp
+ * the step covers, as a step average. */
+static void o_ion_current(osim *s)
+{
+    if (!s->ion_G) return;
+    double t0 = (double)s->step * s->dt, t1 = t0 + s->dt;
+    double a = t0 > s->ion_t0 ? t0 : s->ion_t0, b = t1 < s->ion_t0 + s->ion_T ? t1 : s->ion_t0 + s->ion_T;
+    if (b <= a) return;
+    double f = (b - a) / (s->ion_T * s->dt);
+    for (long i = 0; i < s->ncell; i++) s->F[O_JZ][i] += f * s->ion_G[i];
+}
+
 static void o_step(osim *s)
 {
     for (int f = O_JX; f <= O_JZ; f++) memset(s->F[f], 0, s->ncell * sizeof(double));
     for (int q = 0; q < s->nsp; q++) o_push_species(s, &s->sp[q]);
+    o_ion_current(s);
     osim_fdtd(s);
     s->step++;
     if (s->moving) {
@@ -964,13 +990,14 @@ void osim_step(void *h, long nsteps)
 long osim_dropped(void *h) { return ((osim *)h)->dropped; }
 
 /* Charge density at the nodes from every live particle: rho = sum q w S(node - X) / V. */
-void osim_rho(void *h, double *rho)
+/* Charge density of species q (all species: q < 0) at the nodes, with the deposit's shape. */
+static void o_rho(const osim *s, int only, double *rho)
 {
-    osim *s = (osim *)h;
     memset(rho, 0, s->ncell * sizeof(double));
     double V = s->d[0] * s->d[1] * s->d[2], h2 = 0.5 * (s->order + 1);
     for (int q = 0; q < s->nsp; q++) {
-        osp *p = &s->sp[q];
+        if (only >= 0 && q != only) continue;
+        const osp *p = &s->sp[q];
         for (long i = 0; i < p->n; i++) {
             if (!p->alive[i]) continue;
             const double *X = &p->X[3 * i];
@@ -989,6 +1016,46 @@ void osim_rho(void *h, double *rho)
                     }
         }
     }
+}
+
+void osim_rho(void *h, double *rho) { o_rho((const osim *)h, -1, rho); }
+
+/* Artificial neutralising ions (Sec. "Electron propagation in vacuum and under external field"):
+ * a static background compensating the charge of species spi at the current time, faded
+ * linearly to zero over T (the paper's T_ion).  Reading: a charge can only fade in a
+ * charge-conserving scheme through a current, so the ions carry J_z with div J = -d rho_ion/dt:
+ * J_z(i, j, k + 1/2) = -(dz / T) sum_{k' <= k} rho'(i, j, k'), the prefix along z from the low
+ * face, while they fade.  rho' is the species' density; on a periodic z it is taken relative to
+ * each column's mean (the net column charge of a periodic box cannot leave it: that mean stays as
+ * the usual uniform neutralising background).  Fields start consistent: E = 0 with total charge
+ * zero.  T <= 0 removes the ions at once (no current). */
+void osim_set_ion_ramp(void *h, int spi, double T)
+{
+    osim *s = (osim *)h;
+    free(s->ion_G);
+    s->ion_G = NULL;
+    if (!(T > 0.0)) return;
+    double *rho = (double *)malloc(s->ncell * sizeof(double));
+    o_rho(s, spi, rho);
+    s->ion_G = (double *)calloc(s->ncell, sizeof(double));
+    long nx = s->n[0], ny = s->n[1], nz = s->n[2];
+    int zper = s->bc[2][0] == O_PERIODIC;
+    for (long j = 0; j < ny; j++)
+        for (long i = 0; i < nx; i++) {
+            double mean = 0.0;
+            if (zper) {
+                for (long k = 0; k < nz; k++) mean += rho[(k * ny + j) * nx + i];
+                mean /= (double)nz;
+            }
+            double acc = 0.0;
+            for (long k = 0; k < nz; k++) {
+                acc += rho[(k * ny + j) * nx + i] - mean;
+                s->ion_G[(k * ny + j) * nx + i] = -s->d[2] * acc;
+            }
+        }
+    free(rho);
+    s->ion_t0 = (double)s->step * s->dt;
+    s->ion_T = T;
 }
 
 /* Discrete divergence of E at the nodes (backward differences matching the Yee stagger). */

@@ -131,6 +131,7 @@ def lib(build_if_missing: bool = True):
             "pic_use_graphs": [vp, i],
             "pic_set_pusher": [vp, i],
             "pic_set_gather": [vp, i],
+            "pic_set_ion_ramp": [vp, i, d],
             "pic_resolution_factor": [vp, d, P(d), P(i)],
             "pic_resonant_wavenumber": [d, d, d, d, i, P(d)],
             "pic_checkpoint": [vp, i],
@@ -359,6 +360,10 @@ class Sim:
         r, ok = C.c_double(), C.c_int()
         self._check(self.L.pic_resolution_factor(self.h, float(lambda_lab), C.byref(r), C.byref(ok)))
         return r.value, bool(ok.value)
+
+    def set_ion_ramp(self, species_id, T_ion):
+        """Artificial ions compensating species_id now, faded linearly over T_ion (<= 0: none)."""
+        self._check(self.L.pic_set_ion_ramp(self.h, int(species_id), float(T_ion)))
 
     def set_gather(self, gather):
         """PIC_GATHER_MOMENTUM (0, default) or PIC_GATHER_ENERGY (1)."""

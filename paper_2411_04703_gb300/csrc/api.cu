@@ -920,6 +920,15 @@ int step_once(pic_ctx *c)
         TraceScope ts(c, c->sp[si].frozen ? TR_PUSH_FROZEN : TR_PUSH);
         CK(launch_push(c, si, ext));
     }
+    if (c->ion_G) {
+        // the fading artificial ions' current, averaged over the part of the ramp this step covers
+        const double t0 = (double)c->step * c->dt, t1 = t0 + c->dt;
+        const double a = std::max(t0, c->ion_t0), b = std::min(t1, c->ion_t0 + c->ion_T);
+        if (b > a) {
+            TraceScope ts(c, TR_OTHER);
+            CK(launch_ion_current(c, (float)((b - a) / (c->ion_T * c->dt))));
+        }
+    }
     {
         TraceScope ts(c, TR_FIELDS);
         CK(launch_fdtd_b(c, (float)(0.5 * c->dt)));
@@ -937,6 +946,7 @@ int step_once(pic_ctx *c)
             CK(launch_shift_fields(c));
             for (int si = 0; si < c->nsp; si++)
                 CK(c->sp[si].lattice ? launch_lattice_shift(c, si) : launch_shift_particles(c, si));
+            if (c->ion_G) CK(launch_ion_shift(c));
             c->shifts++;
         }
     }
@@ -948,7 +958,7 @@ int step_once(pic_ctx *c)
 // changes between periods: no moving window, no plasma injection (periodic z), tracing off.
 bool graph_eligible(const pic_ctx *c)
 {
-    if (!c->use_graphs || c->moving || c->trace_on || c->nsp == 0 || c->ad_on) return false;
+    if (!c->use_graphs || c->moving || c->trace_on || c->nsp == 0 || c->ad_on || c->ion_G) return false;
     if (c->plasma && c->bc[2][0] != PIC_BC_PERIODIC) return false;
     return true;
 }
@@ -1169,6 +1179,33 @@ int pic_set_pusher(pic_ctx *c, int pusher)
     if (c->ad_on && pusher != PIC_PUSHER_BORIS) return fail(c, PIC_ERR_STATE, "the adjoint reverses the Boris push");
     drop_graph(c);   // captured launches hold the species parameters
     c->pusher = pusher;
+    return PIC_OK;
+}
+
+int pic_set_ion_ramp(pic_ctx *c, int species_id, double T_ion)
+{
+    int r = check_ctx(c);
+    if (r) return r;
+    if (species_id < 0 || species_id >= c->nsp) return fail(c, PIC_ERR_ARG, "no such species");
+    if (c->ad_on) return fail(c, PIC_ERR_STATE, "the adjoint does not differentiate the artificial ions");
+    drop_graph(c);
+    if (!(T_ion > 0.0)) {
+        dfree(c, c->ion_G);
+        c->ion_G = nullptr;
+        return PIC_OK;
+    }
+    if (!c->ion_G && (r = alloc_zero(c, &c->ion_G, c->ncell))) return r;
+    if (!c->rho && (r = alloc_zero(c, &c->rho, c->ncell))) return r;
+    CK(cudaMemsetAsync(c->rho, 0, sizeof(float) * c->ncell, c->stream));
+    {
+        RecordView v;
+        if ((r = record_view(c, species_id, v))) return r;
+        CK(launch_rho(c, v.s, c->rho));
+    }
+    CK(launch_ion_prefix(c, c->rho, c->ion_G));
+    CK(cudaStreamSynchronize(c->stream));
+    c->ion_t0 = (double)c->step * c->dt;
+    c->ion_T = T_ion;
     return PIC_OK;
 }
 

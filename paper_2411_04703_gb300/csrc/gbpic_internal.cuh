@@ -269,6 +269,9 @@ struct pic_ctx {
     int use_graphs = 1;
     int pusher = 0;               // PIC_PUSHER_*
     int gather = 0;               // PIC_GATHER_*
+    // artificial neutralising ions fading over [ion_t0, ion_t0 + ion_T]: their J_z is ion_G / ion_T
+    float *ion_G = nullptr;
+    double ion_t0 = 0, ion_T = 0;
     cudaGraphExec_t graph = nullptr;
     int64_t graph_steps = 0;      // steps one replay advances
     int64_t graph_kernels = 0;    // kernels one replay runs
@@ -320,6 +323,9 @@ cudaError_t launch_fdtd_b(pic_ctx *c, float dtt);
 cudaError_t launch_fdtd_e(pic_ctx *c);
 cudaError_t launch_shift_fields(pic_ctx *c);
 cudaError_t launch_field_energy(pic_ctx *c, double *out_host, int run);
+cudaError_t launch_ion_prefix(pic_ctx *c, const float *rho, float *G);
+cudaError_t launch_ion_current(pic_ctx *c, float f);
+cudaError_t launch_ion_shift(pic_ctx *c);
 // k_sort.cu
 cudaError_t launch_sort(pic_ctx *c, int si);
 cudaError_t exclusive_scan(pic_ctx *c, int *data, int64_t n);

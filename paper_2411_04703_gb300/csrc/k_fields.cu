@@ -128,6 +128,44 @@ __global__ void __launch_bounds__(256) k_fdtd_e(float *__restrict__ E, const flo
     E[2 * N + ix] = e2 + dt * (dBy_dx - dBx_dy - j2);
 }
 
+// Artificial neutralising ions: the z prefix G(i, j, k) = -dz sum_{k' <= k} rho'(i, j, k') of the
+// compensated species' density (relative to the column mean on a periodic z), FP64 along each
+// column.  The ions' current while they fade over T is J_z = G / T (div J = -d rho_ion / dt).
+__global__ void k_ion_prefix(const float *rho, float *G, int nx, int ny, int nz, double dz, int zper)
+{
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= nx * ny) return;
+    const long long plane = (long long)nx * ny;
+    double mean = 0.0;
+    if (zper) {
+        for (int k = 0; k < nz; k++) mean += rho[k * plane + col];
+        mean /= (double)nz;
+    }
+    double acc = 0.0;
+    for (int k = 0; k < nz; k++) {
+        acc += (double)rho[k * plane + col] - mean;
+        G[k * plane + col] = (float)(-dz * acc);
+    }
+}
+
+__global__ void k_ion_current(float *Jz, const float *G, long long n, float f)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        Jz[i] += f * G[i];
+}
+
+// Moving window with artificial ions: the prefix of the shifted density is the old prefix one
+// plane up minus the dropped plane's part; no ions enter at the front.
+__global__ void k_ion_shift(float *G, int nx, int ny, int nz)
+{
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= nx * ny) return;
+    const long long plane = (long long)nx * ny;
+    const float g0 = G[col];
+    for (int k = 0; k + 1 < nz; k++) G[k * plane + col] = G[(k + 1) * plane + col] - g0;
+    if (nz > 1) G[(long long)(nz - 1) * plane + col] = G[(long long)(nz - 2) * plane + col];
+}
+
 // Moving window: every array moves down one z plane, the front plane becomes zero.  One
 // thread owns one (i, j) column of one array, so the in-place shift has no race.
 __global__ void k_shift_fields(float *const *arrays, int n_arrays, int nx, int ny, int nz)
@@ -175,6 +213,30 @@ cudaError_t launch_fdtd_e(pic_ctx *c)
     dim3 blk(32, 8, 1), grd((c->n[0] + 31) / 32, (c->n[1] + 7) / 8, c->n[2]);
     const PmlDev pml = pml_dev(c);
     k_fdtd_e<<<grd, blk, 0, c->stream>>>(c->E, c->B, c->J, pml.psiE, grid_dev(c), pml);
+    c->kernels++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ion_prefix(pic_ctx *c, const float *rho, float *G)
+{
+    const int cols = c->n[0] * c->n[1];
+    k_ion_prefix<<<(cols + 255) / 256, 256, 0, c->stream>>>(rho, G, c->n[0], c->n[1], c->n[2], c->d[2],
+                                                           c->bc[2][0] == PIC_BC_PERIODIC);
+    c->kernels++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ion_current(pic_ctx *c, float f)
+{
+    k_ion_current<<<c->num_sms * 4, 256, 0, c->stream>>>(c->J + 2 * c->ncell, c->ion_G, c->ncell, f);
+    c->kernels++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ion_shift(pic_ctx *c)
+{
+    const int cols = c->n[0] * c->n[1];
+    k_ion_shift<<<(cols + 255) / 256, 256, 0, c->stream>>>(c->ion_G, c->n[0], c->n[1], c->n[2]);
     c->kernels++;
     return cudaGetLastError();
 }

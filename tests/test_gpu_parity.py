@@ -348,3 +348,43 @@ def test_resolution_factor_matches_oracle():
         assert r == pytest.approx(ro, rel=1e-8)
         assert ok == (ro < lam)
         sim.close()
+
+
+@pytest.mark.parametrize("case", ["vacuum_tsc", "long_undulator_tsc_pml_ramp"])
+def test_artificial_ion_ramp_tracks_oracle(case):
+    # the beam compensated by artificial ions at load (fields zero), faded over 3.5 steps; each
+    # side computes the ions' density and current itself: one step within 1e-5, five within 1e-4
+    w = CASES[case]()
+    sim, ids = api.from_workload(w)
+    o, oid = parity.oracle_from_gpu(w, sim, ids)
+    T = 3.5 * w.dt
+    sim.set_ion_ramp(ids["beam"], T)
+    o.set_ion_ramp(oid["beam"], T)
+    for n, tol in ((1, TOL_STEP), (4, 1e-4)):
+        sim.step(n)
+        sim.sync()
+        o.step(n)
+        f = parity.compare_fields(sim, o)
+        assert max(f.values()) < tol, (n, f)
+    r = parity.compare_species(w, sim, ids["beam"], o, oid["beam"])
+    assert r["u_rel_err"] < 1e-4, r
+
+
+def test_artificial_ion_ramp_keeps_gauss_law_on_gpu():
+    w = W.mini_vacuum(order=2)
+    w.beam.weight *= 1e6   # strong self-fields
+    sim, ids = api.from_workload(w)
+    d = w.d
+    rho0 = sim.get_field(api.PIC_RHO).astype(np.float64)
+    mean = rho0.mean(axis=0, keepdims=True)      # periodic z: the column mean stays as background
+    T = 6.5 * w.dt
+    sim.set_ion_ramp(ids["beam"], T)
+    for n in range(10):
+        ex, ey, ez = (sim.get_field(c).astype(np.float64) for c in range(3))
+        rho = sim.get_field(api.PIC_RHO).astype(np.float64)
+        div = ((ex - np.roll(ex, 1, 2)) / d[0] + (ey - np.roll(ey, 1, 1)) / d[1] + (ez - np.roll(ez, 1, 0)) / d[2])
+        f = min(1.0, n * w.dt / T)
+        G = div - rho - (-(rho0 - mean) * (1.0 - f) - mean)
+        assert np.max(np.abs(G)) < 1e-4 * np.max(np.abs(rho0)), n
+        sim.step(1)
+    assert np.max(np.abs(sim.get_field(api.PIC_EZ))) > 0

@@ -1048,3 +1048,56 @@ def test_energy_conserving_gather_of_a_curl_is_the_curl_of_the_gathered_potentia
             dA[:, dd] = (s.gather_at(X + e)[:3] - s.gather_at(X - e)[:3]) / (2 * h * d[dd])
         curl = np.array([dA[2, 1] - dA[1, 2], dA[0, 2] - dA[2, 0], dA[1, 0] - dA[0, 1]])
         np.testing.assert_allclose(g[3:], curl, rtol=0, atol=1e-6 * (1 + np.max(np.abs(curl))))
+
+
+# ------------------------------------------------------------------ artificial-ion ramp
+
+@pytest.mark.parametrize("zbc", [PERIODIC, OPEN])
+def test_artificial_ion_ramp_keeps_gauss_law_node_by_node(zbc):
+    # Fields start at zero with the beam compensated by static artificial ions; the ions fade
+    # linearly over T (the paper's T_ion) through their current.  Gauss's law holds at every node
+    # at every step: div E = rho_beam(t) + rho_ion(t), rho_ion = -rho_0 (1 - f) - mean (f the
+    # faded fraction; on a periodic z the column mean of rho_0 stays as a background).
+    grid = (8, 6, 16)
+    d = (0.6, 0.5, 0.8)
+    dt = 0.5 / math.sqrt(sum(1 / v ** 2 for v in d))
+    bc = ((PERIODIC, PERIODIC), (PERIODIC, PERIODIC), (zbc, zbc))
+    for order in (1, 2):
+        s = oracle.Sim(grid, d, dt, 3.0, bc=bc, order=order)
+        sid = s.add_species(-1.0, 1.0)
+        rng = np.random.default_rng(90 + order)
+        n = 400
+        X = np.stack([rng.uniform(0, grid[0], n), rng.uniform(0, grid[1], n), rng.uniform(5.5, 9.5, n)], 1)
+        U = np.stack([rng.normal(0, 0.3, n), rng.normal(0, 0.3, n), rng.normal(0.5, 0.1, n)], 1)
+        s.set_state(sid, X, U, np.full(n, 0.05), np.arange(n))
+        rho0 = s.rho()
+        mean = rho0.mean(axis=0, keepdims=True) if zbc == PERIODIC else 0.0 * rho0
+        T = 4.5 * dt
+        s.set_ion_ramp(sid, T)
+        scale = np.max(np.abs(rho0))
+        interior = (slice(2, grid[2] - 2),) if zbc == OPEN else (slice(None),)
+        for n_step in range(8):
+            f = min(1.0, n_step * dt / T)
+            G = s.divE() - s.rho() - (-(rho0 - mean) * (1.0 - f) - mean)
+            assert np.max(np.abs(G[interior])) < 1e-11 * scale, (order, n_step)
+            s.step(1)
+        assert np.max(np.abs(s.field(EZ))) > 1e-3 * scale     # the fields built up
+
+
+def test_artificial_ion_current_is_the_z_prefix_of_the_faded_charge():
+    # one step entirely inside the ramp: J_z(k + 1/2) = -(dz / T) sum_{k' <= k} rho_0 exactly, on
+    # top of the particles' own current (a frozen species carries none)
+    grid, d, dt = (6, 5, 12), (0.6, 0.5, 0.8), 0.2
+    bc = ((PERIODIC, PERIODIC), (PERIODIC, PERIODIC), (OPEN, OPEN))
+    s = oracle.Sim(grid, d, dt, 3.0, bc=bc, order=2)
+    sid = s.add_species(-1.0, 1.0, frozen=True)
+    rng = np.random.default_rng(95)
+    X = np.stack([rng.uniform(0, 6, 50), rng.uniform(0, 5, 50), rng.uniform(4, 8, 50)], 1)
+    s.set_state(sid, X, np.zeros((50, 3)), np.full(50, 0.1), np.arange(50))
+    rho0 = s.rho()
+    T = 7 * dt
+    s.set_ion_ramp(sid, T)
+    s.step(1)
+    expect = -(d[2] / T) * np.cumsum(rho0, axis=0)
+    # frozen particles still drift with their (zero) momentum: no current of their own
+    np.testing.assert_allclose(s.field(JZ), expect, rtol=0, atol=1e-13 * np.max(np.abs(expect)))
