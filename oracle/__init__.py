@@ -96,6 +96,10 @@ def lib():
                 "osim_set_threads": (i, [vp, i]),
                 "osim_set_gather": (None, [vp, i]),
                 "osim_set_ion_ramp": (None, [vp, i, d]),
+                "osim_snapshot_begin": (None, [vp, i, d]),
+                "osim_snapshot_get": (l, [vp, pd, P(C.c_ubyte)]),
+                "osim_snapshot_n": (l, [vp]),
+                "osim_snapshot_moments": (None, [vp, d, pd]),
                 "oracle_field_transform": (None, [pd, pd, d, pd, pd]),
                 "oracle_lab_to_boosted": (None, [d, pd, pd, pd, pd]),
                 "oracle_boosted_to_lab": (None, [d, pd, d, pd, pd, pd, pd]),
@@ -304,6 +308,24 @@ class Sim:
         """Threads of the particle loop (timing only; 1, the default, is the serial reference
         loop).  Returns the number used (1 without OpenMP)."""
         return self.L.osim_set_threads(self.h, int(n))
+
+    def snapshot_begin(self, sid, t_lab):
+        """Arm a lab-frame snapshot of species sid at lab time t_lab (time-skew reconstruction)."""
+        self.L.osim_snapshot_begin(self.h, int(sid), float(t_lab))
+
+    def snapshot(self):
+        """(records [n_ids, 7]: lab x, y, z, u_x, u_y, u_z, w; state [n_ids]: 0 pending, 1 recorded,
+        2 missed) by particle id."""
+        n = self.L.osim_snapshot_n(self.h)
+        rec = np.zeros((max(n, 1), 7))
+        st = np.zeros(max(n, 1), np.uint8)
+        self.L.osim_snapshot_get(self.h, _pd(rec), st.ctypes.data_as(C.POINTER(C.c_ubyte)))
+        return rec[:n], st[:n]
+
+    def snapshot_moments(self, k=0.0):
+        out = np.zeros(len(MOMENT_NAMES))
+        self.L.osim_snapshot_moments(self.h, float(k), _pd(out))
+        return dict(zip(MOMENT_NAMES, out.tolist()))
 
     def set_ion_ramp(self, sid, T):
         """Artificial ions compensating species sid now, faded linearly over T (T <= 0: none)."""

@@ -78,6 +78,12 @@ typedef struct {
     /* artificial neutralising ions fading over [ion_t0, ion_t0 + ion_T]: their current density
      * is ion_G / ion_T (z component, at the E_z points) while they fade */
     double *ion_G, ion_t0, ion_T;
+    /* lab-frame snapshot of species snap_sp at lab time snap_T, by particle id: lab x, y, z,
+     * u_x, u_y, u_z and weight, and a state (0 pending, 1 recorded, 2 missed) */
+    int snap_sp;
+    long snap_n;
+    double snap_T, *snap;
+    unsigned char *snap_state;
     int threads;  /* > 1: the particle loop runs on that many OpenMP threads (timing only) */
 } osim;
 
@@ -197,6 +203,8 @@ void osim_destroy(void *h)
     }
     free(s->zprof); free(s->nprof_v);
     free(s->ion_G);
+    free(s->snap);
+    free(s->snap_state);
     free(s);
 }
 
@@ -339,6 +347,42 @@ void osim_set_external(void *h, int type, double K, double lambda_u, double phas
 
 void osim_set_pusher(void *h, int pusher) { ((osim *)h)->pusher = pusher; }
 void osim_set_gather(void *h, int gather) { ((osim *)h)->gather = gather; }
+
+/* Arm a lab-frame snapshot of species spi at lab time T (o_snap_record).  A particle whose
+ * current lab time is already at or past T cannot be reconstructed: it is marked missed (2). */
+void osim_snapshot_begin(void *h, int spi, double T)
+{
+    osim *s = (osim *)h;
+    osp *p = &s->sp[spi];
+    free(s->snap);
+    free(s->snap_state);
+    s->snap_sp = spi;
+    s->snap_T = T;
+    s->snap_n = p->next_id;
+    s->snap = (double *)calloc(7 * (s->snap_n > 0 ? s->snap_n : 1), sizeof(double));
+    s->snap_state = (unsigned char *)calloc(s->snap_n > 0 ? s->snap_n : 1, 1);
+    double tp = (double)s->step * s->dt;
+    for (long i = 0; i < p->n; i++) {
+        if (!p->alive[i] || p->id[i] >= s->snap_n) continue;
+        double tl = s->gR * (tp + s->bR * (p->X[3 * i + 2] + (double)s->shifts) * s->d[2]);
+        if (tl >= T) s->snap_state[p->id[i]] = 2;
+    }
+}
+
+/* The snapshot's records (by id, [n][7] as recorded) and states; returns the number recorded. */
+long osim_snapshot_get(void *h, double *rec, unsigned char *state)
+{
+    osim *s = (osim *)h;
+    long m = 0;
+    for (long i = 0; i < s->snap_n; i++) {
+        if (rec) memcpy(rec + 7 * i, s->snap + 7 * i, 7 * sizeof(double));
+        if (state) state[i] = s->snap_state[i];
+        if (s->snap_state[i] == 1) m++;
+    }
+    return m;
+}
+
+long osim_snapshot_n(void *h) { return ((osim *)h)->snap_n; }
 
 void osim_external_at(void *h, double y, double zp, double tp, double *E, double *B)
 {
@@ -759,6 +803,37 @@ static void o_esirkepov(const osim *s, double *const J[3], long *dropped, double
         }
 }
 
+/* Lab-frame reconstruction at one lab time (Sec. "Understanding the RRF", Eq. DT): the particles
+ * of one RRF instant sit at different lab times, so a lab snapshot at lab time T is assembled
+ * particle by particle across the RRF steps.  During a step a particle moves on a straight RRF
+ * segment from (x'_n, t'_n) to (x'_{n+1}, t'_n + dt) with momentum u^{n+1/2}; its lab time
+ * t = gamma_R (t' + beta_R z') grows monotonically along it.  When [t_a, t_b) of the step contains
+ * T, the event on the segment at lab time T is transformed to the lab (inverse Eq. Lor1-Lor2:
+ * x, y unchanged, z = gamma_R (z' + beta_R t')) with the lab momentum of u^{n+1/2}
+ * (u_z = gamma_R (u'_z + beta_R gamma')) and recorded under the particle's id.  z' counts the
+ * window shifts; a periodic z is taken in the box's own image. */
+static void o_snap_record(const osim *s, const osp *p, long i, const double X0[3], const double X1[3])
+{
+    long id = p->id[i];
+    if (id < 0 || id >= s->snap_n || s->snap_state[id] != 0) return;
+    double t0 = (double)s->step * s->dt;
+    double z0 = (X0[2] + (double)s->shifts) * s->d[2], z1 = (X1[2] + (double)s->shifts) * s->d[2];
+    double ta = s->gR * (t0 + s->bR * z0), tb = s->gR * (t0 + s->dt + s->bR * z1);
+    if (!(ta < s->snap_T && s->snap_T <= tb)) return;
+    double a = (s->snap_T - ta) / (tb - ta);
+    double xp[3] = {(X0[0] + a * (X1[0] - X0[0])) * s->d[0], (X0[1] + a * (X1[1] - X0[1])) * s->d[1],
+                    z0 + a * (z1 - z0)};
+    double tp = t0 + a * s->dt;
+    const double *U = &p->U[3 * i];
+    double xl[3], ul[3], tl;
+    oracle_boosted_to_lab(s->gR, xp, tp, U, xl, &tl, ul);
+    double *r = &s->snap[7 * id];
+    r[0] = xl[0]; r[1] = xl[1]; r[2] = xl[2];
+    r[3] = ul[0]; r[4] = ul[1]; r[5] = ul[2];
+    r[6] = p->W[i];
+    s->snap_state[id] = 1;
+}
+
 /* Gather + push + move + deposit of particle i of species p (one leap-frog step); the current
  * goes to J[3], deposits outside a non-periodic grid are counted in *dropped. */
 static void o_push_one(const osim *s, osp *p, long i, double *const J[3], long *dropped)
@@ -784,6 +859,7 @@ static void o_push_one(const osim *s, osp *p, long i, double *const J[3], long *
     o_wrap_pos(s, Xw);
     if (!o_inside(s, Xw)) { p->alive[i] = 0; return; }
     o_esirkepov(s, J, dropped, p->q * p->W[i], X, X1);
+    if (s->snap && p == &s->sp[s->snap_sp]) o_snap_record(s, p, i, X, X1);
     memcpy(X, Xw, sizeof Xw);
 }
 
@@ -1139,6 +1215,46 @@ enum {
     OM_EFIELD, OM_N
 };
 
+/* Weighted statistics of m particles (weights w summing to sw > 0): means, rms sizes, mean
+ * momenta and gamma, relative energy spread, normalised emittances sqrt(<dx^2><du^2> -
+ * <dx du>^2) from central weighted moments, kinetic energy sum w mass (gamma - 1) and bunching
+ * |sum w exp(-i k z)| / sum w. */
+static void o_beam_stats(long m, const double *w, double sw, const double *x, const double *y, const double *z,
+                         const double *ux, const double *uy, const double *uz, const double *g, double mass,
+                         double k, double *out)
+{
+    double mean[7] = {0};
+    const double *cols[7] = {x, y, z, ux, uy, uz, g};
+    for (int q = 0; q < 7; q++) {
+        for (long i = 0; i < m; i++) mean[q] += w[i] * cols[q][i];
+        mean[q] /= sw;
+    }
+    double vx = 0, vy = 0, vz = 0, vux = 0, vuy = 0, cxu = 0, cyu = 0, vg = 0, ek = 0;
+    double cr = 0, ci = 0;
+    for (long i = 0; i < m; i++) {
+        double dxx = x[i] - mean[0], dyy = y[i] - mean[1], dzz = z[i] - mean[2];
+        double dux = ux[i] - mean[3], duy = uy[i] - mean[4], dg = g[i] - mean[6];
+        vx += w[i] * dxx * dxx; vy += w[i] * dyy * dyy; vz += w[i] * dzz * dzz;
+        vux += w[i] * dux * dux; vuy += w[i] * duy * duy;
+        cxu += w[i] * dxx * dux; cyu += w[i] * dyy * duy;
+        vg += w[i] * dg * dg;
+        ek += w[i] * mass * (g[i] - 1.0);
+        cr += w[i] * cos(k * z[i]);
+        ci += -w[i] * sin(k * z[i]);
+    }
+    vx /= sw; vy /= sw; vz /= sw; vux /= sw; vuy /= sw; cxu /= sw; cyu /= sw; vg /= sw;
+    out[OM_MX] = mean[0]; out[OM_MY] = mean[1]; out[OM_MZ] = mean[2];
+    out[OM_SX] = sqrt(vx); out[OM_SY] = sqrt(vy); out[OM_SZ] = sqrt(vz);
+    out[OM_MUX] = mean[3]; out[OM_MUY] = mean[4]; out[OM_MUZ] = mean[5];
+    out[OM_MG] = mean[6];
+    out[OM_SG_REL] = sqrt(vg) / mean[6];
+    double ex = vx * vux - cxu * cxu, ey = vy * vuy - cyu * cyu;
+    out[OM_EMX] = sqrt(ex > 0 ? ex : 0);
+    out[OM_EMY] = sqrt(ey > 0 ? ey : 0);
+    out[OM_BUNCH] = sqrt(cr * cr + ci * ci) / sw;
+    out[OM_EKIN] = ek;
+}
+
 /* Weighted beam moments of species spi.  frame 0: RRF at t' = step dt (positions in
  * normalised RRF length, z' absolute).  frame 1: lab — each particle's event (z', t') and
  * momentum are transformed back (inverse Eq. Lor1-Lor2) and drifted ballistically to the
@@ -1192,36 +1308,7 @@ void osim_moments(void *h, int spi, int frame, double k, double *out)
                 z[i] += dtl * uz[i] / g[i];
             }
         }
-        double mean[7] = {0};
-        double *cols[7] = {x, y, z, ux, uy, uz, g};
-        for (int q = 0; q < 7; q++) {
-            for (long i = 0; i < m; i++) mean[q] += w[i] * cols[q][i];
-            mean[q] /= sw;
-        }
-        double vx = 0, vy = 0, vz = 0, vux = 0, vuy = 0, cxu = 0, cyu = 0, vg = 0, ek = 0;
-        double cr = 0, ci = 0;
-        for (long i = 0; i < m; i++) {
-            double dxx = x[i] - mean[0], dyy = y[i] - mean[1], dzz = z[i] - mean[2];
-            double dux = ux[i] - mean[3], duy = uy[i] - mean[4], dg = g[i] - mean[6];
-            vx += w[i] * dxx * dxx; vy += w[i] * dyy * dyy; vz += w[i] * dzz * dzz;
-            vux += w[i] * dux * dux; vuy += w[i] * duy * duy;
-            cxu += w[i] * dxx * dux; cyu += w[i] * dyy * duy;
-            vg += w[i] * dg * dg;
-            ek += w[i] * p->m * (g[i] - 1.0);
-            cr += w[i] * cos(k * z[i]);
-            ci += -w[i] * sin(k * z[i]);
-        }
-        vx /= sw; vy /= sw; vz /= sw; vux /= sw; vuy /= sw; cxu /= sw; cyu /= sw; vg /= sw;
-        out[OM_MX] = mean[0]; out[OM_MY] = mean[1]; out[OM_MZ] = mean[2];
-        out[OM_SX] = sqrt(vx); out[OM_SY] = sqrt(vy); out[OM_SZ] = sqrt(vz);
-        out[OM_MUX] = mean[3]; out[OM_MUY] = mean[4]; out[OM_MUZ] = mean[5];
-        out[OM_MG] = mean[6];
-        out[OM_SG_REL] = sqrt(vg) / mean[6];
-        double ex = vx * vux - cxu * cxu, ey = vy * vuy - cyu * cyu;
-        out[OM_EMX] = sqrt(ex > 0 ? ex : 0);
-        out[OM_EMY] = sqrt(ey > 0 ? ey : 0);
-        out[OM_BUNCH] = sqrt(cr * cr + ci * ci) / sw;
-        out[OM_EKIN] = ek;
+        o_beam_stats(m, w, sw, x, y, z, ux, uy, uz, g, p->m, k, out);
         out[OM_MT] = mt;
     }
     double fe = 0.0;
@@ -1230,6 +1317,35 @@ void osim_moments(void *h, int spi, int frame, double k, double *out)
     out[OM_EFIELD] = 0.5 * fe * s->d[0] * s->d[1] * s->d[2];
     free(w);
     free(x);
+}
+
+/* Moments of the recorded lab snapshot (statistics of o_beam_stats; lab wavenumber k; mean_t is
+ * the snapshot's lab time, field_energy 0). */
+void osim_snapshot_moments(void *h, double k, double *out)
+{
+    osim *s = (osim *)h;
+    memset(out, 0, OM_N * sizeof(double));
+    long m = 0;
+    for (long i = 0; i < s->snap_n; i++) m += s->snap_state[i] == 1;
+    double *buf = (double *)malloc((m > 0 ? m : 1) * 8 * sizeof(double));
+    double *x = buf, *y = x + m, *z = y + m, *ux = z + m, *uy = ux + m, *uz = uy + m, *g = uz + m, *w = g + m;
+    long c = 0;
+    double sw = 0.0;
+    for (long i = 0; i < s->snap_n; i++) {
+        if (s->snap_state[i] != 1) continue;
+        const double *r = &s->snap[7 * i];
+        x[c] = r[0]; y[c] = r[1]; z[c] = r[2]; ux[c] = r[3]; uy[c] = r[4]; uz[c] = r[5]; w[c] = r[6];
+        g[c] = sqrt(1.0 + r[3] * r[3] + r[4] * r[4] + r[5] * r[5]);
+        sw += w[c];
+        c++;
+    }
+    const osp *p = &s->sp[s->snap_sp];
+    out[OM_COUNT] = (double)m;
+    out[OM_SUMW] = sw;
+    out[OM_CHARGE] = p->q * sw;
+    if (m > 0 && sw > 0.0) o_beam_stats(m, w, sw, x, y, z, ux, uy, uz, g, p->m, k, out);
+    out[OM_MT] = s->snap_T;
+    free(buf);
 }
 
 /* ------------------------------------------------------------------ resonance */

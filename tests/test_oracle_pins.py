@@ -1101,3 +1101,97 @@ def test_artificial_ion_current_is_the_z_prefix_of_the_faded_charge():
     expect = -(d[2] / T) * np.cumsum(rho0, axis=0)
     # frozen particles still drift with their (zero) momentum: no current of their own
     np.testing.assert_allclose(s.field(JZ), expect, rtol=0, atol=1e-13 * np.max(np.abs(expect)))
+
+
+# ------------------------------------------------------------------ time-skew reconstruction
+
+def test_lab_snapshot_of_a_ballistic_beam_is_the_lab_straight_line():
+    # Particles recorded at one lab time T across the RRF steps: for a charge-free beam every
+    # particle is on its lab straight line, x(T) = x_i + (u_i / gamma_i) T (plus the grid origin:
+    # o_x dx transversely, gamma_R o_z dz longitudinally), to rounding
+    rng = np.random.default_rng(101)
+    n = 500
+    X = np.stack([rng.normal(0, 0.3, n), rng.normal(0, 0.3, n), rng.uniform(-2, 2, n)])
+    ux = rng.normal(0, 0.05, n)
+    g = GB_LAB * (1 + 1e-3 * rng.standard_normal(n))
+    U = np.stack([ux, np.zeros(n), np.sqrt(g * g - 1 - ux * ux)])
+    s = oracle.Sim((64, 8, 512), (1.0, 1.0, 1.0), 0.5, GR_LAB, order=1)
+    sid = s.add_species(0.0, 1.0)
+    org = (32.0, 4.0, 256.0)
+    assert s.load(sid, X, U, w=np.full(n, 2.0), frame=LAB, origin=org) == n
+    bR = s.beta_R
+    Xg, _, _, _ = s.particles(sid)
+    t_now = GR_LAB * bR * Xg[:, 2]                 # lab times of the loaded events (t' = 0)
+    T = float(np.max(t_now)) + 3.0
+    s.snapshot_begin(sid, T)
+    for _ in range(200):
+        s.step(1)
+        if np.all(s.snapshot()[1] == 1):
+            break
+    rec, st = s.snapshot()
+    assert np.all(st == 1)
+    gl = np.sqrt(1 + np.sum(U * U, axis=0))
+    # the grid's longitudinal origin shifts the lab clock too: absolute lab time = lab time of
+    # the loaded events (t = 0) + gamma_R beta_R o_z dz
+    tau = GR_LAB * bR * org[2] * 1.0
+    np.testing.assert_allclose(rec[:, 0], org[0] + X[0] + U[0] / gl * (T - tau), rtol=0, atol=1e-9)
+    np.testing.assert_allclose(rec[:, 2], GR_LAB * org[2] + X[2] + U[2] / gl * (T - tau), rtol=0, atol=1e-8)
+    np.testing.assert_allclose(rec[:, 3:6], U.T, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(rec[:, 6], 2.0)
+    # its moments equal the drift-to-a-common-lab-time moments taken at that time
+    m_snap = s.snapshot_moments(k=2.1)
+    assert m_snap["mean_t"] == T and m_snap["count"] == n
+    zs = rec[:, 2]
+    assert m_snap["rms_z"] == pytest.approx(np.std(zs), rel=1e-9)
+    assert m_snap["bunching"] == pytest.approx(abs(np.mean(np.exp(-1j * 2.1 * zs))), rel=1e-9)
+
+
+def test_lab_snapshot_of_an_rrf_run_reproduces_a_lab_frame_run_in_the_undulator():
+    # The paper's premise checked at one lab time: test electrons (no self-field) entering a planar
+    # undulator through its ramp, simulated (a) in the lab (gamma_R = 1) up to lab time T and
+    # (b) in the RRF with the time-skew reconstruction at T, agree to the discretisation error of
+    # the two leap-frogs.  The electrons start at different lab z next to the common origin of the
+    # two frames' clocks; their t' = 0 events sit at lab times up to ~2 gamma_R^2 dz apart (Eq. DT),
+    # all before the undulator entrance, where the loader's ballistic drift to t' = 0 is exact.
+    K, gB = 1.0, 10.0
+    lam = 2 * math.pi                       # lab units with k_u = 1
+    rng = np.random.default_rng(102)
+    n = 8
+    X = np.stack([rng.normal(0, 0.01, n), np.zeros(n), rng.uniform(0.0, 0.2, n)])
+    ux = rng.normal(0, 0.01, n)
+    U = np.stack([ux, np.zeros(n), np.sqrt(gB * gB - 1 - ux * ux)])
+    z0, ramp = 6.0, lam
+    T = z0 + 2.0 * lam                      # through the ramp and one more period
+    org = (4.0, 2.0, 0.0)
+    # (a) lab frame
+    dz, dt = 0.05, 0.004
+    lab = oracle.Sim((8, 4, 400), (1.0, 1.0, dz), dt, 1.0, order=1)
+    a = lab.add_species(-1.0, 1.0)
+    lab.set_external(K=K, lambda_u=lam, z_start=z0, ramp=ramp)
+    lab.load(a, X, U, w=np.zeros(n), frame=LAB, origin=org)
+    lab.step(int(round(T / dt)))
+    XL, UL, _, idl = lab.particles(a)
+    # (b) boosted frame gamma_R = 3, lambda'_u = lam / gamma_R resolved by 64 cells
+    gR = 3.0
+    dzp = lam / gR / 64
+    rrf = oracle.Sim((8, 4, 400), (1.0, 1.0, dzp), 0.2 * dzp, gR, order=1)
+    b = rrf.add_species(-1.0, 1.0)
+    rrf.set_external(K=K, lambda_u=lam, z_start=z0, ramp=ramp)
+    rrf.load(b, X, U, w=np.zeros(n), frame=LAB, origin=org)
+    rrf.snapshot_begin(b, T)
+    for _ in range(5000):
+        rrf.step(1)
+        if np.all(rrf.snapshot()[1] == 1):
+            break
+    rec, st = rrf.snapshot()
+    assert np.all(st == 1)
+    o = np.argsort(idl)
+    xl, zl = XL[o, 0] - org[0], XL[o, 2] * dz
+    xr, zr = rec[:, 0] - org[0], rec[:, 2]
+    amp = K / gB                           # lab orbit amplitude K / (gamma k_u)
+    assert np.max(np.abs(xl)) > 0.3 * amp  # inside the undulator at T
+    np.testing.assert_allclose(xr, xl, rtol=0, atol=2e-2 * amp)
+    np.testing.assert_allclose(zr, zl, rtol=0, atol=2e-3)
+    np.testing.assert_allclose(rec[:, 3], UL[o, 0], rtol=0, atol=2e-2 * K)
+    # u_z oscillates at 2 k_u with amplitude ~K^2 / (4 gamma) about its mean
+    np.testing.assert_allclose(rec[:, 5], UL[o, 2], rtol=0, atol=2e-2 * K * K / gB)
