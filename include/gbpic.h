@@ -265,6 +265,7 @@ int pic_set_gather(pic_ctx *ctx, int gather);
  * PIC_ERR_STATE while adjoint checkpoints are recorded. */
 int pic_set_ion_ramp(pic_ctx *ctx, int species_id, double T_ion);
 
+
 /* Replay of captured step sequences in pic_step (on = 1, the default) or one launch per kernel
  * (on = 0).  The capture is redone when species, the external field or the tuning change; if
  * capturing fails the context falls back to launching. */
@@ -338,6 +339,29 @@ typedef struct {
     double bunching, kinetic_energy, mean_t, field_energy;
 } pic_moments;
 int pic_get_moments(pic_ctx *ctx, int species_id, int frame, double k_bunch, pic_moments *out);
+
+/* Lab-frame reconstruction at one lab time (Sec. "Understanding the RRF", Eq. delta2electrons,
+ * Eq. DT): the particles of one RRF instant sit at lab times spread by gamma_R beta_R dz', so a
+ * lab snapshot at lab time t_lab is assembled particle by particle while the RRF steps pass
+ * through it.  In every step a particle moves on a straight RRF segment from x^n to x^{n+1} with
+ * momentum u^{n+1/2}; when the segment's lab times gamma_R (t' + beta_R z') span t_lab, its event
+ * at t_lab is transformed to the lab (inverse Eq. Lor1-Lor2; x, y unchanged) with the lab
+ * momentum of u^{n+1/2} and recorded in FP64 under the particle's id.  Lab coordinates are those
+ * of the grid's absolute RRF coordinates (x' = cell + offset in units of d, z' counting window
+ * shifts): the lab origin and clock coincide with the RRF's at the grid's origin node.
+ * pic_lab_snapshot arms a snapshot of particle species species_id (ids 0 .. next id - 1; a
+ * particle already at or past t_lab is marked missed); t_lab = NaN disarms and frees it.  While
+ * armed, every step runs one more kernel over the species, and replay of captured steps is off.
+ * pic_lab_snapshot_read copies the records (rec: host or device double[n][7] = lab x, y, z, u_x,
+ * u_y, u_z, w) and states (host uint8[n]: 0 pending, 1 recorded, 2 missed) for n >= *n_ids ids;
+ * rec and state may be NULL; *n_ids and *recorded (may be NULL) receive the number of ids and of
+ * recorded particles.  pic_lab_snapshot_moments gives the moments of the recorded particles with
+ * the definitions of pic_get_moments (bunching at the lab wavenumber k_bunch; mean_t = t_lab;
+ * field_energy 0).  Synchronous.  A periodic z is taken in the box's own image.  PIC_ERR_ARG for a
+ * lattice species, an unknown species or an ensemble; PIC_ERR_STATE when none is armed. */
+int pic_lab_snapshot(pic_ctx *ctx, int species_id, double t_lab);
+int pic_lab_snapshot_read(pic_ctx *ctx, double *rec, uint8_t *state, int64_t n, int64_t *n_ids, int64_t *recorded);
+int pic_lab_snapshot_moments(pic_ctx *ctx, double k_bunch, pic_moments *out);
 
 /* pic_get_moments restricted to the particles and field cells of one run of an ensemble
  * (0 <= run < runs); positions are in the run's own coordinates.  Synchronous. */

@@ -132,6 +132,9 @@ def lib(build_if_missing: bool = True):
             "pic_set_pusher": [vp, i],
             "pic_set_gather": [vp, i],
             "pic_set_ion_ramp": [vp, i, d],
+            "pic_lab_snapshot": [vp, i, d],
+            "pic_lab_snapshot_read": [vp, vp, vp, i64, P(i64), P(i64)],
+            "pic_lab_snapshot_moments": [vp, d, P(pic_moments)],
             "pic_resolution_factor": [vp, d, P(d), P(i)],
             "pic_resonant_wavenumber": [d, d, d, d, i, P(d)],
             "pic_checkpoint": [vp, i],
@@ -360,6 +363,26 @@ class Sim:
         r, ok = C.c_double(), C.c_int()
         self._check(self.L.pic_resolution_factor(self.h, float(lambda_lab), C.byref(r), C.byref(ok)))
         return r.value, bool(ok.value)
+
+    def lab_snapshot(self, species_id, t_lab):
+        """Arm the lab-frame snapshot of a species at lab time t_lab (NaN disarms)."""
+        self._check(self.L.pic_lab_snapshot(self.h, int(species_id), float(t_lab)))
+
+    def lab_snapshot_read(self):
+        """(records [n_ids, 7]: lab x, y, z, u_x, u_y, u_z, w; states [n_ids]: 0 pending,
+        1 recorded, 2 missed) by particle id."""
+        n, m = C.c_int64(), C.c_int64()
+        self._check(self.L.pic_lab_snapshot_read(self.h, None, None, 0, C.byref(n), None))
+        rec = np.zeros((max(n.value, 1), 7))
+        st = np.zeros(max(n.value, 1), np.uint8)
+        self._check(self.L.pic_lab_snapshot_read(self.h, rec.ctypes.data, st.ctypes.data, n.value, C.byref(n),
+                                                 C.byref(m)))
+        return rec[:n.value], st[:n.value]
+
+    def lab_snapshot_moments(self, k_bunch=0.0):
+        m = pic_moments()
+        self._check(self.L.pic_lab_snapshot_moments(self.h, float(k_bunch), C.byref(m)))
+        return dict(zip(MOMENT_NAMES, list(m.v)))
 
     def set_ion_ramp(self, species_id, T_ion):
         """Artificial ions compensating species_id now, faded linearly over T_ion (<= 0: none)."""

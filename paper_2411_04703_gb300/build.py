@@ -16,7 +16,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(OUT_DIR, "libgbpic.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 SOURCES = ["api.cu", "k_push1.cu", "k_push2.cu", "k_fields.cu", "k_sort.cu", "k_init.cu", "k_sort_noalloc.cu", "k_lattice.cu", "k_adjoint.cu",
-           "k_push2_fm.cu", "k_push2_ff.cu", "k_push2_dm.cu", "k_push2_df.cu", "k_push2_fm_ec.cu", "k_push2_dm_ec.cu"]
+           "k_push2_fm.cu", "k_push2_ff.cu", "k_push2_dm.cu", "k_push2_df.cu", "k_push2_fm_ec.cu", "k_push2_dm_ec.cu", "k_snapshot.cu"]
 GENCODE = "arch=compute_103a,code=sm_103a"
 
 

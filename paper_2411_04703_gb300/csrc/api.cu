@@ -920,6 +920,10 @@ int step_once(pic_ctx *c)
         TraceScope ts(c, c->sp[si].frozen ? TR_PUSH_FROZEN : TR_PUSH);
         CK(launch_push(c, si, ext));
     }
+    if (c->snap) {
+        TraceScope ts(c, TR_OTHER);
+        CK(launch_snap_record(c));
+    }
     if (c->ion_G) {
         // the fading artificial ions' current, averaged over the part of the ramp this step covers
         const double t0 = (double)c->step * c->dt, t1 = t0 + c->dt;
@@ -958,7 +962,7 @@ int step_once(pic_ctx *c)
 // changes between periods: no moving window, no plasma injection (periodic z), tracing off.
 bool graph_eligible(const pic_ctx *c)
 {
-    if (!c->use_graphs || c->moving || c->trace_on || c->nsp == 0 || c->ad_on || c->ion_G) return false;
+    if (!c->use_graphs || c->moving || c->trace_on || c->nsp == 0 || c->ad_on || c->ion_G || c->snap) return false;
     if (c->plasma && c->bc[2][0] != PIC_BC_PERIODIC) return false;
     return true;
 }
@@ -1206,6 +1210,62 @@ int pic_set_ion_ramp(pic_ctx *c, int species_id, double T_ion)
     CK(cudaStreamSynchronize(c->stream));
     c->ion_t0 = (double)c->step * c->dt;
     c->ion_T = T_ion;
+    return PIC_OK;
+}
+
+int pic_lab_snapshot(pic_ctx *c, int species_id, double t_lab)
+{
+    int r = check_ctx(c);
+    if (r) return r;
+    drop_graph(c);
+    dfree(c, c->snap);
+    dfree(c, c->snap_state);
+    c->snap = nullptr;
+    c->snap_state = nullptr;
+    c->snap_n = 0;
+    c->snap_sp = -1;
+    if (std::isnan(t_lab)) return PIC_OK;
+    if (species_id < 0 || species_id >= c->nsp || c->sp[species_id].lattice)
+        return fail(c, PIC_ERR_ARG, "no such particle species");
+    if (c->runs != 1) return fail(c, PIC_ERR_ARG, "the lab snapshot is for a single run");
+    const int64_t n = std::max<int64_t>(c->sp[species_id].next_id, 1);
+    if ((r = alloc_zero(c, &c->snap, 7 * (size_t)n)) || (r = alloc_zero(c, &c->snap_state, (size_t)n))) return r;
+    c->snap_sp = species_id;
+    c->snap_n = c->sp[species_id].next_id;
+    c->snap_T = t_lab;
+    CK(launch_snap_arm(c));
+    return PIC_OK;
+}
+
+int pic_lab_snapshot_read(pic_ctx *c, double *rec, uint8_t *state, int64_t n, int64_t *n_ids, int64_t *recorded)
+{
+    int r = check_ctx(c);
+    if (r) return r;
+    if (!c->snap) return fail(c, PIC_ERR_STATE, "no lab snapshot is armed");
+    if (n_ids) *n_ids = c->snap_n;
+    if ((rec || state) && n < c->snap_n) return fail(c, PIC_ERR_ARG, "buffers smaller than the snapshot's ids");
+    std::vector<uint8_t> st((size_t)std::max<int64_t>(c->snap_n, 1));
+    CK(cudaMemcpyAsync(st.data(), c->snap_state, (size_t)c->snap_n, cudaMemcpyDeviceToHost, c->stream));
+    if (rec) CK(cudaMemcpyAsync(rec, c->snap, sizeof(double) * 7 * (size_t)c->snap_n, cudaMemcpyDefault, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (state) std::memcpy(state, st.data(), (size_t)c->snap_n);
+    if (recorded) {
+        int64_t m = 0;
+        for (int64_t i = 0; i < c->snap_n; i++) m += st[(size_t)i] == 1;
+        *recorded = m;
+    }
+    return PIC_OK;
+}
+
+int pic_lab_snapshot_moments(pic_ctx *c, double k_bunch, pic_moments *out)
+{
+    int r = check_ctx(c);
+    if (r) return r;
+    if (!out) return fail(c, PIC_ERR_ARG, "out is NULL");
+    if (!c->snap) return fail(c, PIC_ERR_STATE, "no lab snapshot is armed");
+    double v[20];
+    CK(launch_snap_moments(c, k_bunch, v));
+    std::memcpy(out, v, sizeof(v));
     return PIC_OK;
 }
 

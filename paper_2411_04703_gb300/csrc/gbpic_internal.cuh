@@ -272,6 +272,13 @@ struct pic_ctx {
     // artificial neutralising ions fading over [ion_t0, ion_t0 + ion_T]: their J_z is ion_G / ion_T
     float *ion_G = nullptr;
     double ion_t0 = 0, ion_T = 0;
+    // lab-frame snapshot of species snap_sp at lab time snap_T (time-skew reconstruction): by
+    // particle id, lab x, y, z, u_x, u_y, u_z, w (FP64) and a state (0 pending, 1 recorded, 2 missed)
+    double *snap = nullptr;
+    unsigned char *snap_state = nullptr;
+    int snap_sp = -1;
+    int64_t snap_n = 0;
+    double snap_T = 0;
     cudaGraphExec_t graph = nullptr;
     int64_t graph_steps = 0;      // steps one replay advances
     int64_t graph_kernels = 0;    // kernels one replay runs
@@ -326,6 +333,10 @@ cudaError_t launch_field_energy(pic_ctx *c, double *out_host, int run);
 cudaError_t launch_ion_prefix(pic_ctx *c, const float *rho, float *G);
 cudaError_t launch_ion_current(pic_ctx *c, float f);
 cudaError_t launch_ion_shift(pic_ctx *c);
+// k_snapshot.cu
+cudaError_t launch_snap_arm(pic_ctx *c);
+cudaError_t launch_snap_record(pic_ctx *c);
+cudaError_t launch_snap_moments(pic_ctx *c, double k, double *out);
 // k_sort.cu
 cudaError_t launch_sort(pic_ctx *c, int si);
 cudaError_t exclusive_scan(pic_ctx *c, int *data, int64_t n);

@@ -388,3 +388,48 @@ def test_artificial_ion_ramp_keeps_gauss_law_on_gpu():
         assert np.max(np.abs(G)) < 1e-4 * np.max(np.abs(rho0)), n
         sim.step(1)
     assert np.max(np.abs(sim.get_field(api.PIC_EZ))) > 0
+
+
+def test_lab_snapshot_tracks_oracle():
+    # The time-skew reconstruction at one lab time on the GPU against the oracle's: the long
+    # undulator case (entrance ramp, PML, TSC), both sides loading the same seeded lab beam; the
+    # snapshot time is a little past the latest particle's lab time at load, so every particle
+    # records during the following steps.  Records per particle (FP32 drift over the steps) and
+    # the snapshot's moments (the long-run tolerance) agree.
+    w = W.mini_long_undulator()
+    x, u, wt = W.sample_beam(w)
+    sim, ids = api.from_workload(w, beam_arrays=(x, u, wt))
+    o = oracle.Sim(w.grid, w.d, w.dt, w.gamma_R, bc=w.bc, pml=w.pml, order=w.order)
+    un = w.undulator
+    o.set_external(un.K, un.lambda_u, un.phase, un.z_start, un.ramp, kind=un.kind)
+    sb = o.add_species(-1.0, 1.0, capacity=x.shape[1])
+    o.load(sb, x, u, wt, frame=oracle.LAB, origin=w.beam.origin, match_undulator=un.match)
+    X, _, _, _ = o.particles(sb)
+    bR = o.beta_R
+    t_lab = w.gamma_R * bR * X[:, 2] * w.d[2]
+    T = float(np.max(t_lab)) + 2.0 * w.gamma_R * w.dt
+    sim.lab_snapshot(ids["beam"], T)
+    o.snapshot_begin(sb, T)
+    for _ in range(60):
+        sim.step(5)
+        o.step(5)
+        _, so = o.snapshot()
+        if np.all(so != 0):
+            break
+    rg, sg = sim.lab_snapshot_read()
+    ro, so = o.snapshot()
+    assert np.array_equal(sg, so)
+    assert np.sum(so == 1) > 0.9 * x.shape[1]
+    rec = so == 1
+    size = np.std(ro[rec, :3], axis=0)
+    for c in range(3):
+        np.testing.assert_allclose(rg[rec, c] - ro[rec, c], 0.0, atol=1e-4 * size[c])
+    for c in range(3, 6):
+        np.testing.assert_allclose(rg[rec, c], ro[rec, c], rtol=0, atol=1e-4 * np.max(np.abs(ro[rec, c])))
+    k_lab = api.resonant_wavenumber(un.lambda_u, un.K, w.beam.gamma)
+    mg = sim.lab_snapshot_moments(k_lab)
+    mo = o.snapshot_moments(k_lab)
+    assert mg["count"] == mo["count"] and mg["mean_t"] == mo["mean_t"] == T
+    for key in ("bunching", "emit_nx", "emit_ny", "rel_energy_spread", "rms_z", "mean_gamma"):
+        assert mg[key] == pytest.approx(mo[key], rel=1e-3), key
+    sim.lab_snapshot(ids["beam"], float("nan"))
