@@ -167,6 +167,31 @@ def oracle_sample_ensemble(steps, warmup, seed=4):
     return value, t, sample
 
 
+def oracle_sample_long(steps, warmup, seed=3):
+    """FP64 oracle on a bounded sample of the long undulator: a 32 x 32 x 128 sub-box (same cells,
+    undulator and ramp, PML) with the beam scaled to the sub-box's volume."""
+    import oracle
+    from paper_2411_04703_gb300 import workloads as W
+    oracle.build()
+    w = W.long_undulator(grid=(32, 32, 128), n_beam=65536, seed=seed)
+    o = oracle.Sim(w.grid, w.d, w.dt, w.gamma_R, bc=w.bc, pml=w.pml, order=w.order)
+    un = w.undulator
+    o.set_external(un.K, un.lambda_u, un.phase, un.z_start, un.ramp, kind=un.kind)
+    sb = o.add_species(-1.0, 1.0)
+    x, u, wt = W.sample_beam(w)
+    o.load(sb, x, u, wt, frame=0, origin=w.beam.origin, match_undulator=un.match)
+    if warmup:
+        o.step(warmup)
+    n0 = o.count(sb)
+    t0 = time.perf_counter()
+    o.step(steps)
+    t = time.perf_counter() - t0
+    value = 0.5 * (n0 + o.count(sb)) * steps / t
+    sample = (f"FP64 oracle, 32x32x128 sub-box of the long undulator ({n0} beam, TSC, PML), {steps} steps, "
+              f"single thread")
+    return value, t, sample
+
+
 def oracle_sample(steps, warmup, seed=2):
     """FP64 oracle on a bounded sample of the workload: a 32 x 32 x 128 sub-box with the same
     cells, plasma density, particles per cell, beam density, boundaries and window."""
@@ -484,6 +509,16 @@ def run_gbpic(args):
         ncell_total = w.ncell
         boundaries = "periodic"
         l2 = "L2-resident (fields 2.4 MB, particles 2 MB): launch-bound, timed as a CUDA graph"
+    elif args.workload == "long_undulator":
+        # the long undulator 256x256x1024: 33.5M beam electrons of lab gamma 2000 at rest on average
+        # in a frame of gamma_R = gamma / sqrt(1 + K^2/2), TSC, PML on every face, entrance ramp;
+        # the FP64 lab-frame bunching is taken every 100 steps inside the timed steps
+        w = W.long_undulator(seed=3 + rank)
+        beam = W.sample_beam(w)
+        sim, ids = api.from_workload(w, device=local, beam_arrays=beam)
+        ncell_total = w.ncell
+        boundaries = "CPML 10 cells on every face, static window"
+        l2 = "inputs larger than L2 (beam state ~2 GB, fields and CPML ~5.6 GB)"
     elif args.workload == "ensemble":
         # batched sweep: 64 runs of 64x64x128 stacked in one context (one launch per kernel)
         import numpy as np
@@ -549,8 +584,22 @@ def run_gbpic(args):
     torch.cuda.synchronize()
     shifts0 = sim.get_time()[1]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    diag = []
     e0.record(stream)
-    sim.step(args.steps)
+    if args.workload == "long_undulator":
+        # the workload's FP64 back-transformed bunching diagnostic every 100 steps, inside the
+        # timed steps (each one a host round trip)
+        un = w.undulator
+        k_lab = api.resonant_wavenumber(un.lambda_u, un.K, w.beam.gamma)
+        done = 0
+        while done < args.steps:
+            nxt = min(args.steps, done + 100 - (done % 100))
+            sim.step(nxt - done)
+            done = nxt
+            if done % 100 == 0:
+                diag.append(sim.get_moments(ids["beam"], api.PIC_FRAME_LAB, k_bunch=k_lab)["bunching"])
+    else:
+        sim.step(args.steps)
     e1.record(stream)
     sim.sync()
     torch.cuda.synchronize()
@@ -672,6 +721,8 @@ def run_gbpic(args):
             cv, ct, sample = oracle_sample_vacuum(20, 0)
         elif ens is not None:
             cv, ct, sample = oracle_sample_ensemble(2, 0)
+        elif args.workload == "long_undulator":
+            cv, ct, sample = oracle_sample_long(10, 0)
         else:
             cv, ct, sample = oracle_sample(3, 0)
         cpu = {"value": cv, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
@@ -697,6 +748,7 @@ def run_gbpic(args):
                        "sort_every_from": "autotuner" if tuned else "workload",
                        "l2": l2,
                        "window_shifts_in_timed_region": int(shifts_timed),
+                       "lab_bunching_every_100_steps": diag if diag else None,
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "fp32_vs_fp64": accuracy, "adjoint": adjoint,
@@ -730,7 +782,8 @@ def main():
     ap.add_argument("--autotune", action="store_true",
                     help="buncher: pick the sort cadence with the autotuner (its slow drift makes the "
                          "cadence matter little; the default keeps 8)")
-    ap.add_argument("--workload", choices=["buncher", "buncher2d", "ensemble", "vacuum", "adjoint"], default="buncher",
+    ap.add_argument("--workload", choices=["buncher", "buncher2d", "long_undulator", "ensemble", "vacuum", "adjoint"],
+                    default="buncher",
                     help="buncher: the plasma buncher 128x128x512 (default); ensemble: the batched sweep "
                          "of 64 runs of 64x64x128 in one context")
     args = ap.parse_args()

@@ -122,6 +122,13 @@ __device__ __forceinline__ void cross(const float a[3], const float b[3], float 
     c[2] = a[0] * b[1] - a[1] * b[0];
 }
 
+// PASS 0: the whole particle adjoint in one kernel.  PASS 1 and 2 split it around a per-record
+// intermediate so that neither half keeps the other's values live (the single kernel spills):
+// pass 1 recomputes the forward step and reverses the deposit and the move, leaving in lx the
+// position adjoint gathered so far and in lu the adjoint of u^{n+1/2}; pass 2 recomputes the
+// gather (with its derivatives) and Boris, reverses Boris and the gather, and writes the final
+// adjoints of x^n and u^{n-1/2}.  Both passes do the same arithmetic as the single kernel.
+template <int PASS>
 __global__ void __launch_bounds__(kAdjThreads, 2) k_adj_particles(AdjP a)
 {
     const GridDev &g = a.g;
@@ -188,9 +195,11 @@ __global__ void __launch_bounds__(kAdjThreads, 2) k_adj_particles(AdjP a)
                         const int ix = (st0 ? ns[0][i] : nu[0][i]) + (st1 ? ns[1][j] : nu[1][j]) + (st2 ? ns[2][k] : nu[2][k]);
                         const float f = __ldg(fld + ix);
                         v = fmaf(wx * wy * wz, f, v);
-                        dv[0] = fmaf(dx_ * wy * wz, f, dv[0]);
-                        dv[1] = fmaf(wx * dy_ * wz, f, dv[1]);
-                        dv[2] = fmaf(wx * wy * dz_, f, dv[2]);
+                        if constexpr (PASS != 1) {
+                            dv[0] = fmaf(dx_ * wy * wz, f, dv[0]);
+                            dv[1] = fmaf(wx * dy_ * wz, f, dv[1]);
+                            dv[2] = fmaf(wx * wy * dz_, f, dv[2]);
+                        }
                     }
             F[comp] = v;
 #pragma unroll
@@ -224,6 +233,15 @@ __global__ void __launch_bounds__(kAdjThreads, 2) k_adj_particles(AdjP a)
         const float ig1 = rsqrtf(1.f + dot3<3>(u1, u1));
         float dd[3];
         for (int d = 0; d < 3; d++) dd[d] = u1[d] * ig1 * g.dt_over_d[d];
+        float lo[3] = {0.f, 0.f, 0.f};
+        float lu1[3];
+        if constexpr (PASS == 2) {
+            // pass 1's position adjoint so far and adjoint of u^{n+1/2}
+            const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 LX = live ? a.lx[p] : z4, LU = live ? a.lu[p] : z4;
+            lo[0] = LX.x; lo[1] = LX.y; lo[2] = LX.z;
+            lu1[0] = LU.x; lu1[1] = LU.y; lu1[2] = LU.z;
+        } else {
         // ---- adjoint of the deposit (general window of three nodes per dim)
         const float w = Mo.w;
         int st[3], wn[3][3];       // window start (-1 or 0) and the window's node offsets
@@ -276,7 +294,7 @@ __global__ void __launch_bounds__(kAdjThreads, 2) k_adj_particles(AdjP a)
             lDS[comp][1] += fac * lP[1];
         }
         // A = S0 + DS/2, Q = DS/12, DS = Sn - S0; S0 = S(o - m), Sn = S(o + d - m)
-        float lo[3] = {0.f, 0.f, 0.f}, ld[3] = {0.f, 0.f, 0.f};
+        float ld[3] = {0.f, 0.f, 0.f};
         for (int d = 0; d < 3; d++)
             for (int q = 0; q < 3; q++) {
                 const float lds = lDS[d][q] + 0.5f * lA[d][q] + lQ[d][q] * (1.f / 12.f);
@@ -294,13 +312,22 @@ __global__ void __launch_bounds__(kAdjThreads, 2) k_adj_particles(AdjP a)
             lo[d] += lx1[d];
             ld[d] += lx1[d];
         }
-        float lu1[3] = {LU.x, LU.y, LU.z};
+        lu1[0] = LU.x; lu1[1] = LU.y; lu1[2] = LU.z;
         {
             float sdot = 0.f;
             for (int d = 0; d < 3; d++) sdot += ld[d] * g.dt_over_d[d] * u1[d];
             const float ig3 = ig1 * ig1 * ig1;
             for (int d = 0; d < 3; d++) lu1[d] += ld[d] * g.dt_over_d[d] * ig1 - ig3 * u1[d] * sdot;
         }
+        if (live) a.lw[a.sp.id[p]] += (double)lw_step;
+        if constexpr (PASS == 1) {
+            if (live) {
+                a.lx[p] = make_float4(lo[0], lo[1], lo[2], 0.f);
+                a.lu[p] = make_float4(lu1[0], lu1[1], lu1[2], 0.f);
+            }
+            continue;
+        }
+        }   // PASS != 2
         // ---- adjoint of Boris
         float lE[3], lB[3], lum[3], lup[3], lsv[3], lt[3];
         for (int d = 0; d < 3; d++) lE[d] = h * lu1[d];
@@ -418,7 +445,6 @@ __global__ void __launch_bounds__(kAdjThreads, 2) k_adj_particles(AdjP a)
         if (live) {
             a.lx[p] = make_float4(lo[0], lo[1], lo[2], 0.f);
             a.lu[p] = make_float4(lu0[0], lu0[1], lu0[2], 0.f);
-            a.lw[a.sp.id[p]] += (double)lw_step;
         }
     }
     // adjoint of K: block reduction, one atomic per block
@@ -615,8 +641,10 @@ cudaError_t adj_particles(pic_ctx *c, const Species &rec, const float *E, const 
     a.K = (float)c->K;
     a.n = n;
     const int blocks = std::min((n + kAdjThreads - 1) / kAdjThreads, c->num_sms * 8);
-    k_adj_particles<<<blocks, kAdjThreads, 0, c->stream>>>(a);
-    c->kernels++;
+    // two passes around the per-record intermediate in lx, lu (see k_adj_particles)
+    k_adj_particles<1><<<blocks, kAdjThreads, 0, c->stream>>>(a);
+    k_adj_particles<2><<<blocks, kAdjThreads, 0, c->stream>>>(a);
+    c->kernels += 2;
     return cudaGetLastError();
 }
 
