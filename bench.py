@@ -513,12 +513,21 @@ def run_gbpic(args):
         # the long undulator 256x256x1024: 33.5M beam electrons of lab gamma 2000 at rest on average
         # in a frame of gamma_R = gamma / sqrt(1 + K^2/2), TSC, PML on every face, entrance ramp;
         # the FP64 lab-frame bunching is taken every 100 steps inside the timed steps
-        w = W.long_undulator(seed=3 + rank)
+        if args.grid:
+            # a reduced grid keeps the bunch's peak density (sigma_r is 6 cells, sigma_z 1/12 of
+            # the z extent): the beam count scales with nz only
+            grid = tuple(int(v) for v in args.grid.split(","))
+            nb = args.beam or int(round(33554432 * grid[2] / 1024))
+            w = W.long_undulator(grid=grid, n_beam=nb, seed=3 + rank,
+                                 name=f"long undulator {grid[0]}x{grid[1]}x{grid[2]} (reduced), {nb} beam, TSC")
+        else:
+            w = W.long_undulator(seed=3 + rank)
         beam = W.sample_beam(w)
         sim, ids = api.from_workload(w, device=local, beam_arrays=beam)
         ncell_total = w.ncell
         boundaries = "CPML 10 cells on every face, static window"
-        l2 = "inputs larger than L2 (beam state ~2 GB, fields and CPML ~5.6 GB)"
+        l2 = ("inputs larger than L2 (beam state ~2 GB, fields and CPML ~5.6 GB)" if not args.grid else
+              "reduced case for profiling captures")
     elif args.workload == "ensemble":
         # batched sweep: 64 runs of 64x64x128 stacked in one context (one launch per kernel)
         import numpy as np
@@ -541,7 +550,7 @@ def run_gbpic(args):
         boundaries = "periodic (each run)"
         l2 = "inputs larger than L2 (particle state ~8 GB, fields 0.4 GB)"
     else:
-        grid = tuple(int(v) for v in args.grid.split(","))
+        grid = tuple(int(v) for v in (args.grid or "128,128,512").split(","))
         if args.workload == "buncher2d":
             # the paper's 2-D geometry (x-z, ny = 1): 1024 x 2048 cells, 4 ppc, 1M beam
             w = W.plasma_buncher_2d(seed=6 + rank)
@@ -565,7 +574,8 @@ def run_gbpic(args):
         ncell_total = w.ncell
         boundaries = "transverse CPML 10 cells, moving window" + (" (2-D: x PML, y uniform)" if args.workload == "buncher2d" else "")
         l2 = ("inputs larger than L2 (particle state ~0.6 GB, fields 0.05 GB)" if args.workload == "buncher2d"
-              else "inputs larger than L2 (particle state ~9 GB, fields 0.3 GB)")
+              else "inputs larger than L2 (particle state ~9 GB, fields 0.3 GB)" if grid == (128, 128, 512)
+              else "reduced case for profiling captures")
     # periodic workloads replay their steps as CUDA graphs (tracing would turn that off): their
     # kernel-class composition comes from a traced pass after the timed region
     graphs = args.workload in ("vacuum", "ensemble")
@@ -772,8 +782,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true",
                     help="skip the oracle leg (CPU timing and the FP32-vs-FP64 accuracy block)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward block")
-    ap.add_argument("--grid", default="128,128,512",
-                    help="plasma-buncher grid (a smaller one, e.g. 64,64,128, for profiling captures)")
+    ap.add_argument("--grid", default="",
+                    help="grid of the plasma buncher (default 128,128,512) or the long undulator (default "
+                         "256,256,1024); a smaller one, e.g. 64,64,128, for profiling captures")
     ap.add_argument("--beam", type=int, default=0, help="beam macroparticles (0: scaled with the grid)")
     ap.add_argument("--sort-every", type=int, default=0, help="steps between tile sorts (0: the workload's)")
     ap.add_argument("--tile", default="", help="buncher: tile size in cells, e.g. 8,4,4 (default: the workload's)")

@@ -437,6 +437,42 @@ def test_gauss_law_invariant_whole_step():
         assert np.max(np.abs(s.field(EX))) > 1e-4  # fields really evolved
 
 
+def test_threaded_particle_loop_matches_the_serial_loop():
+    # The oracle's threaded particle loop (each thread deposits into a private J, added to the
+    # grid's afterwards) is a timing aid: it must give the serial loop's step up to the order of
+    # the FP64 sums.  A lost private buffer, a double-added one or a race on shared state shows
+    # as an O(1) difference in J, the fields or the particles; Gauss's law must keep holding.
+    grid = (12, 10, 16)
+    d = (0.6, 0.5, 0.8)
+    dt = 0.5 / math.sqrt(sum(1 / v ** 2 for v in d))
+    runs = []
+    for threads in (1, 4):
+        s = oracle.Sim(grid, d, dt, 3.0, order=2)
+        se = s.add_species(-1.0, 1.0)
+        rng = np.random.default_rng(35)
+        n = 4000
+        X = rng.uniform(0, 1, (n, 3)) * np.array(grid)
+        U = rng.normal(size=(n, 3)) * 2
+        s.set_state(se, X, U, rng.uniform(0.5, 1.5, n) * 0.05, np.arange(n))
+        used = s.set_threads(threads)
+        G0 = s.divE() - s.rho()
+        s.step(5)
+        G = s.divE() - s.rho()
+        assert np.max(np.abs(G - G0)) < 1e-11 * max(1.0, np.max(np.abs(G0)))
+        Xo, Uo, _, ids = s.particles(se)
+        o = np.argsort(ids)
+        runs.append((used, [s.field(c) for c in range(9)], Xo[o], Uo[o]))
+    if runs[1][0] < 2:
+        pytest.skip("oracle built without OpenMP")
+    (_, F1, X1, U1), (_, F4, X4, U4) = runs
+    for c in range(9):
+        scale = np.max(np.abs(F1[c]))
+        assert scale > 0
+        np.testing.assert_allclose(F4[c], F1[c], rtol=0, atol=1e-12 * scale)
+    np.testing.assert_allclose(X4, X1, rtol=0, atol=1e-10)
+    np.testing.assert_allclose(U4, U1, rtol=0, atol=1e-11 * np.max(np.abs(U1)))
+
+
 def test_drifting_cold_plasma_oscillates_at_wp_over_gamma():
     # RRF plasma: density gamma_R n0 (Eq. Nnormi), drift -beta_R (Eq. Vprime), frozen ions.
     # A uniform longitudinal velocity perturbation oscillates at w_p0/gamma_R (longitudinal
