@@ -1065,8 +1065,8 @@ void osim_step(void *h, long nsteps)
 
 long osim_dropped(void *h) { return ((osim *)h)->dropped; }
 
-/* Charge density at the nodes from every live particle: rho = sum q w S(node - X) / V. */
-/* Charge density of species q (all species: q < 0) at the nodes, with the deposit's shape. */
+/* Charge density at the nodes, rho = sum q w S(node - X) / V, with the deposit's shape: of
+ * species `only`, or of every live species when only < 0. */
 static void o_rho(const osim *s, int only, double *rho)
 {
     memset(rho, 0, s->ncell * sizeof(double));

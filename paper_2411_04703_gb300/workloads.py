@@ -171,10 +171,14 @@ def plasma_buncher(grid=(128, 128, 512), n_beam=4194304, steps=5000, seed=2, pml
 
 
 def long_undulator(grid=(256, 256, 1024), n_beam=33554432, steps=20000, seed=3, pml=10,
-                   name="long undulator 256x256x1024, 32M beam, TSC") -> Workload:
+                   name="long undulator 256x256x1024, 32M beam, TSC", z_start=None) -> Workload:
     """Long undulator: lab gamma 2000, K = 1.5, lambda_u = 2 cm, boost gamma/sqrt(1+K^2/2)
-    (beam at rest on average), PML on all faces, static window, undulator entrance ramp of
-    one lab period, second-order shape, 64 cells per RRF undulator period."""
+    (beam at rest on average once inside), PML on all faces, static window, second-order shape,
+    64 cells per RRF undulator period.  The beam starts in front of the undulator and enters it
+    through a linear ramp of one lab period (the gentle slope that avoids a transverse kick):
+    by default the entrance sits four RRF bunch lengths ahead of the bunch centre at t' = 0
+    (lab z = gamma_R z' there), so it sweeps over the bunch from head to tail.  z_start = 0 puts
+    the grid's origin at the entrance instead: the bunch then starts inside the field."""
     K = 1.5
     gB = 2000.0
     gR = gB / math.sqrt(1 + K * K / 2)
@@ -188,7 +192,9 @@ def long_undulator(grid=(256, 256, 1024), n_beam=33554432, steps=20000, seed=3, 
     beam = Beam(n=n_beam, gamma=gB, rel_spread=5e-4, emit_n=0.5e-6 / L, sigma_r=6 * dxy,
                 sigma_z=grid[2] * dz / 12 / 1866.0, weight=beam_weight(30e-12, n_beam, omega_n),
                 origin=(grid[0] / 2, grid[1] / 2, grid[2] / 2))
-    und = Undulator(K=K, lambda_u=lam_u_m / L, match=False, z_start=0.0, ramp=lam_u_m / L)
+    if z_start is None:
+        z_start = gR * grid[2] * dz * (0.5 + 4.0 / 12.0)
+    und = Undulator(K=K, lambda_u=lam_u_m / L, match=False, z_start=z_start, ramp=lam_u_m / L)
     return Workload(name=name, grid=grid, d=d, dt=dt, gamma_R=gR,
                     bc=((PML, PML),) * 3, pml=pml, order=2, moving_window=False,
                     window_v=0.0, beam=beam, undulator=und, plasma=None, steps=steps,
@@ -199,6 +205,19 @@ def long_undulator(grid=(256, 256, 1024), n_beam=33554432, steps=20000, seed=3, 
 def mini_vacuum(order=1, seed=11):
     return vacuum_undulator(grid=(20, 18, 44), n_beam=6000, steps=20, seed=seed, order=order,
                             name=f"mini vacuum undulator 20x18x44 order {order}")
+
+
+def mini_dense_bunch(order=2, seed=17, n_beam=150000):
+    """The vacuum undulator's physics on an oracle-sized grid with a dense bunch: sigma_r 1.2
+    cells, ~3 RRF cells long, ~2000 particles per cell at the peak, its core filling one 8^3 tile
+    with a few hundred particles per cell on average (the dense-bunch path of the particle
+    kernel)."""
+    w = vacuum_undulator(grid=(24, 20, 48), n_beam=n_beam, steps=20, seed=seed, order=order,
+                         name=f"mini dense bunch 24x20x48 order {order}")
+    w.beam.sigma_r = 1.2 * w.d[0]
+    w.beam.sigma_z *= 3.0 / 8.0
+    w.beam.origin = (12.0, 12.0, 20.0)
+    return w
 
 
 def mini_plasma(seed=12, grid=(28, 26, 52), n_beam=4000, steps=20):
@@ -238,8 +257,9 @@ def mini_plasma_2d(seed=16, grid=(28, 1, 52), n_beam=3000, steps=20):
 
 
 def mini_long_undulator(seed=13):
+    # the grid lies inside the entrance ramp at t' = 0 (the entrance at its origin)
     w = long_undulator(grid=(24, 20, 48), n_beam=4000, steps=20, seed=seed, pml=4,
-                       name="mini long undulator 24x20x48")
+                       name="mini long undulator 24x20x48", z_start=0.0)
     return w
 
 

@@ -72,7 +72,7 @@ def _sampled_push_check(w, o, before, after, tp, qm=-1.0, tol=1e-5):
 
 
 def test_long_undulator_full_size_push_and_continuity():
-    w = W.long_undulator()
+    w = W.long_undulator(z_start=0.0)      # the bunch inside the field from the first step
     sim, ids = api.from_workload(w)
     rng = np.random.default_rng(7)
     for c in range(6):

@@ -326,6 +326,25 @@ def test_esirkepov_total_current_identity(order):
             assert J[c].sum() * V == pytest.approx(qw * (X1[c] - X0[c]) * d[c] / dt, rel=1e-12, abs=1e-14)
 
 
+def test_deposit_outside_an_open_face_is_dropped_and_counted():
+    # On a non-periodic face the part of the shape beyond the grid has no node to go to: it is
+    # left out of J and counted.  A TSC particle at x = 0.1 (nearest node 0, offset 0.1) has the
+    # weight 0.5 (0.5 - 0.1)^2 = 0.08 on node -1, so a move along z keeps exactly 0.92 of the
+    # total current q w v_z / V, and the interior deposit drops nothing.
+    d = (0.5, 0.8, 1.3)
+    dt = 0.2
+    V = d[0] * d[1] * d[2]
+    s = oracle.Sim((8, 8, 8), d, dt, 5.0, bc=((OPEN, OPEN), (PERIODIC, PERIODIC), (PERIODIC, PERIODIC)), order=2)
+    qw, dz = 0.7, 0.2
+    J = s.deposit_one(qw, [4.1, 4.3, 4.2], [4.1, 4.3, 4.2 + dz])
+    assert s.dropped() == 0
+    assert J[2].sum() * V == pytest.approx(qw * dz * d[2] / dt, rel=1e-12)
+    J = s.deposit_one(qw, [0.1, 4.3, 4.2], [0.1, 4.3, 4.2 + dz])
+    assert s.dropped() > 0
+    assert J[2].sum() * V == pytest.approx((1 - 0.5 * 0.4 ** 2) * qw * dz * d[2] / dt, rel=1e-12)
+    assert np.all(J[0] == 0) and np.all(J[1] == 0)
+
+
 def _frac_shape(order, dd):
     a = abs(dd)
     if order == 1:
