@@ -66,6 +66,8 @@ CASES = {
     "vacuum_tsc_undulator_3d": lambda: _und3d(W.mini_vacuum(order=2)),
     "long_undulator_3d_pml_ramp": lambda: _und3d(W.mini_long_undulator()),
     "plasma_2d_tsc_pml_window": lambda: W.mini_plasma_2d(),
+    "dense_bunch_cic": lambda: W.mini_dense_bunch(order=1),
+    "dense_bunch_tsc": lambda: W.mini_dense_bunch(order=2),
 }
 
 
