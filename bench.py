@@ -44,9 +44,11 @@ BYTES_WEIGHT = 4.0
 BYTES_FROZEN = 32.0
 BYTES_CELL_PUSH = 36.0
 # DRAM bytes (read + write) of the particle kernel per step of the plasma buncher 128x128x512 (its
-# two launches: plasma electrons and beam), from one ncu capture of dram__bytes_read.sum and
-# dram__bytes_write.sum; None until the counters are taken on the kernel as built.
-TRAFFIC_PUSH_BUNCHER_STEP = None
+# two launches: plasma electrons and beam): one-pass ncu capture of dram__bytes_read.sum and
+# dram__bytes_write.sum on the half-length grid 128x128x256 (plasma launch 2.24 GB for 30.38M
+# electrons, beam launch 0.110 GB for 2.10M), scaled by the particles each launch pushes at full
+# size (61.36M and 4.19M).
+TRAFFIC_PUSH_BUNCHER_STEP = 4.74e9
 
 
 def peaks():
@@ -569,7 +571,8 @@ def run_gbpic(args):
     elif args.workload == "ensemble":
         # batched sweep: 64 runs of 64x64x128 stacked in one context (one launch per kernel)
         import numpy as np
-        ens = W.batched_ensemble(runs=args.runs, seed=4 + rank)
+        ens = W.batched_ensemble(runs=args.runs, seed=4 + rank,
+                                 name=f"batched ensemble {args.runs} x (64x64x128), K and density sweep, TSC")
         w = ens.base
         parts = [W.sample_beam(W.ensemble_run(ens, r)) for r in range(ens.runs)]
         beam = (np.concatenate([q[0] for q in parts], axis=1), np.concatenate([q[1] for q in parts], axis=1),
@@ -577,16 +580,19 @@ def run_gbpic(args):
         if args.sort_every:
             ens.base.sort_every = args.sort_every
         elif not args.no_autotune:
-            # the autotuner's trials advance a run: tune on a throwaway copy, measure a fresh one
+            # the autotuner's trials advance a run: tune tile and cadence on a throwaway copy,
+            # measure a fresh one
             tmp, _ = api.from_ensemble(ens, device=local)
-            ens.base.sort_every = tuned = tmp.autotune(16)
+            tile, tuned = tmp.autotune_tiles(((8, 8, 8), (8, 8, 4), (8, 4, 4), (4, 4, 4)), 16)
+            ens.base.tile, ens.base.sort_every = tuple(tile), tuned
             tmp.close()
             del tmp
             torch.cuda.empty_cache()
         sim, ids = api.from_ensemble(ens, device=local)
         ncell_total = w.ncell * ens.runs
         boundaries = "periodic (each run)"
-        l2 = "inputs larger than L2 (particle state ~8 GB, fields 0.4 GB)"
+        l2 = (f"inputs larger than L2 (particle state ~{8 * ens.runs / 64:.1f} GB, fields "
+              f"{0.4 * ens.runs / 64:.2f} GB)")
     else:
         grid = tuple(int(v) for v in (args.grid or "128,128,512").split(","))
         if args.workload == "buncher2d":
@@ -786,6 +792,7 @@ def run_gbpic(args):
                        "shape": shape, "boundaries": boundaries,
                        "tile": list(w.tile), "sort_every": tuned if tuned else w.sort_every,
                        "sort_every_from": "autotuner" if tuned else "workload",
+                       "tile_from": "autotuner" if (tuned and ens is not None) else "workload",
                        "l2": l2,
                        "window_shifts_in_timed_region": int(shifts_timed),
                        "lab_bunching_every_100_steps": diag if diag else None,

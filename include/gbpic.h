@@ -430,8 +430,9 @@ int pic_tile_sort_noalloc(const int32_t *cells, int64_t n, const int grid[3], co
  * state at the start of the differentiated interval and every every_k steps after (pic_step then
  * also sorts at those steps); pic_backward restores each checkpoint in reverse order, recomputes
  * its segment recording every step, and runs the segment's adjoint.  Requirements: first-order
- * shape, Boris pusher, one run, periodic grid, no moving window or PML, undulator without
- * entrance ramp; otherwise PIC_ERR_ARG and nothing is recorded.  every_k <= 0 turns recording off
+ * shape, Boris pusher, momentum-conserving gather, one run, periodic grid, no moving window or
+ * PML, the 1-D planar undulator field without entrance ramp, no artificial ions; otherwise
+ * PIC_ERR_ARG and nothing is recorded.  every_k <= 0 turns recording off
  * and frees the checkpoints.  The checkpoints and the per-step records of one segment are device
  * allocations of the context (about 250 MB per recorded step for 6.3M particles on 64x64x256). */
 int pic_checkpoint(pic_ctx *ctx, int every_k);

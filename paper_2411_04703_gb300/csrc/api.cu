@@ -1676,6 +1676,7 @@ int pic_checkpoint(pic_ctx *c, int every_k)
         return fail(c, PIC_ERR_ARG, "the adjoint is built for the 1-D planar undulator field");
     if (c->gather != PIC_GATHER_MOMENTUM)
         return fail(c, PIC_ERR_ARG, "the adjoint reverses the momentum-conserving gather");
+    if (c->ion_G) return fail(c, PIC_ERR_ARG, "the adjoint does not differentiate the artificial ions");
     drop_graph(c);
     c->ad_on = 1;
     c->ad_every = every_k;

@@ -392,6 +392,28 @@ def test_artificial_ion_ramp_keeps_gauss_law_on_gpu():
     assert np.max(np.abs(sim.get_field(api.PIC_EZ))) > 0
 
 
+def test_adjoint_refuses_what_it_does_not_differentiate():
+    # the artificial ions' current, the energy-conserving gather and the Vay pusher are not
+    # reversed by the adjoint: recording is refused with them, and they are refused while recording
+    w = W.mini_vacuum(order=1)
+    sim, ids = api.from_workload(w)
+    sim.set_ion_ramp(ids["beam"], 3.0 * w.dt)
+    with pytest.raises(api.PicError, match="artificial ions"):
+        sim.checkpoint(10)
+    sim.set_ion_ramp(ids["beam"], 0.0)
+    sim.set_gather(api.PIC_GATHER_ENERGY)
+    with pytest.raises(api.PicError, match="momentum-conserving gather"):
+        sim.checkpoint(10)
+    sim.set_gather(api.PIC_GATHER_MOMENTUM)
+    sim.checkpoint(10)
+    with pytest.raises(api.PicError, match="artificial ions"):
+        sim.set_ion_ramp(ids["beam"], 3.0 * w.dt)
+    with pytest.raises(api.PicError, match="Boris"):
+        sim.set_pusher(api.PIC_PUSHER_VAY)
+    sim.checkpoint(0)
+    sim.close()
+
+
 def test_lab_snapshot_tracks_oracle():
     # The time-skew reconstruction at one lab time on the GPU against the oracle's: the long
     # undulator case (entrance ramp, PML, TSC), both sides loading the same seeded lab beam; the
