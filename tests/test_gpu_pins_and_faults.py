@@ -112,6 +112,46 @@ def test_gpu_boris_rotates_in_a_uniform_magnetic_field():
     sim.close()
 
 
+def test_gpu_entrance_ramp_leaves_no_transverse_drift():
+    # The GPU path against the closed form (no oracle): zero-weight electrons of the long
+    # undulator's beam meet the undulator with u_x = 0; past a one-period linear ramp their
+    # canonical drift P = u_x - K sin(k_u z_lab) vanishes for any entrance phase, past a sudden
+    # entrance it is -K sin(theta) up to the leap-frog error of the jump.
+    w = W.long_undulator(grid=(16, 16, 64), n_beam=4)
+    K, lam = w.undulator.K, w.undulator.lambda_u
+    gR, dz, dt = w.gamma_R, w.d[2], w.dt
+    ku = 2 * math.pi / lam
+    gB = 2000.0
+    bB = math.sqrt(1 - 1 / gB ** 2)
+    bR = math.sqrt(1 - 1 / gR ** 2)
+    vp = (bB - bR) / (1 - bB * bR)
+    for theta in (math.pi / 2, 0.3 + 2 * math.pi, 4.0):
+        for ramp in (lam, 0.0):
+            sim = api.Sim((16, 16, 64), w.d, dt, gR, bc=((0, 0),) * 3, order=2)
+            zs = theta / ku
+            sim.set_external_field(K, lam, 0.0, zs, ramp)
+            x = np.zeros((3, 3))
+            x[0] = [0.0, 0.3, -0.2]
+            u = np.zeros((3, 3))
+            u[2] = math.sqrt(gB * gB - 1)
+            sid = sim.load_species(-1.0, 1.0, x, u, np.zeros(3), frame=api.PIC_FRAME_LAB, origin=(8.0, 8.0, 10.0))
+            P0 = _by_id(sim.get_particles(sid))
+            z0 = (P0["cell"][:, 2] + P0["off"][:, 2]).min()
+            n = int(((zs + ramp) / gR - z0 * dz) / ((vp + bR) * dt)) + 20
+            sim.step(n)
+            A = _by_id(sim.get_particles(sid))
+            sim.step(1)
+            Bp = _by_id(sim.get_particles(sid))
+            zc = A["cell"][:, 2].astype(np.float64) + A["off"][:, 2]
+            zlab = gR * (zc * dz + bR * n * dt)
+            P = 0.5 * (A["u"][:, 0].astype(np.float64) + Bp["u"][:, 0]) - K * np.sin(ku * zlab)
+            if ramp > 0:
+                assert np.all(np.abs(P) < 5e-3 * K), (theta, P / K)
+            else:
+                assert np.all(np.abs(P + K * math.sin(theta)) < 0.05 * K), (theta, P / K)
+            sim.close()
+
+
 # ------------------------------------------------------------------ degenerate and handover cases
 
 def test_empty_species_steps_as_vacuum():

@@ -172,6 +172,50 @@ def test_undulator_entrance_ramp_sits_at_its_lab_position():
             np.testing.assert_allclose(Bs, f_step * Bf, rtol=1e-9, atol=1e-12)
 
 
+def test_entrance_ramp_of_one_period_leaves_no_transverse_drift():
+    # An electron that meets the undulator with u_x = 0 keeps its canonical momentum u_x - A_x
+    # (q = -1; the field does not depend on x) at the value it had before the entrance, where A_x
+    # = 0.  Past the entrance, P = u_x - A_ideal(z) with A_ideal = (B0/k_u) sin(k_u z) is the drift
+    # of its oscillation: through a linear ramp of one period the integral of the missing field
+    # cancels exactly, P = 0, whatever the entrance phase theta; a sudden entrance leaves
+    # P = -K sin(theta), the transverse kick the paper's gentle slope avoids (Sec. "Electron
+    # propagation in vacuum and under external field"), up to the leap-frog error of the jump.
+    # Zero-weight electrons (no self fields) of the long-undulator beam, in its boosted frame.
+    from paper_2411_04703_gb300 import workloads as W
+    w = W.long_undulator(grid=(16, 16, 64), n_beam=4)
+    K, lam = w.undulator.K, w.undulator.lambda_u
+    gR, dz, dt = w.gamma_R, w.d[2], w.dt
+    ku = 2 * math.pi / lam
+    gB = 2000.0
+    bB = math.sqrt(1 - 1 / gB ** 2)
+    for theta in (math.pi / 2, 0.3 + 2 * math.pi, 2.0, 4.0, 5.5):   # entrance ahead of the electrons
+        for ramp in (lam, 0.0):
+            s = oracle.Sim((16, 16, 64), w.d, dt, gR, order=2)
+            zs = theta / ku                                        # lab entrance at phase theta
+            s.set_external(K, lam, 0.0, zs, ramp)
+            sid = s.add_species(-1.0, 1.0)
+            x = np.zeros((3, 3))
+            x[0] = [0.0, 0.3, -0.2]
+            u = np.zeros((3, 3))
+            u[2] = math.sqrt(gB * gB - 1)
+            s.load(sid, x, u, w=np.zeros(3), frame=LAB, origin=(8.0, 8.0, 10.0))
+            X, _, _, _ = s.particles(sid)
+            bR = s.beta_R
+            vp = (bB - bR) / (1 - bB * bR)                         # RRF velocity before the entrance
+            n = int(((zs + ramp) / gR - X[:, 2].min() * dz) / ((vp + bR) * dt)) + 20
+            s.step(n)
+            X, U0, _, _ = s.particles(sid)
+            s.step(1)
+            _, U1, _, _ = s.particles(sid)
+            zlab = gR * (X[:, 2] * dz + bR * n * dt)
+            P = 0.5 * (U0[:, 0] + U1[:, 0]) - np.array([s.undulator_Ax(z) for z in zlab])
+            if ramp > 0:
+                assert np.all(np.abs(P) < 2e-3 * K), (theta, P / K)
+            else:
+                assert np.all(np.abs(P + K * math.sin(theta)) < 0.05 * K), (theta, P / K)
+                assert np.all(np.abs(P) > 0.2 * K), (theta, P / K)
+
+
 # ------------------------------------------------------------------ push
 
 def test_boris_uniform_electric_field_exact():
