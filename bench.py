@@ -539,8 +539,12 @@ def run_gbpic(args):
         # the vacuum undulator 32x32x64, 65,536 beam electrons, CIC: small enough to be bound by
         # launches, so its step sequence runs as a replayed CUDA graph
         w = W.vacuum_undulator(seed=1 + rank)
+        if args.sort_every:
+            w.sort_every = args.sort_every
         beam = W.sample_beam(w)
         sim, ids = api.from_workload(w, device=local, beam_arrays=beam)
+        if args.autotune and not args.sort_every:
+            w.sort_every = tuned = sim.autotune(16)     # the trials advance this periodic run
         ncell_total = w.ncell
         boundaries = "periodic"
         l2 = "L2-resident (fields 2.4 MB, particles 2 MB): launch-bound, timed as a CUDA graph"
@@ -557,6 +561,8 @@ def run_gbpic(args):
                                  name=f"long undulator {grid[0]}x{grid[1]}x{grid[2]} (reduced), {nb} beam, TSC")
         else:
             w = W.long_undulator(seed=3 + rank)
+        if args.sort_every:
+            w.sort_every = args.sort_every
         beam = W.sample_beam(w)
         sim, ids = api.from_workload(w, device=local, beam_arrays=beam)
         # the bunch starts in front of the undulator; the timed steps are those of the run inside
@@ -564,6 +570,10 @@ def run_gbpic(args):
         pre_steps = entry_steps(w)
         sim.step(pre_steps)
         sim.sync()
+        if args.autotune and not args.sort_every:
+            t0_steps = sim.get_time()[0]
+            w.sort_every = tuned = sim.autotune(16)     # trials inside the undulator, after the entry
+            pre_steps += sim.get_time()[0] - t0_steps
         ncell_total = w.ncell
         boundaries = "CPML 10 cells on every face, static window"
         l2 = ("inputs larger than L2 (beam state ~2 GB, fields and CPML ~5.6 GB)" if not args.grid else
@@ -829,8 +839,8 @@ def main():
     ap.add_argument("--runs", type=int, default=64, help="ensemble runs (the batched sweep has 64)")
     ap.add_argument("--no-autotune", action="store_true", help="ensemble: keep the workload's sort cadence")
     ap.add_argument("--autotune", action="store_true",
-                    help="buncher: pick the sort cadence with the autotuner (its slow drift makes the "
-                         "cadence matter little; the default keeps 8)")
+                    help="buncher, vacuum, long undulator: pick the sort cadence with the autotuner "
+                         "(the default keeps the workload's 8)")
     ap.add_argument("--workload", choices=["buncher", "buncher2d", "long_undulator", "ensemble", "vacuum", "adjoint"],
                     default="buncher",
                     help="buncher: the plasma buncher 128x128x512 (default); ensemble: the batched sweep "

@@ -131,6 +131,7 @@ int make_species(pic_ctx *c, double q, double m, int frozen, int64_t cap, int *s
         (r = alloc_zero(c, &s.items, s.max_items)) || (r = alloc_zero(c, &s.cell_start, c->n_keys + 1)) ||
         (r = alloc_zero(c, &s.chunk_start, c->ntiles + 1)) || (r = alloc_zero(c, &s.dlim, 4)) ||
         (r = alloc_zero(c, &s.sparse_start, c->ntiles + 1)) || (r = alloc_zero(c, &s.sparse_tiles, c->ntiles)) ||
+        (r = alloc_zero(c, &s.tile_start, c->ntiles + 1)) || (r = alloc_zero(c, &s.occ, c->ntiles + 1)) ||
         (r = alloc_zero(c, &s.dmax, 4)))
         return r;
     {
@@ -211,12 +212,15 @@ int retile(pic_ctx *c, const int T[3])
         dfree(c, s.chunk_start);
         dfree(c, s.sparse_start);
         dfree(c, s.sparse_tiles);
+        dfree(c, s.tile_start);
+        dfree(c, s.occ);
         s.items = nullptr;
-        s.cell_start = s.chunk_start = s.sparse_start = s.sparse_tiles = nullptr;
+        s.cell_start = s.chunk_start = s.sparse_start = s.sparse_tiles = s.tile_start = s.occ = nullptr;
         s.max_items = c->ntiles + s.cap / kChunkMin + 2;
         if ((r = alloc_zero(c, &s.items, s.max_items)) || (r = alloc_zero(c, &s.cell_start, c->n_keys + 1)) ||
             (r = alloc_zero(c, &s.chunk_start, c->ntiles + 1)) || (r = alloc_zero(c, &s.sparse_start, c->ntiles + 1)) ||
-            (r = alloc_zero(c, &s.sparse_tiles, c->ntiles)))
+            (r = alloc_zero(c, &s.sparse_tiles, c->ntiles)) || (r = alloc_zero(c, &s.tile_start, c->ntiles + 1)) ||
+            (r = alloc_zero(c, &s.occ, c->ntiles + 1)))
             return r;
     }
     c->sort_base = c->step;   // the stored order is of the old tiles: sort before the next push
@@ -387,6 +391,7 @@ TileDev tile_dev(const pic_ctx *c, const Species &s)
     t.hl = margin_lo(c);
     for (int d = 0; d < 3; d++) t.R[d] = c->T[d] + 2 * c->M + margin_lo(c) + margin_hi(c);
     t.cell_start = s.cell_start;
+    t.tile_start = s.tile_start;
     t.items = s.items;
     t.sparse_tiles = s.sparse_tiles;
     t.chunk = s.chunk;

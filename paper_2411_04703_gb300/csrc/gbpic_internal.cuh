@@ -133,7 +133,9 @@ struct TileDev {
     int M;                // allowed drift outside the tile between sorts (cells)
     int hl;               // stencil reach below the particle cell (1 CIC, 2 TSC)
     int R[3];             // shared-memory region size per dim
-    const int *cell_start;   // [n_keys + 1]: first sorted slot of each key (8 keys per cell)
+    const int *cell_start;   // [n_keys + 1]: first sorted slot of each key (8 keys per cell), valid
+                             // for the tiles holding particles at the last sort
+    const int *tile_start;   // [ntiles + 1]: first sorted slot of each tile (the last: the live count)
     const int2 *items;       // (tile, chunk) work items of the tiles with >= kSparse particles
     const int *sparse_tiles; // tiles with 1 .. kSparse-1 particles (count[3] of them)
     int chunk;               // particles per work item (kChunkMin .. kChunk), fixed at the sort
@@ -176,7 +178,10 @@ struct Species {
     int *rank = nullptr;      // device [cap] sort scratch
     int2 *items = nullptr;    // device work items
     int64_t max_items = 0;
-    int *cell_start = nullptr;  // device [n_keys + 1]
+    int *cell_start = nullptr;  // device [n_keys + 1]; zero outside the tiles listed in occ
+    int *tile_start = nullptr;  // device [ntiles + 1]: particles per tile, then their exclusive scan
+    int *occ = nullptr;         // device [ntiles + 1]: the tiles holding particles at the last sort;
+                                // occ[ntiles] counts them
     int *chunk_start = nullptr; // device [ntiles + 1]
     int *sparse_start = nullptr;  // device [ntiles + 1]: scan of the sparse-tile flags
     int *sparse_tiles = nullptr;  // device [ntiles]: the sparse tiles

@@ -600,9 +600,8 @@ k_push(SpeciesDev sp, GridDev g, TileDev t, FieldsDev f, ExtDev ext0, int *work,
         const int tx = tile % t.nt[0], ty = (tile / t.nt[0]) % t.nt[1], tz = tile / (t.nt[0] * t.nt[1]);
         const int t0[3] = {tx * t.T[0], ty * t.T[1], tz * t.T[2]};
         const int reg0[3] = {t0[0] - t.M - t.hl, t0[1] - t.M - t.hl, t0[2] - t.M - t.hl};
-        const int key0 = tile * t.tile_cells * 8;
-        const int p_begin = t.cell_start[key0] + wi.y * chunk;
-        const int p_end = min(p_begin + chunk, t.cell_start[key0 + t.tile_cells * 8]);
+        const int p_begin = t.tile_start[tile] + wi.y * chunk;
+        const int p_end = min(p_begin + chunk, t.tile_start[tile + 1]);
         // Region of the tile: nodes reg0 + (0..R-1) per dim (plane pitch padded).
         const int R2 = reg.r2(), Ry = reg.ry(), Rz = R3 / R2;
         const int zb = g.nzr == g.n[2] ? 0 : zblock(t0[2], g.nzr);   // the tile's run (tiles never straddle runs)
@@ -763,15 +762,14 @@ k_push(SpeciesDev sp, GridDev g, TileDev t, FieldsDev f, ExtDev ext0, int *work,
     // sparse tiles (fewer than kSparse particles): staging and flushing a region would cost more
     // than the global-memory path of their few particles; each warp takes whole tiles
     const int n_sparse = sp.count[3];
-    const int kpt = t.tile_cells * 8;
     for (;;) {
         int it = 0;
         if (lane == 0) it = atomicAdd(work_sparse, 1);
         it = __shfl_sync(0xffffffffu, it, 0);
         if (it >= n_sparse) break;
         const int tile = t.sparse_tiles[it];
-        const int pe = t.cell_start[(tile + 1) * kpt];
-        for (int p = t.cell_start[tile * kpt] + lane; p < pe; p += 32) step_global<ORDER, FROZEN, GATHER>(sp, g, f, ext, err, p);
+        const int pe = t.tile_start[tile + 1];
+        for (int p = t.tile_start[tile] + lane; p < pe; p += 32) step_global<ORDER, FROZEN, GATHER>(sp, g, f, ext, err, p);
     }
 }
 
