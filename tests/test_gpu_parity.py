@@ -216,6 +216,48 @@ def test_whole_run_tracks_oracle(case):
                 assert mg[key] == pytest.approx(mo[key], rel=1e-3), (frame, key)
 
 
+def test_long_undulator_entry_through_the_ramp_tracks_oracle():
+    # The long undulator's bunch in front of the undulator at t' = 0 (its entrance two cells past
+    # the bunch's 3-sigma head), through the one-period ramp until the whole bunch is inside: the
+    # same initial state on both sides, then the GPU and the oracle step on their own (self fields
+    # of a bunch of 1e-3 of the workload's charge, CPML on every face); the bunch's momenta and
+    # diagnostics in both frames agree within the ensemble tolerance, no particle is lost, and the
+    # bunch ends up oscillating in the field.
+    import math
+    import os
+    grid = (48, 40, 96)
+    w = W.long_undulator(grid=grid, n_beam=4000, steps=200, pml=4, name="long undulator entry 48x40x96")
+    w.beam.sigma_r = 3.0 * w.d[0]
+    w.beam.weight *= 1e-3
+    w.beam.origin = (24.0, 20.0, 40.0)
+    sig = grid[2] / 12.0                        # RRF bunch length (cells) before the entrance
+    un, b = w.undulator, w.beam
+    gR = w.gamma_R
+    un.z_start = gR * (b.origin[2] + 3 * sig + 2) * w.d[2]
+    bR, bB = math.sqrt(1 - 1 / gR ** 2), math.sqrt(1 - 1 / b.gamma ** 2)
+    vp = (bB - bR) / (1 - bB * bR)              # RRF velocity before the entrance
+    n = int(math.ceil(((un.z_start + un.ramp) / gR - (b.origin[2] - 3 * sig) * w.d[2]) / ((bR + vp) * w.dt))) + 10
+    sim, ids = api.from_workload(w)
+    o, oid = parity.oracle_from_gpu(w, sim, ids)
+    o.set_threads(os.cpu_count() or 1)
+    n0 = sim.get_count(ids["beam"])
+    sim.step(n)
+    sim.sync()
+    o.step(n)
+    assert sim.get_count(ids["beam"]) == n0 == o.count(oid["beam"])
+    r = parity.compare_species(w, sim, ids["beam"], o, oid["beam"])
+    assert r["only_gpu"] + r["only_oracle"] <= max(2, r["ties"]), r
+    assert r["u_rel_err"] < 1e-3, r
+    for frame in (api.PIC_FRAME_BOOSTED, api.PIC_FRAME_LAB):
+        mg = sim.get_moments(ids["beam"], frame, k_bunch=1.0)
+        mo = o.moments(oid["beam"], frame=0 if frame == api.PIC_FRAME_BOOSTED else 1, k=1.0)
+        for key in ["emit_nx", "emit_ny", "rel_energy_spread", "rms_z", "mean_gamma"]:
+            assert mg[key] == pytest.approx(mo[key], rel=1e-3), (frame, key)
+        assert abs(mg["mean_ux"] - mo["mean_ux"]) < 1e-3 * un.K, frame
+    ux = sim.get_particles(ids["beam"])["u"][:, 0]
+    assert np.sqrt(np.mean(ux.astype(np.float64) ** 2)) > 0.5 * un.K   # inside the field
+
+
 PML_CASES = ["plasma_tsc_pml_window", "long_undulator_tsc_pml_ramp"]
 
 
