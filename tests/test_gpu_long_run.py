@@ -94,3 +94,40 @@ def test_plasma_buncher_300_steps_diagnostics_track_oracle():
             for key in ("bunching", "emit_nx", "emit_ny", "rel_energy_spread"):
                 assert mg[key] == pytest.approx(mo[key], rel=TOL_DIAG), (frame, k, key, mg[key], mo[key])
     sim.close()
+
+
+def test_plasma_buncher_after_the_tile_autotuner_tracks_oracle():
+    # The same plasma-buncher physics, with the tile size and sort cadence chosen by
+    # pic_autotune_tiles on the GPU run itself: its trial steps (several hundred, each candidate
+    # re-tiling the species, with window shifts and plasma injection) are real steps, and the
+    # oracle takes as many from the same initial state; the beam's diagnostics in both frames agree
+    # to 1e-3 and the plasma electron count is exact.
+    import os
+    w = W.mini_plasma(steps=300)
+    x, u, wt = W.sample_beam(w)
+    sim, ids = api.from_workload(w, beam_arrays=(x, u, wt))
+    o = oracle.Sim(w.grid, w.d, w.dt, w.gamma_R, bc=w.bc, pml=w.pml, order=w.order,
+                   moving_window=w.moving_window, window_v=w.window_v)
+    o.set_threads(os.cpu_count() or 1)
+    se = o.add_species(-1.0, 1.0)
+    si = o.add_species(1.0, 1836.15267343, frozen=True)
+    sb = o.add_species(-1.0, 1.0, capacity=x.shape[1])
+    p = w.plasma
+    o.set_plasma(se, si, p.ppc, p.xrange, p.z_nodes, p.n_nodes)
+    o.load(sb, x, u, wt, frame=oracle.LAB, origin=w.beam.origin)
+    cands = ((8, 8, 8), (4, 4, 4))
+    tile, se_ = sim.autotune_tiles(cands, max_sort_every=2)
+    assert tile in cands and se_ in (1, 2)
+    n = sim.get_time()[0]
+    sim.sync()
+    o.step(n)
+    assert sim.get_time() == o.time()
+    assert n >= 4 * 32 and sim.get_time()[1] >= 30     # the window moved through the plasma
+    assert sim.get_count(ids["plasma_e"]) == o.count(se)
+    for frame, oframe in ((api.PIC_FRAME_BOOSTED, 0), (api.PIC_FRAME_LAB, 1)):
+        mg = sim.get_moments(ids["beam"], frame, k_bunch=1.0)
+        mo = o.moments(sb, frame=oframe, k=1.0)
+        assert mg["count"] == mo["count"]
+        for key in ("bunching", "emit_nx", "emit_ny", "rel_energy_spread"):
+            assert mg[key] == pytest.approx(mo[key], rel=TOL_DIAG), (frame, key, mg[key], mo[key])
+    sim.close()

@@ -94,7 +94,7 @@ def test_one_step_from_identical_state(case):
 
 
 @pytest.mark.parametrize("tile", [(8, 4, 4), (4, 4, 4), (8, 8, 4)])
-@pytest.mark.parametrize("case", ["vacuum_cic", "plasma_tsc_pml_window"])
+@pytest.mark.parametrize("case", ["vacuum_cic", "plasma_tsc_pml_window", "dense_bunch_tsc"])
 def test_one_step_on_other_tiles_from_identical_state(case, tile):
     # tiles other than 8^3 run the particle kernel's runtime-sized region (what the tile
     # autotuner can choose): the same per-step bar against the oracle
