@@ -799,9 +799,9 @@ def run_gbpic(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": w.name, "grid": list(w.grid), "beam": int(n_beam),
                        "plasma_electrons": int(n_e), "frozen_ions": int(0.5 * (frozen0 + frozen1)),
-                       "plasma_fill": ("the lattice fills every cell that the transverse absorbing layers and "
-                                       "the shape's margins leave (8 ppc there), not the whole grid"
-                                       if w.plasma is not None else None),
+                       "plasma_fill": (f"the lattice fills every cell that the transverse absorbing layers and "
+                                       f"the shape's margins leave ({w.plasma.ppc[0] * w.plasma.ppc[1] * w.plasma.ppc[2]}"
+                                       f" per cell there), not the whole grid" if w.plasma is not None else None),
                        "shape": shape, "boundaries": boundaries,
                        "tile": list(w.tile), "sort_every": tuned if tuned else w.sort_every,
                        "sort_every_from": "autotuner" if tuned else "workload",
